@@ -1,0 +1,33 @@
+"""FP64 CPU oracle for one explicit inertial-coupling (IC) time step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain, obviously-correct
+statement of what the GPU path computes, written from the paper (Balboa
+Usabiaga & Delgado-Buscalioni, "A minimal model for acoustic forces on
+Brownian particles", arXiv 1307.0702).  Only ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+The product path (``paper_1307_0702_gb300``) never imports, calls or links it,
+and it shares no code with the CUDA library: the only common module is the
+seeded workload generator, which holds no arithmetic of the method.
+
+Modules
+-------
+peskin  : 3-point Roma-Peskin function, staggered kernel weights, J and S
+          (Sec. 2, Eqs. (Jdis), (Sdis), (k1), (k2), (kvol); App. A.1).
+philox  : Philox4x32-10 counter-based generator and the Box-Muller normal
+          transform used for the stochastic stress (App. A.2, Eqs. for W_1..W_3).
+fluid   : conservative staggered flux divergence and the SSP-RK3 substep
+          (Sec. 4.2 Eqs. (eq:consvDens), (eq:consvMom), (totp); App. A.2).
+ic      : the full IC time step, substeps 1-7 of App. A.2, with the particle
+          pressure of Eqs. (eq:pressure), (omega).
+theory  : closed forms used as pins (Eqs. (eq:acousticForce2), (f1), (f2),
+          (part_svel), (ke), (eq:densityVariance); discrete dispersion).
+
+Parity status
+-------------
+Every function here is pinned by a ``-m "not gpu"`` test against something
+other than itself (closed forms, invariants, published known answers, brute
+force), except the rounding order of the nonlinear advection flux, whose
+discretisation the paper leaves to a reference that is not available: the
+advective flux form is a reading, "parity unpinned" beyond the invariants it
+must satisfy (mass and momentum conservation, Galilean-free linear limit).
+"""

@@ -1,0 +1,158 @@
+"""Seeded synthetic workloads (inputs only; no arithmetic of the method).
+
+Each recipe returns plain host data: a dict of grid parameters, the initial
+density and momentum fields, and the particle arrays.  The same arrays feed
+the CUDA library and the CPU oracle in the tests and the benchmark.  The
+paper uses no dataset: these stand in for its Table I runs and for the
+standing-wave, thermal and many-particle workloads of the benchmark.
+
+Units: h = 1, rho0 = 1, c = 4, eta = 0.5, dt = 0.1 h / c unless stated.
+Volume of one particle kernel V = 8 h^3 (excess mass m_e is given in units of
+rho0 V through ``mass_ratio`` = m_p / (rho0 V) = 1 + m_e / (rho0 V)).
+"""
+import numpy as np
+
+KERNEL_VOLUME_CELLS = 8.0   # V / h^3 of the 3-point kernel
+
+
+def grid_params(n, *, h=1.0, rho0=1.0, c=4.0, eta=0.5, zeta=0.0, kT=0.0, dt=None,
+                seed=0, forcing="mode", wave_axis=0, wave_amp=1e-3, wave_nlambda=1,
+                precision="fp64", plane_index=0):
+    nx, ny, nz = (n, n, n) if np.isscalar(n) else n
+    return dict(nx=int(nx), ny=int(ny), nz=int(nz), h=float(h), rho0=float(rho0), c=float(c),
+                eta=float(eta), zeta=float(zeta), kT=float(kT),
+                dt=float(0.1 * h / c if dt is None else dt), seed=int(seed),
+                forcing=forcing, wave_axis=int(wave_axis), wave_amp=float(wave_amp),
+                wave_nlambda=int(wave_nlambda), precision=precision, plane_index=int(plane_index))
+
+
+def standing_wave_fields(gp):
+    """rho = rho0 + A cos(k x) along the wave axis, g = 0 (fields shaped [z, y, x])."""
+    shape = (gp["nz"], gp["ny"], gp["nx"])
+    n_ax = (gp["nx"], gp["ny"], gp["nz"])[gp["wave_axis"]]
+    x = np.arange(n_ax) * gp["h"]
+    k = 2.0 * np.pi * gp["wave_nlambda"] / (n_ax * gp["h"])
+    prof = gp["wave_amp"] * np.cos(k * (x - gp["plane_index"] * gp["h"]))
+    bshape = [1, 1, 1]
+    bshape[2 - gp["wave_axis"]] = n_ax
+    rho = gp["rho0"] + np.broadcast_to(prof.reshape(bshape), shape)
+    return np.ascontiguousarray(rho), [np.zeros(shape) for _ in range(3)]
+
+
+def random_fields(gp, seed, amp_rho=1e-3, amp_g=1e-3):
+    """Smooth-free random fields for parity tests: rho0 + amp * U(-1,1), g = amp * U(-1,1)."""
+    rng = np.random.default_rng(seed)
+    shape = (gp["nz"], gp["ny"], gp["nx"])
+    rho = gp["rho0"] + amp_rho * rng.uniform(-1, 1, shape)
+    g = [amp_g * rng.uniform(-1, 1, shape) for _ in range(3)]
+    return rho, g
+
+
+def place_uniform(n_particles, lengths, seed, min_sep=0.0):
+    """Uniform positions in the periodic box, rejection-sampled for a minimum
+    separation (periodic Euclidean distance)."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(lengths, dtype=np.float64)
+    if min_sep <= 0.0:
+        return rng.uniform(0.0, 1.0, (n_particles, 3)) * L
+    out = np.empty((n_particles, 3))
+    count = 0
+    # uniform cell list with cells of side >= min_sep for the rejection test
+    ncell = np.maximum(1, np.floor(L / min_sep).astype(int))
+    csize = L / ncell
+    buckets = {}
+    tries = 0
+    while count < n_particles:
+        tries += 1
+        if tries > 200 * n_particles + 10000:
+            raise RuntimeError("could not place particles with the requested separation")
+        x = rng.uniform(0.0, 1.0, 3) * L
+        c = np.floor(x / csize).astype(int) % ncell
+        ok = True
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    key = tuple((c + np.array([dx, dy, dz])) % ncell)
+                    for j in buckets.get(key, ()):
+                        d = out[j] - x
+                        d -= L * np.round(d / L)
+                        if d @ d < min_sep * min_sep:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            out[count] = x
+            buckets.setdefault(tuple(c), []).append(count)
+            count += 1
+    return out
+
+
+def single_particle_config(n=32, steps=2000):
+    """Deterministic standing wave with one tethered particle (kT = 0, FP64).
+
+    32^3 grid, wave along x with density amplitude 1e-3 rho0 and wavelength L;
+    one particle at (L/8, L/2, L/2) (sin 2kx = 1) with m_p = 1.5 rho0 V and
+    kappa_p = 0.5 kappa_f, tethered by a spring k_s = 1; seed 0.
+    """
+    gp = grid_params(n, wave_amp=1e-3, seed=0)
+    L = n * gp["h"]
+    parts = dict(q=np.array([[L / 8.0, L / 2.0, L / 2.0]]),
+                 m_e=np.array([0.5 * KERNEL_VOLUME_CELLS * gp["rho0"] * gp["h"] ** 3]),
+                 kappa_ratio=np.array([0.5]), k_spring=np.array([1.0]))
+    return gp, parts, steps
+
+
+def many_particle_config(n, n_particles, *, kT=1e-3, wave_amp=5e-3, wave_nlambda=1, seed=1,
+                         min_sep=0.0, mass_range=(0.5, 2.0), kappa_range=(0.0, 2.0),
+                         kappa_min=0.04, fixed_contrast=None, k_spring=0.0, precision="fp64",
+                         place_seed=None):
+    """Fluctuating box with many particles.
+
+    Particle mass ratio m_p/(rho0 V) ~ U(mass_range) and kappa_p/kappa_f ~
+    U(kappa_range) clamped below at ``kappa_min`` (a vanishing kappa_p makes
+    the particle sound speed, hence the CFL number, unbounded); or, with
+    ``fixed_contrast=(mass_ratio, kappa_ratio)``, the same contrast for all.
+    """
+    gp = grid_params(n, kT=kT, wave_amp=wave_amp, wave_nlambda=wave_nlambda, seed=seed,
+                     precision=precision)
+    L = np.array([gp["nx"], gp["ny"], gp["nz"]], dtype=np.float64) * gp["h"]
+    rng = np.random.default_rng(seed + 1000)
+    q = place_uniform(n_particles, L, seed if place_seed is None else place_seed, min_sep)
+    vol = KERNEL_VOLUME_CELLS * gp["h"] ** 3
+    if fixed_contrast is None:
+        mass_ratio = rng.uniform(*mass_range, n_particles)
+        kappa = np.maximum(rng.uniform(*kappa_range, n_particles), kappa_min)
+    else:
+        mass_ratio = np.full(n_particles, fixed_contrast[0])
+        kappa = np.full(n_particles, fixed_contrast[1])
+    parts = dict(q=q, m_e=(mass_ratio - 1.0) * gp["rho0"] * vol, kappa_ratio=kappa,
+                 k_spring=np.full(n_particles, float(k_spring)))
+    return gp, parts
+
+
+def large_box_config(n=128, n_particles=10000):
+    """128^3 FP32 box, 1e4 particles (min separation 2h, host RNG seed 3),
+    contrasts of the single-particle case (m_p = 1.5 rho0 V, kappa_p = 0.5
+    kappa_f, spring k_s = 1), kT = 1e-3, two wavelengths along x, A = 1e-3."""
+    return many_particle_config(n, n_particles, kT=1e-3, wave_amp=1e-3, wave_nlambda=2, seed=3,
+                                min_sep=2.0, fixed_contrast=(1.5, 0.5), k_spring=1.0,
+                                precision="fp32", place_seed=3)
+
+
+def blackman_harris(nsteps, skip=0):
+    """Averaging weights: zero for the first ``skip`` steps, then a 4-term
+    Blackman-Harris window normalised to sum 1."""
+    w = np.zeros(nsteps)
+    m = nsteps - skip
+    if m <= 0:
+        return w
+    t = np.arange(m) / max(m - 1, 1)
+    a = (0.35875, 0.48829, 0.14128, 0.01168)
+    win = a[0] - a[1] * np.cos(2 * np.pi * t) + a[2] * np.cos(4 * np.pi * t) - a[3] * np.cos(6 * np.pi * t)
+    w[skip:] = win / win.sum()
+    return w

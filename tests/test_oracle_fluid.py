@@ -1,0 +1,140 @@
+"""Pins of the oracle's fluid solver (Sec. 4.2, App. A.2, Table I)."""
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import curve_fit
+
+from oracle import fluid, ic, theory
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def table1():
+    vals = {}
+    with open(os.path.join(GOLDEN, "table1.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def run_trace(p, nsteps, rho=None, g=None, probe=None):
+    s = ic.Simulation(p, rho, g)
+    out = np.empty(nsteps + 1)
+    probe = probe or (lambda sim: ic.mode_amplitude(p, sim.rho))
+    out[0] = probe(s)
+    for i in range(nsteps):
+        s.step()
+        out[i + 1] = probe(s)
+    return s, out
+
+
+def test_mass_and_momentum_conserved_with_noise():
+    p = ic.GridParams(nx=6, ny=5, nz=7, kT=1e-2, zeta=0.3, seed=4)
+    rng = np.random.default_rng(1)
+    rho = 1.0 + 1e-2 * rng.uniform(-1, 1, p.shape)
+    g = [1e-2 * rng.uniform(-1, 1, p.shape) for _ in range(3)]
+    s = ic.Simulation(p, rho, g)
+    m0, p0 = s.rho.sum(), s.total_momentum()
+    s.run(20)
+    assert s.rho.sum() == pytest.approx(m0, rel=1e-14)
+    assert np.allclose(s.total_momentum(), p0, atol=1e-14)
+    assert np.max(np.abs(s.g[0] - g[0])) > 1e-4          # something happened
+
+
+def test_sound_frequency_matches_table1():
+    """Inviscid standing wave oscillates at Table I's omega = 0.0784137."""
+    t1 = table1()
+    h, n, c = t1["h"], int(t1["cells"]), t1["c_f"]
+    dt = 0.1 * h / c
+    p = ic.GridParams(nx=n, ny=4, nz=4, h=h, c=c, eta=0.0, zeta=0.0, dt=dt, wave_amp=1e-7)
+    period = 2 * np.pi / 0.0784
+    nsteps = int(0.8 * period / dt)
+    _, a = run_trace(p, nsteps)
+    t = dt * np.arange(nsteps + 1)
+    # first zero crossing of A0 cos(omega t): linear interpolation is exact to O(dt^3) there
+    i = np.nonzero(np.sign(a[1:]) != np.sign(a[:-1]))[0]
+    crossings = [t[j] + dt * a[j] / (a[j] - a[j + 1]) for j in i]
+    omega = (np.pi / 2) / crossings[0]
+    assert omega == pytest.approx(t1["omega_fig4"], abs=6e-8)
+    assert omega == pytest.approx(theory.discrete_sound_frequency(c, h, n), rel=1e-6)
+    assert abs(omega - 2 * np.pi * c / (n * h)) > 1e-4      # not the continuum value
+
+
+def test_shear_mode_decays_at_eta_k2():
+    """A transverse mode g_y = B cos(k x) decays at (eta/rho0) k~^2 with k~ = (2/h) sin(kh/2)."""
+    p = ic.GridParams(nx=16, ny=4, nz=4, h=1.0, eta=0.7, zeta=0.4, c=4.0)
+    k = 2 * np.pi / 16
+    x = np.arange(16) * p.h
+    rho = np.full(p.shape, 1.0)
+    g = [np.zeros(p.shape), np.broadcast_to(1e-6 * np.cos(k * x), p.shape).copy(), np.zeros(p.shape)]
+    probe = lambda sim: 2 * np.mean(sim.g[1] * np.cos(k * ic.axis_coordinate(p, 0)))
+    nsteps = 400
+    _, b = run_trace(p, nsteps, rho, g, probe)
+    rate = -np.log(b[-1] / b[0]) / (nsteps * p.dt)
+    kd2 = (2 / p.h * np.sin(k * p.h / 2)) ** 2
+    assert rate == pytest.approx(p.eta / p.rho0 * kd2, rel=1e-5)
+
+
+@pytest.mark.parametrize("eta,zeta", [(0.5, 0.0), (0.2, 0.9)])
+def test_sound_mode_decays_at_gamma_k2(eta, zeta):
+    """A sound mode decays at Gamma k~^2 with Gamma = (4 eta/3 + zeta) / (2 rho0) (Sec. 6)."""
+    p = ic.GridParams(nx=16, ny=4, nz=4, eta=eta, zeta=zeta, wave_amp=1e-7)
+    nsteps = 1200
+    _, a = run_trace(p, nsteps)
+    t = p.dt * np.arange(nsteps + 1)
+    model = lambda t, a0, b0, gam, om: np.exp(-gam * t) * (a0 * np.cos(om * t) + b0 * np.sin(om * t))
+    _, kd, omega, gamma = ic.wave_numbers(p)
+    popt, _ = curve_fit(model, t, a / 1e-7, p0=[1.0, 0.0, gamma * kd ** 2, omega], xtol=1e-14, ftol=1e-14)
+    assert popt[2] == pytest.approx(gamma * kd ** 2, rel=2e-4)
+    assert popt[3] == pytest.approx(np.sqrt(omega ** 2 - (gamma * kd ** 2) ** 2), rel=1e-5)
+
+
+@pytest.mark.parametrize("forcing", ["mode", "plane"])
+def test_driven_mode_holds_amplitude(forcing):
+    """The resonant drive keeps the k mode at the target amplitude A (linear response, Sec. 6)."""
+    A = 1e-6
+    p = ic.GridParams(nx=16, ny=4, nz=4, eta=0.5, zeta=0.5, wave_amp=A, forcing=forcing)
+    _, kd, omega, gamma = ic.wave_numbers(p)
+    period = 2 * np.pi / omega
+    nsteps = int(6 * period / p.dt)
+    _, a = run_trace(p, nsteps)
+    last = a[-int(period / p.dt) - 2:]
+    tol = 2e-3 if forcing == "mode" else 2e-2          # the plane also excites other modes
+    assert np.max(np.abs(last)) == pytest.approx(A, rel=tol)
+
+
+def test_equipartition_and_density_variance():
+    """Thermal fluid: <v^2> = kT / (rho0 h^3) per face, <drho^2> = rho0 kT / (c^2 h^3).
+
+    The initial sample is the Gibbs state; after the short-wavelength modes have
+    relaxed several times, a noise normalisation off by a factor would show.
+    """
+    p = ic.GridParams(nx=8, ny=8, nz=8, h=1.0, kT=1e-4, eta=0.5, zeta=0.5, seed=21)
+    rho, g = ic.thermal_state(p, seed=99)
+    s = ic.Simulation(p, rho, g)
+    s.run(100)
+    v2, r2 = [], []
+    for i in range(500):
+        s.step()
+        if i % 2 == 0:
+            v = s.velocities()
+            v2.append(np.mean([np.mean(v[a] ** 2) for a in range(3)]))
+            r2.append(np.mean((s.rho - p.rho0) ** 2))
+    expect_v = p.kT / (p.rho0 * p.h ** 3)
+    expect_r = p.rho0 * p.kT / (p.c ** 2 * p.h ** 3)
+    # <v^2> per face, and the total of N^3 - 1 nonzero density modes
+    assert np.mean(v2) == pytest.approx(expect_v * (1 - 1 / 512), rel=0.04)
+    assert np.mean(r2) == pytest.approx(expect_r * (1 - 1 / 512), rel=0.04)
+
+
+def test_thermal_state_statistics():
+    p = ic.GridParams(nx=16, ny=16, nz=16, kT=2e-3, c=3.0)
+    rho, g = ic.thermal_state(p, seed=5)
+    assert abs(np.mean(rho) - p.rho0) < 1e-15
+    assert np.mean((rho - p.rho0) ** 2) == pytest.approx(p.rho0 * p.kT / p.c ** 2, rel=0.05)
+    for a in range(3):
+        assert abs(np.mean(g[a])) < 1e-16
+        assert np.mean(g[a] ** 2) == pytest.approx(p.rho0 * p.kT, rel=0.05)
