@@ -1,0 +1,319 @@
+"""Throughput of the IC time step on GB300: cell-updates/s and particle-steps/s.
+
+Workload (default): 128^3 periodic staggered grid, FP32 state with FP64
+accumulators, kT = 1e-3 (Philox stochastic stress), a standing wave of two
+wavelengths along x held by the mode drive, 10^4 particles placed uniformly
+at random with minimum separation 2h (m_p = 1.5 rho0 V, kappa_p = 0.5
+kappa_f, tether k_s = 1), thermal (Gibbs) initial state.
+
+One step = the whole IC step (App. A.2 substeps 1-7: particle half step,
+three RK3 fluid stages with particle-pressure corrections, impulse, spreading,
+final position, accumulators), launched as one CUDA graph.  Inputs are resident
+in HBM.  Between timed steps the L2 is flushed by writing a 512 MB buffer, and
+each step is timed alone with CUDA events on the library's stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs its own box (box id = rank): weak scaling, no
+collective in the data path; rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and particle-steps/s (128^3, 1e4 particles); % of HBM roofline"
+WORKLOAD = ("128^3 staggered grid FP32 state + FP64 accumulators, 1e4 particles (min sep 2h), kT=1e-3, "
+            "2-wavelength standing wave along x, thermal start")
+# algorithmic bytes of the stage-wise SSP-RK3 sweep per cell and step (FP32):
+# stage 1 reads U_s (4 words) and writes 4; stages 2-3 read U_s and U^n (8) and write 4
+ALG_BYTES_PER_CELL_STEP = {"fp32": 128, "fp64": 256}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_box(gp, parts, seed_thermal):
+    from paper_1307_0702_gb300 import Grid, workloads as W
+
+    grid = Grid(gp)
+    rho, g = W.standing_wave_fields(gp)
+    grid.set_state(rho, g)
+    if gp["kT"] > 0:
+        grid.init_thermal(seed_thermal, add=True)
+    grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])
+    return grid
+
+
+def cpu_baseline(seconds_budget=20.0):
+    """The oracle as it stands on the host: a 64^3 sub-box with the same particle
+    density (1250 particles) and fluid parameters; cell-updates/s is intensive."""
+    from oracle import ic as oic
+    from paper_1307_0702_gb300 import workloads as W
+
+    gp, parts = W.many_particle_config(64, 1250, kT=1e-3, wave_amp=1e-3, wave_nlambda=1, seed=3, min_sep=2.0,
+                                       fixed_contrast=(1.5, 0.5), k_spring=1.0)
+    p = oic.GridParams(**{k: v for k, v in gp.items() if k in oic.GridParams.__dataclass_fields__})
+    rho, g = W.standing_wave_fields(gp)
+    sim = oic.Simulation(p, rho, g)
+    sim.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])
+    sim.step()   # warm-up (page-in, caches)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step()
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or steps >= 50:
+            break
+    cells = 64 ** 3
+    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"64^3 sub-box, 1250 particles, kT=1e-3, {steps} oracle steps in {el:.1f} s (numpy FP64, 1 thread)",
+            "particle_steps_per_s": 1250 * steps / el}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    res = []
+    for _ in range(args.warmup):
+        cpu_baseline(seconds_budget=0.0)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        b = cpu_baseline(seconds_budget=0.0)
+        vals.append(b["value"])
+    el = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "64^3 sub-box with 1250 particles per step (same density)"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v,
+                             "sample": "each step: one oracle step of a 64^3 sub-box, 1250 particles"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--particles", type=int, default=10000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1307_0702_gb300 import workloads as W
+
+    gp, parts = W.large_box_config(args.n, args.particles)
+    gp["precision"] = args.precision
+    gp["box"] = rank
+    grid = setup_box(gp, parts, seed_thermal=1000 + rank)
+    cells = gp["nx"] * gp["ny"] * gp["nz"]
+    npart = parts["q"].shape[0]
+    stream = grid.stream
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (captures the graphs)
+    grid.step(args.warmup)
+    grid.sync()
+
+    # timed region: K steps, each bracketed by events on the library's stream, L2 flushed in between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+        grid.step(1)
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    grid.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = float(np.sum(step_ms)) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * cells * args.steps / t_max
+    pvalue = world * npart * args.steps / t_max
+
+    # kernel timing pass: same steps with events around every kernel (graphs off)
+    grid.profile(True)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        grid.step(1)
+    prof = grid.profile_read()
+    grid.profile(False)
+    fluid_ms, fluid_launches = prof["fluid"]
+    part_ms, part_launches = prof["particles"]
+    end_ms, end_launches = prof["end"]
+    launches_per_step = (fluid_launches + part_launches + end_launches) / args.steps
+    peak, peak_kind = load_peaks()
+    alg_bytes = ALG_BYTES_PER_CELL_STEP[args.precision] * cells       # per step = per 3 stage launches
+    stage_ms_per_step = fluid_ms / args.steps
+    achieved = alg_bytes / (stage_ms_per_step * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tj = json.load(f)
+        if tj.get("precision") == args.precision and tj.get("cells") == cells:
+            traffic = tj.get("bytes_per_launch")
+
+    # end-to-end through the public API with host buffers: one step per call,
+    # weight uploaded from pinned memory, particle forces read back every step
+    e2e = None
+    if not args.no_e2e:
+        pinned_w = torch.ones(1, dtype=torch.float64).pin_memory().numpy()
+        outs = tuple(torch.empty((npart, 3), dtype=torch.float64).pin_memory().numpy() for _ in range(3))
+        grid.step(1, pinned_w)
+        grid.forces(outs)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            grid.step(1, pinned_w)
+            grid.forces(outs)
+        barrier()
+        el = time.perf_counter() - t0
+        tt = torch.tensor([el], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+        e2e = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": 8 + 8, "d2h_bytes_per_step": 3 * npart * 3 * 8,
+               "particle_steps_per_s": world * npart * args.steps / el}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "particles": npart, "precision": args.precision,
+                       "parallelism": f"{world} independent boxes (one per GPU)",
+                       "l2": "flushed between timed steps (512 MB write, outside the step events)",
+                       "particle_steps_per_s": pvalue},
+            "particle_steps_per_s": pvalue,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_rk3_stage (3 launches per step)",
+                         "alg_bytes_per_step": alg_bytes, "stage_ms_per_step": stage_ms_per_step,
+                         "particle_ms_per_step": part_ms / args.steps, "end_ms_per_step": end_ms / args.steps},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": base,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * ic.h -- C ABI of libic: one explicit time step of the inertial-coupling
+ * (IC) method with particle compressibility (Balboa Usabiaga and
+ * Delgado-Buscalioni, "A minimal model for acoustic forces on Brownian
+ * particles", arXiv 1307.0702), on a single GPU.
+ *
+ * The step (App. A.2, substeps 1-7) couples compressible Landau-Lifshitz
+ * fluctuating hydrodynamics on a periodic staggered grid (Sec. 4.2, Eqs.
+ * (eq:consvDens), (eq:consvMom), (totp)), advanced by SSP-RK3 with the noise
+ * combinations W_1..W_3 of App. A.2, to point particles through the 3-point
+ * Peskin kernel (App. A.1): interpolation J (Eq. (Jdis)), spreading S (Eq.
+ * (Sdis)), the no-slip impulse exchange (Eq. (eq:noSlip), substeps 4-6) and
+ * the particle pressure pi = p(rho) + S Omega, Omega = epsilon V (J rho - rho0)
+ * (Eqs. (eq:pressure), (omega)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an ic_status; on failure ic_last_error(ctx) holds a
+ *    one-line message.  A NULL ctx or a NULL required pointer gives
+ *    IC_ERR_ARG.
+ *  - Grid arrays are nx*ny*nz values indexed [z][y][x] (x fastest).  The
+ *    alpha component of a vector field lives on the alpha-face r_i + h/2 e_alpha
+ *    and is stored at the index of cell i.  Particle arrays are n*3 values
+ *    (x, y, z per particle).
+ *  - Host pointers passed in are only read (or written) during the call; the
+ *    caller keeps ownership.  All device memory belongs to the context and is
+ *    freed by ic_destroy.  It is obtained from params->alloc when given (e.g.
+ *    PyTorch's caching allocator), else from cudaMalloc.
+ *  - Work is ordered on params->stream (NULL: the library creates its own).
+ *    ic_step only enqueues work; ic_sync, ic_forces, ic_time_average,
+ *    ic_stats, ic_get_state and ic_checkpoint synchronise that stream and
+ *    report device-side errors (non-finite state, neighbour-list overflow).
+ *  - A context is not thread-safe.  Different contexts are independent.
+ */
+#ifndef IC_H
+#define IC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ic_ctx ic_ctx;
+
+typedef enum {
+  IC_OK = 0,
+  IC_ERR_ARG = -1,        /* invalid argument or parameter                  */
+  IC_ERR_CUDA = -2,       /* a CUDA runtime call or kernel launch failed    */
+  IC_ERR_OOM = -3,        /* device allocation failed                       */
+  IC_ERR_NONFINITE = -4,  /* the state became NaN/Inf (e.g. CFL violated)   */
+  IC_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up             */
+  IC_ERR_STATE = -6,      /* call not valid in the current state            */
+  IC_ERR_CAPACITY = -7    /* a fixed-size device table overflowed           */
+} ic_status;
+
+enum { IC_FP64 = 0, IC_FP32 = 1 };
+/* Standing-wave drive.  MODE: body pressure P cos(k x) sin(omega t) with
+ * P = 2 Gamma omega A that holds the k mode at density amplitude A.  PLANE:
+ * the paper's drive, Eq. (pext): Delta p0 sin(omega t) on one grid plane with
+ * Delta p0 = A N Gamma omega.  omega = (2c/h) sin(kh/2), Gamma = (4 eta/3 +
+ * zeta)/(2 rho0), k = 2 pi nlambda / L along wave_axis; both drives use
+ * sin(omega t + phi) with phi = wave_phase. */
+enum { IC_FORCE_NONE = 0, IC_FORCE_MODE = 1, IC_FORCE_PLANE = 2 };
+
+typedef struct {
+  int nx, ny, nz;       /* cells per direction, each >= 6                      */
+  double h;             /* grid spacing                                        */
+  double rho0;          /* equilibrium density                                 */
+  double c;             /* fluid speed of sound c_f, p = p0 + c^2 rho          */
+  double eta, zeta;     /* shear and bulk viscosity                            */
+  double kT;            /* temperature (0: deterministic, no stochastic stress) */
+  double dt;            /* time step                                           */
+  uint64_t seed;        /* Philox key of the stochastic stress                 */
+  uint32_t box;         /* Philox counter word 3: independent replicas          */
+  int precision;        /* IC_FP64 or IC_FP32 (accumulators are FP64 in both)  */
+  int forcing;          /* IC_FORCE_*                                          */
+  int wave_axis;        /* 0 = x, 1 = y, 2 = z                                 */
+  double wave_amp;      /* density amplitude A of the driven mode              */
+  int wave_nlambda;     /* wavelengths per box along wave_axis                 */
+  int plane_index;      /* driven plane for IC_FORCE_PLANE                     */
+  double wave_phase;    /* drive phase phi: sin(omega t + phi)                 */
+  void *stream;         /* cudaStream_t or NULL                                */
+  void *(*alloc)(size_t bytes, void *alloc_ctx);          /* NULL: cudaMalloc  */
+  void (*free)(void *ptr, size_t bytes, void *alloc_ctx); /* NULL: cudaFree    */
+  void *alloc_ctx;
+} ic_grid_params;
+
+/* Zero-copy device views of the current state, valid until the next call
+ * that steps, restores or adds particles.  Fields hold delta rho = rho - rho0
+ * (not rho) and g; element type is double (IC_FP64) or float (IC_FP32). */
+typedef struct {
+  void *drho, *gx, *gy, *gz;
+  int precision;
+  int n_particles;
+  double *q;            /* n*3 device positions (FP64 in both precisions) */
+} ic_views;
+
+/* Creates a context: validates params (IC_ERR_ARG), allocates the three
+ * RK3 state buffers and sets rho = rho0, g = 0. */
+ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out);
+
+/* Uploads the fluid state from host arrays (density rho, not delta rho, and
+ * face momenta g), each nx*ny*nz doubles.  Any of gx, gy, gz may be NULL (zero). */
+ic_status ic_set_state(ic_ctx *ctx, const double *rho, const double *gx, const double *gy,
+                       const double *gz);
+
+/* Downloads the fluid state to host arrays of nx*ny*nz doubles (NULL skips). */
+ic_status ic_get_state(ic_ctx *ctx, double *rho, double *gx, double *gy, double *gz);
+
+/* Thermal initial state: draws delta rho ~ N(0, rho0 kT/(c^2 h^3)) and
+ * g ~ N(0, rho0 kT/h^3) (the discrete Gibbs measure of the linearised fluid,
+ * whose velocity variance kT/(rho0 h^3) is the equipartition of Sec. 4.5)
+ * from Philox purpose 1, removes their means, and adds them to the current
+ * state (add != 0) or replaces it (add == 0).  Call before ic_add_particles,
+ * which sets particle velocities from the fluid. */
+ic_status ic_init_thermal(ic_ctx *ctx, uint64_t seed, int add);
+
+/* Appends n particles.  q: n*3 positions (wrapped into the box); u: n*3
+ * velocities or NULL for u = J v at q (no-slip, Eq. (noslip)); m_e: n excess
+ * masses (m_e > -m_f; Eq. (eq:particleMass)); kappa_ratio: n values of
+ * kappa_p/kappa_f > 0, giving epsilon_pf = c^2 (kappa_f/kappa_p - 1) (Eqs.
+ * (part_svel), (ke)); k_spring: n spring constants of a tether
+ * F = -k_s (q - q_eq) with q_eq the initial position, or NULL (free).
+ * *first_id (if not NULL) receives the index of the first new particle. */
+ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u,
+                           const double *m_e, const double *kappa_ratio,
+                           const double *k_spring, int *first_id);
+
+/* Advances nsteps time steps (App. A.2 substeps 1-7).  w: nsteps host
+ * weights of the time averages (Sigma w F, Sigma w lambda, Sigma w A^2), or
+ * NULL for weight 0.  Enqueues work only (a CUDA graph per buffer parity). */
+ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w);
+
+/* Latest step's particle data to host n*3 arrays (NULL skips): lambda, the
+ * fluid force on each particle (substep 4: dg = dt (lambda + F)); u; q. */
+ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q);
+
+/* Weighted time averages since the last reset: spring force <F>_w and fluid
+ * force <lambda>_w (n*3 each, NULL skips) and <A^2>_w of the driven-mode
+ * density amplitude A(t) = (2/N) sum (rho - rho0) cos(k x).  The radiation
+ * force of Sec. 6 is -<F>_w.  reset != 0 zeroes the sums after reading.
+ * IC_ERR_STATE if the weights summed to 0. */
+ic_status ic_time_average(ic_ctx *ctx, double *f_spring, double *lambda, double *a2, int reset);
+
+/* Total momentum h^3 sum g + sum m_e u (3 doubles, Eq. (eq:totmom)), current
+ * driven-mode amplitude A, and the step counter (each may be NULL). */
+ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step);
+
+/* Synchronises the stream and reports device-side errors raised since the
+ * last check (IC_ERR_NONFINITE, IC_ERR_CAPACITY). */
+ic_status ic_sync(ic_ctx *ctx);
+
+/* Serialises the complete state (fields, particles, accumulators, step
+ * counter).  buf == NULL: *bytes receives the size needed.  Resuming from a
+ * checkpoint reproduces the uninterrupted run bit for bit. */
+ic_status ic_checkpoint(ic_ctx *ctx, void *buf, size_t *bytes);
+/* Restores a checkpoint written by a context of the same grid and precision. */
+ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes);
+
+ic_status ic_device_views(ic_ctx *ctx, ic_views *out);
+
+/* Kernel timing for measurement.  While enabled, ic_step launches without
+ * CUDA graphs and brackets every kernel with CUDA events on the context's
+ * stream.  ic_profile_read synchronises and returns, per kernel class
+ * (0: fluid RK3 stages, 1: particle kernels, 2: end-of-step reduction), the
+ * summed device milliseconds (ms[3]) and launch counts (launches[3]) since
+ * the last reset. */
+ic_status ic_profile(ic_ctx *ctx, int enable);
+ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+const char *ic_last_error(const ic_ctx *ctx);
+void ic_destroy(ic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IC_H */

@@ -60,10 +60,12 @@ def noise_amplitudes(p):
     return np.sqrt(2.0 * p.eta * p.kT / vol_dt), np.sqrt(p.zeta * p.kT / (3.0 * vol_dt))
 
 
-def rates(rho, g, p, pressure_extra=None, normals=None, face_force=None):
+def rates(drho, g, p, pressure_extra=None, normals=None, face_force=None):
     """Time derivatives (d rho/dt, [d g^x/dt, d g^y/dt, d g^z/dt]).
 
-    rho            : total density at centres
+    drho           : density excess rho - rho0 at centres (the constant p0 + c^2 rho0
+                     of the equation of state p = p0 + c^2 rho, Sec. 3, has no gradient,
+                     so the state is carried as rho - rho0 to avoid cancellation)
     g              : list of the three face momentum arrays
     pressure_extra : pressure added to c^2 rho at centres (particle term S Omega
                      plus the external drive), or None
@@ -73,14 +75,14 @@ def rates(rho, g, p, pressure_extra=None, normals=None, face_force=None):
     """
     h = p.h
     # mass, Eq. (eq:consvDens)
-    drho = -sum(g[a] - dn(g[a], a) for a in range(3)) / h
+    drho_dt = -sum(g[a] - dn(g[a], a) for a in range(3)) / h
 
-    rho_face = [0.5 * (rho + up(rho, a)) for a in range(3)]
+    rho_face = [p.rho0 + 0.5 * (drho + up(drho, a)) for a in range(3)]
     v = [g[a] / rho_face[a] for a in range(3)]
     dv = [(v[a] - dn(v[a], a)) / h for a in range(3)]
     div_v = dv[0] + dv[1] + dv[2]
 
-    pi = p.c ** 2 * rho
+    pi = p.c ** 2 * drho
     if pressure_extra is not None:
         pi = pi + pressure_extra
 
@@ -119,7 +121,7 @@ def rates(rho, g, p, pressure_extra=None, normals=None, face_force=None):
         if face_force is not None:
             rate = rate + face_force[a]
         dg.append(rate)
-    return drho, dg
+    return drho_dt, dg
 
 
 # SSP-RK3 stage weights (App. A.2): U_{s+1} = a_s U^n + b_s (U_s + dU(U_s))

@@ -25,7 +25,7 @@ project's design notes):
   and all spreads are added (the paper only says the generalisation to N
   particles is straightforward, Sec. 4.2).
 * The standing wave is held by a body pressure (``forcing='mode'``,
-  p_ext = P cos(k x) sin(omega t) with P = 2 Gamma omega A, Gamma = (4 eta/3 +
+  p_ext = P cos(k x) sin(omega t + phi) with P = 2 Gamma omega A, Gamma = (4 eta/3 +
   zeta)/(2 rho0), omega = (2c/h) sin(kh/2)), which keeps the mode at density
   amplitude A from the exact initial eigenmode rho0 + A cos(kx).  The paper's
   own drive (Eq. (pext)), a pressure on one grid plane, is ``forcing='plane'``
@@ -60,6 +60,7 @@ class GridParams:
     wave_amp: float = 0.0          # target density amplitude A of the driven mode
     wave_nlambda: int = 1          # wavelengths per box along wave_axis
     plane_index: int = 0           # grid plane driven when forcing == 'plane'
+    wave_phase: float = 0.0        # drive phase phi: sin(omega t + phi)
     momentum_form: str = "g"       # 'g' (default) or 'v' (paper's literal form)
 
     @property
@@ -104,19 +105,19 @@ def external_pressure(p, t):
     k, kd, omega, gamma = wave_numbers(p)
     if p.forcing == "mode":
         amp = 2.0 * gamma * omega * p.wave_amp
-        return amp * np.cos(k * axis_coordinate(p, p.wave_axis)) * np.sin(omega * t)
+        return amp * np.cos(k * axis_coordinate(p, p.wave_axis)) * np.sin(omega * t + p.wave_phase)
     if p.forcing == "plane":
         n_ax = (p.nx, p.ny, p.nz)[p.wave_axis]
         dp0 = p.wave_amp * n_ax * gamma * omega
         idx = np.rint(axis_coordinate(p, p.wave_axis) / p.h).astype(np.int64)
-        return np.where(idx == p.plane_index, dp0 * np.sin(omega * t), 0.0)
+        return np.where(idx == p.plane_index, dp0 * np.sin(omega * t + p.wave_phase), 0.0)
     raise ValueError(p.forcing)
 
 
-def mode_amplitude(p, rho):
-    """A(t) = (2/N) sum_i (rho_i - rho0) cos(k x_i) along the wave axis."""
+def mode_amplitude(p, drho):
+    """A(t) = (2/N) sum_i (rho_i - rho0) cos(k x_i) along the wave axis (drho = rho - rho0)."""
     k = wave_numbers(p)[0]
-    return 2.0 * np.mean((rho - p.rho0) * np.cos(k * axis_coordinate(p, p.wave_axis)))
+    return 2.0 * np.mean(drho * np.cos(k * axis_coordinate(p, p.wave_axis)))
 
 
 def standing_wave(p):
@@ -126,8 +127,8 @@ def standing_wave(p):
     return np.array(rho), [np.zeros(p.shape) for _ in range(3)]
 
 
-def thermal_state(p, seed):
-    """Sample of the discrete Gibbs state of the linearised fluid.
+def thermal_fluctuation(p, seed):
+    """(delta rho, g) of a sample of the discrete Gibbs state of the linearised fluid.
 
     delta rho ~ N(0, rho0 kT / (c^2 h^3)), g^alpha ~ N(0, rho0 kT / h^3) from
     Philox purpose 1, with the means removed so that total mass and momentum
@@ -143,12 +144,21 @@ def thermal_state(p, seed):
         ga = np.sqrt(p.rho0 * p.kT / vol) * z[1 + a]
         ga -= ga.mean()
         g.append(ga.reshape(p.shape))
-    return p.rho0 + drho.reshape(p.shape), g
+    return drho.reshape(p.shape), g
 
 
-def particle_pressure(centre, rho, eps, p):
-    """S Omega at the cell centres, Omega = epsilon V (J rho - rho0) (Eqs. (eq:pressure), (omega))."""
-    omega = eps * peskin.kernel_volume(p.h) * (centre.interp(rho) - p.rho0)
+def thermal_state(p, seed):
+    """The Gibbs sample as (rho, g)."""
+    drho, g = thermal_fluctuation(p, seed)
+    return p.rho0 + drho, g
+
+
+def particle_pressure(centre, drho, eps, p):
+    """S Omega at the cell centres, Omega = epsilon V (J rho - rho0) (Eqs. (eq:pressure), (omega)).
+
+    drho = rho - rho0; J rho - rho0 = J drho because the weights sum to 1 (Eq. (k1)).
+    """
+    omega = eps * peskin.kernel_volume(p.h) * centre.interp(drho)
     return centre.spread(omega, p.shape, p.h)
 
 
@@ -175,14 +185,19 @@ class Accumulators:
 
 
 class Simulation:
-    """State (rho, g, particles) and the IC step."""
+    """State (rho, g, particles) and the IC step.
 
-    def __init__(self, p: GridParams, rho=None, g=None):
+    The density is carried as drho = rho - rho0 (``rho`` is a derived view).
+    """
+
+    def __init__(self, p: GridParams, rho=None, g=None, drho=None):
         self.p = p
-        if rho is None:
-            rho, g = standing_wave(p) if p.wave_amp != 0.0 else (
-                np.full(p.shape, p.rho0), [np.zeros(p.shape) for _ in range(3)])
-        self.rho = np.array(rho, dtype=np.float64)
+        if drho is None:
+            if rho is None:
+                rho, g = standing_wave(p) if p.wave_amp != 0.0 else (
+                    np.full(p.shape, p.rho0), [np.zeros(p.shape) for _ in range(3)])
+            drho = np.asarray(rho, dtype=np.float64) - p.rho0
+        self.drho = np.array(drho, dtype=np.float64)
         self.g = [np.array(a, dtype=np.float64) for a in g]
         self.parts = Particles(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0), np.zeros(0),
                                np.zeros(0), np.zeros((0, 3)))
@@ -190,11 +205,16 @@ class Simulation:
         self.acc = Accumulators(sf=np.zeros((0, 3)), sl=np.zeros((0, 3)))
         self.last = {}
 
+    @property
+    def rho(self):
+        return self.p.rho0 + self.drho
+
     # ------------------------------------------------------------------ setup
-    def velocities(self, rho=None, g=None):
-        rho = self.rho if rho is None else rho
+    def velocities(self, drho=None, g=None):
+        """v^a = g^a / rho^a with the face density rho0 + (drho_i + drho_{i+a}) / 2."""
+        drho = self.drho if drho is None else drho
         g = self.g if g is None else g
-        return [g[a] / (0.5 * (rho + fluid.up(rho, a))) for a in range(3)]
+        return [g[a] / (self.p.rho0 + 0.5 * (drho + fluid.up(drho, a))) for a in range(3)]
 
     def add_particles(self, q, m_e, kappa_ratio, k_spring=None, u=None):
         """Append particles; u defaults to J v at q (no-slip, Eq. (noslip))."""
@@ -233,7 +253,7 @@ class Simulation:
         h, dt, shape = p.h, p.dt, p.shape
         vol = peskin.kernel_volume(h)
         t_n = self.step_index * dt
-        rho_n, g_n = self.rho, self.g
+        rho_n, g_n = self.drho, self.g
         v_n = self.velocities(rho_n, g_n)
         npart = pt.n
 
@@ -274,7 +294,7 @@ class Simulation:
             # substep 4: impulse from the unperturbed velocity
             v_tilde = self.velocities(rho_new, g_tilde)
             jv_tilde = np.stack([faces[a].interp(v_tilde[a]) for a in range(3)], axis=1)
-            m_f = vol * centre.interp(rho_new)
+            m_f = vol * (p.rho0 + centre.interp(rho_new))
             me = pt.m_e[:, None]
             mf = m_f[:, None]
             dgp = me * mf / (me + mf) * (jv_tilde - pt.u)
@@ -284,7 +304,7 @@ class Simulation:
             if p.momentum_form == "g":
                 g_new = [g_tilde[a] - faces[a].spread(dgp[:, a], shape, h) for a in range(3)]
             else:
-                rf = [0.5 * (rho_new + fluid.up(rho_new, a)) for a in range(3)]
+                rf = [p.rho0 + 0.5 * (rho_new + fluid.up(rho_new, a)) for a in range(3)]
                 g_new = [rf[a] * (v_tilde[a] - faces[a].spread(vol / m_f * dgp[:, a], shape, h))
                          for a in range(3)]
             v_new = self.velocities(rho_new, g_new)
@@ -300,11 +320,11 @@ class Simulation:
             lam = np.zeros((0, 3))
             self.last = dict(g_tilde=g_tilde)
 
-        self.rho, self.g = rho_new, g_new
+        self.drho, self.g = rho_new, g_new
         self.step_index += 1
         if weight != 0.0:
             self.acc.sw += weight
-            self.acc.sa2 += weight * mode_amplitude(p, self.rho) ** 2
+            self.acc.sa2 += weight * mode_amplitude(p, self.drho) ** 2
             self.acc.sf += weight * force
             self.acc.sl += weight * lam
         self.lam = lam

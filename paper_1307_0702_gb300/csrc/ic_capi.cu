@@ -1,0 +1,670 @@
+// C ABI of libic (include/ic.h): context lifetime, host <-> device transfers,
+// and the step driver that chains the fluid and particle kernels of one IC
+// time step (App. A.2 substeps 1-7) on one stream, captured once per buffer
+// parity into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "ic_internal.hpp"
+
+namespace ic {
+
+void *dev_alloc(ic_ctx *ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (ctx->n_allocs >= 64) return nullptr;
+  void *p = nullptr;
+  if (ctx->p.alloc) {
+    p = ctx->p.alloc(bytes, ctx->p.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    ctx->allocs[ctx->n_allocs] = p;
+    ctx->alloc_bytes[ctx->n_allocs] = bytes;
+    ++ctx->n_allocs;
+  }
+  return p;
+}
+
+void dev_free(ic_ctx *ctx, void *p) {
+  if (!p) return;
+  for (int i = 0; i < ctx->n_allocs; ++i) {
+    if (ctx->allocs[i] == p) {
+      if (ctx->p.free)
+        ctx->p.free(p, ctx->alloc_bytes[i], ctx->p.alloc_ctx);
+      else
+        cudaFree(p);
+      ctx->allocs[i] = ctx->allocs[ctx->n_allocs - 1];
+      ctx->alloc_bytes[i] = ctx->alloc_bytes[ctx->n_allocs - 1];
+      --ctx->n_allocs;
+      return;
+    }
+  }
+}
+
+}  // namespace ic
+
+namespace {
+
+using ic::dev_alloc;
+using ic::dev_free;
+
+ic_status fail(ic_ctx *ctx, ic_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return st;
+}
+
+ic_status cuda_fail(ic_ctx *ctx, cudaError_t e, const char *where) {
+  return fail(ctx, IC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define IC_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+void invalidate_graphs(ic_ctx *ctx) {
+  for (int i = 0; i < 2; ++i)
+    if (ctx->graph[i]) {
+      cudaGraphExecDestroy(ctx->graph[i]);
+      ctx->graph[i] = nullptr;
+    }
+}
+
+cudaEvent_t pooled_event(ic_ctx *ctx) {
+  if (ctx->event_next == ctx->event_pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    ctx->event_pool.push_back(ev);
+  }
+  return ctx->event_pool[ctx->event_next++];
+}
+
+// Launch `fn` and, while profiling, bracket it with events of class `cls`.
+template <typename F>
+cudaError_t timed_launch(ic_ctx *ctx, int cls, F &&fn) {
+  if (!ctx->profiling) return fn();
+  cudaEvent_t a = pooled_event(ctx), b = pooled_event(ctx);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, ctx->stream);
+  const cudaError_t e = fn();
+  cudaEventRecord(b, ctx->stream);
+  ctx->timed.push_back({a, b, cls});
+  return e;
+}
+
+// Enqueue one full time step with U^n in buffer `cur`; U^{n+1} lands in 1 - cur.
+cudaError_t enqueue_step(ic_ctx *ctx, int cur) {
+  void *const *U0 = ctx->U[cur];
+  void *const *U1 = ctx->U[1 - cur];
+  void *const *U2 = ctx->U[2];
+  const bool parts = ctx->ps.n > 0;
+  cudaError_t e;
+  auto fluid = [&](int stage, void *const *s, void *const *n, void *const *o) {
+    return timed_launch(ctx, 0, [&] { return ic::launch_stage(ctx, stage, s, n, o); });
+  };
+  auto part = [&](ic::ParticlePhase ph, int stage, void *const *tgt) {
+    return timed_launch(ctx, 1, [&] { return ic::launch_particles(ctx, ph, stage, U0, tgt); });
+  };
+#define IC_TRY(x)                           \
+  do {                                      \
+    if ((e = (x)) != cudaSuccess) return e; \
+  } while (0)
+  if (parts) IC_TRY(part(ic::kHalfStep, 0, U0));
+  IC_TRY(fluid(0, U0, U0, U1));
+  if (parts) IC_TRY(part(ic::kStageCorrection, 0, U1));
+  IC_TRY(fluid(1, U1, U0, U2));
+  if (parts) IC_TRY(part(ic::kStageCorrection, 1, U2));
+  IC_TRY(fluid(2, U2, U0, U1));
+  if (parts) {
+    IC_TRY(part(ic::kStageCorrection, 2, U1));
+    IC_TRY(part(ic::kImpulse, 0, U1));
+    IC_TRY(part(ic::kSpread, 0, U1));
+    IC_TRY(part(ic::kFinal, 0, U1));
+  }
+  IC_TRY(timed_launch(ctx, 2, [&] { return ic::launch_end_of_step(ctx); }));
+#undef IC_TRY
+  return cudaSuccess;
+}
+
+bool graphs_enabled() {
+  const char *v = std::getenv("IC_NO_GRAPH");
+  return !(v && v[0] == '1');
+}
+
+template <typename real>
+void to_real(const double *src, double offset, std::vector<unsigned char> &dst, size_t n) {
+  dst.resize(n * sizeof(real));
+  real *d = reinterpret_cast<real *>(dst.data());
+  for (size_t i = 0; i < n; ++i) d[i] = real(src[i] - offset);
+}
+
+template <typename real>
+void from_real(const unsigned char *src, double offset, double *dst, size_t n) {
+  const real *s = reinterpret_cast<const real *>(src);
+  for (size_t i = 0; i < n; ++i) dst[i] = double(s[i]) + offset;
+}
+
+ic_status upload_real(ic_ctx *ctx, void *dev, const double *host, double offset, size_t n) {
+  std::vector<unsigned char> tmp;
+  if (ctx->p.precision == IC_FP32)
+    to_real<float>(host, offset, tmp, n);
+  else
+    to_real<double>(host, offset, tmp, n);
+  IC_CUDA(ctx, cudaMemcpyAsync(dev, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, ctx->stream));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return IC_OK;
+}
+
+ic_status download_real(ic_ctx *ctx, double *host, const void *dev, double offset, size_t n) {
+  std::vector<unsigned char> tmp(n * ctx->real_size);
+  IC_CUDA(ctx, cudaMemcpyAsync(tmp.data(), dev, tmp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->p.precision == IC_FP32)
+    from_real<float>(tmp.data(), offset, host, n);
+  else
+    from_real<double>(tmp.data(), offset, host, n);
+  return IC_OK;
+}
+
+ic_status check_device_status(ic_ctx *ctx) {
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int st = 0;
+  IC_CUDA(ctx, cudaMemcpy(&st, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st == 0) return IC_OK;
+  IC_CUDA(ctx, cudaMemset(ctx->d.status, 0, sizeof(int)));
+  if (st & ic::kStatusNonfinite)
+    return fail(ctx, IC_ERR_NONFINITE, "state became non-finite (check the CFL numbers c dt/h and c_p dt/h)");
+  if (st & ic::kStatusNbrOverflow)
+    return fail(ctx, IC_ERR_CAPACITY, "more than %d particles within the neighbour cutoff of one particle",
+                ic::kMaxNeighbours);
+  return fail(ctx, IC_ERR_STATE, "a particle moved more than half the neighbour skin within one step");
+}
+
+// Particle arrays: (pointer slot, bytes per particle)
+struct PArray {
+  void **slot;
+  size_t per;
+};
+
+std::vector<PArray> particle_arrays(ic_ctx *ctx) {
+  ic::ParticleStore &s = ctx->ps;
+  const size_t r = ctx->real_size;
+  return {{(void **)&s.q, 24},       {(void **)&s.q_eq, 24},     {(void **)&s.q_build, 24},
+          {(void **)&s.q_half, 24},  {(void **)&s.acc, 48},      {&s.u, 3 * r},
+          {&s.m_e, r},               {&s.eps, r},                {&s.k_s, r},
+          {&s.w, 18 * r},            {&s.jv_n, 3 * r},           {&s.omega, 2 * r},
+          {&s.force, 3 * r},         {&s.dg, 3 * r},             {&s.lam, 3 * r},
+          {(void **)&s.base, 6 * sizeof(int)},
+          {(void **)&s.nbr, ic::kMaxNeighbours * sizeof(int)},
+          {(void **)&s.nnbr, sizeof(int)}};
+}
+
+ic_status grow_particles(ic_ctx *ctx, int need) {
+  ic::ParticleStore &s = ctx->ps;
+  if (need <= s.cap) return IC_OK;
+  const int cap = std::max(need, std::max(16, 2 * s.cap));
+  for (PArray a : particle_arrays(ctx)) {
+    void *fresh = dev_alloc(ctx, a.per * size_t(cap));
+    if (!fresh) return fail(ctx, IC_ERR_OOM, "particle buffer allocation of %zu bytes failed", a.per * cap);
+    IC_CUDA(ctx, cudaMemsetAsync(fresh, 0, a.per * size_t(cap), ctx->stream));
+    if (*a.slot) {
+      if (s.n > 0)
+        IC_CUDA(ctx, cudaMemcpyAsync(fresh, *a.slot, a.per * size_t(s.n), cudaMemcpyDeviceToDevice, ctx->stream));
+      IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      dev_free(ctx, *a.slot);
+    }
+    *a.slot = fresh;
+  }
+  s.cap = cap;
+  invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
+  if (!params || !out) return IC_ERR_ARG;
+  *out = nullptr;
+  const ic_grid_params &p = *params;
+  if (p.nx < 6 || p.ny < 6 || p.nz < 6) return IC_ERR_ARG;
+  if (!(p.h > 0) || !(p.rho0 > 0) || !(p.c > 0) || !(p.dt > 0) || p.eta < 0 || p.zeta < 0 || p.kT < 0)
+    return IC_ERR_ARG;
+  if (p.precision != IC_FP64 && p.precision != IC_FP32) return IC_ERR_ARG;
+  if (p.forcing < IC_FORCE_NONE || p.forcing > IC_FORCE_PLANE || p.wave_axis < 0 || p.wave_axis > 2)
+    return IC_ERR_ARG;
+  if ((int64_t)p.nx * p.ny * p.nz >= (int64_t(1) << 32)) return IC_ERR_ARG;   // Philox cell counter is 32-bit
+  if ((p.alloc == nullptr) != (p.free == nullptr)) return IC_ERR_ARG;
+  const int n_ax = p.wave_axis == 0 ? p.nx : (p.wave_axis == 1 ? p.ny : p.nz);
+  if (p.wave_nlambda < 1 || p.plane_index < 0 || p.plane_index >= n_ax) return IC_ERR_ARG;
+
+  ic_ctx *ctx = new ic_ctx();
+  ctx->p = p;
+  ctx->cells = int64_t(p.nx) * p.ny * p.nz;
+  ctx->real_size = p.precision == IC_FP32 ? 4 : 8;
+  auto bail = [&](ic_status st) {
+    ic_destroy(ctx);
+    return st;
+  };
+  if (p.stream) {
+    ctx->stream = static_cast<cudaStream_t>(p.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IC_ERR_CUDA);
+    ctx->own_stream = true;
+  }
+  // driven mode: k, discrete k~, omega = c k~, Gamma
+  const double L = n_ax * p.h;
+  ctx->kwave = 2.0 * M_PI * p.wave_nlambda / L;
+  const double kd = (2.0 / p.h) * std::sin(0.5 * ctx->kwave * p.h);
+  ctx->omega = p.c * kd;
+  const double gamma = (4.0 * p.eta / 3.0 + p.zeta) / (2.0 * p.rho0);
+  ctx->force_amp = p.forcing == IC_FORCE_MODE ? 2.0 * gamma * ctx->omega * p.wave_amp
+                                              : p.wave_amp * n_ax * gamma * ctx->omega;
+
+  const size_t fbytes = size_t(ctx->cells) * ctx->real_size;
+  for (int b = 0; b < 3; ++b)
+    for (int j = 0; j < 4; ++j) {
+      ctx->U[b][j] = dev_alloc(ctx, fbytes);
+      if (!ctx->U[b][j]) return bail(IC_ERR_OOM);
+      if (cudaMemsetAsync(ctx->U[b][j], 0, fbytes, ctx->stream) != cudaSuccess) return bail(IC_ERR_CUDA);
+    }
+  ctx->n_partials = ic::fluid_num_partials(ctx);
+  ctx->d.partials = (double *)dev_alloc(ctx, ctx->n_partials * sizeof(double));
+  ctx->d.step = (int64_t *)dev_alloc(ctx, 4 * sizeof(int64_t));
+  ctx->d.scalars = (double *)dev_alloc(ctx, 16 * sizeof(double));
+  ctx->d.status = (int *)dev_alloc(ctx, 2 * sizeof(int));
+  ctx->cos_table = (double *)dev_alloc(ctx, n_ax * sizeof(double));
+  ctx->weights_cap = 1024;
+  ctx->d.weights = (double *)dev_alloc(ctx, ctx->weights_cap * sizeof(double));
+  if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->cos_table || !ctx->d.weights)
+    return bail(IC_ERR_OOM);
+  if (cudaMallocHost(&ctx->staging, (ctx->weights_cap + 3) * sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess)
+    return bail(IC_ERR_OOM);
+  ctx->d.rebuild = ctx->d.status + 1;
+  std::vector<double> tab(n_ax);
+  for (int i = 0; i < n_ax; ++i) tab[i] = std::cos(ctx->kwave * i * p.h);
+  const int zero_rebuild[2] = {0, 1};
+  if (cudaMemcpyAsync(ctx->cos_table, tab.data(), n_ax * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
+      cudaMemsetAsync(ctx->d.step, 0, 4 * sizeof(int64_t), ctx->stream) ||
+      cudaMemsetAsync(ctx->d.scalars, 0, 16 * sizeof(double), ctx->stream) ||
+      cudaMemsetAsync(ctx->d.weights, 0, ctx->weights_cap * sizeof(double), ctx->stream) ||
+      cudaMemcpyAsync(ctx->d.status, zero_rebuild, sizeof(zero_rebuild), cudaMemcpyHostToDevice, ctx->stream) ||
+      cudaStreamSynchronize(ctx->stream))
+    return bail(IC_ERR_CUDA);
+  // a state of rho = rho0 is delta rho = 0: the buffers are already zero
+  *out = ctx;
+  return IC_OK;
+}
+
+ic_status ic_set_state(ic_ctx *ctx, const double *rho, const double *gx, const double *gy, const double *gz) {
+  if (!ctx || !rho) return IC_ERR_ARG;
+  const size_t n = size_t(ctx->cells);
+  ic_status st = upload_real(ctx, ctx->U[ctx->cur][0], rho, ctx->p.rho0, n);
+  if (st) return st;
+  const double *g[3] = {gx, gy, gz};
+  for (int a = 0; a < 3; ++a) {
+    if (g[a]) {
+      st = upload_real(ctx, ctx->U[ctx->cur][1 + a], g[a], 0.0, n);
+      if (st) return st;
+    } else {
+      IC_CUDA(ctx, cudaMemsetAsync(ctx->U[ctx->cur][1 + a], 0, n * ctx->real_size, ctx->stream));
+    }
+  }
+  return IC_OK;
+}
+
+ic_status ic_get_state(ic_ctx *ctx, double *rho, double *gx, double *gy, double *gz) {
+  if (!ctx) return IC_ERR_ARG;
+  const size_t n = size_t(ctx->cells);
+  double *dst[4] = {rho, gx, gy, gz};
+  for (int j = 0; j < 4; ++j) {
+    if (!dst[j]) continue;
+    ic_status st = download_real(ctx, dst[j], ctx->U[ctx->cur][j], j == 0 ? ctx->p.rho0 : 0.0, n);
+    if (st) return st;
+  }
+  return check_device_status(ctx);
+}
+
+ic_status ic_init_thermal(ic_ctx *ctx, uint64_t seed, int add) {
+  if (!ctx) return IC_ERR_ARG;
+  if (!(ctx->p.kT > 0)) return fail(ctx, IC_ERR_STATE, "ic_init_thermal needs kT > 0");
+  IC_CUDA(ctx, ic::launch_thermal(ctx, seed, add));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return IC_OK;
+}
+
+ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u, const double *m_e,
+                           const double *kappa_ratio, const double *k_spring, int *first_id) {
+  if (!ctx || n < 0 || (n > 0 && (!q || !m_e || !kappa_ratio))) return IC_ERR_ARG;
+  if (n == 0) return IC_OK;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const ic_grid_params &p = ctx->p;
+  const double L[3] = {p.nx * p.h, p.ny * p.h, p.nz * p.h};
+  for (int i = 0; i < n; ++i) {
+    if (!(kappa_ratio[i] > 0)) return fail(ctx, IC_ERR_ARG, "kappa_ratio[%d] must be > 0", i);
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(q[3 * i + a])) return fail(ctx, IC_ERR_ARG, "q[%d] is not finite", i);
+  }
+  const int first = ctx->ps.n;
+  ic_status st = grow_particles(ctx, first + n);
+  if (st) return st;
+  ic::ParticleStore &s = ctx->ps;
+  std::vector<double> qw(3 * n), eps(n), ks(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      double x = std::fmod(q[3 * i + a], L[a]);
+      if (x < 0) x += L[a];
+      if (x >= L[a]) x -= L[a];
+      qw[3 * i + a] = x;
+    }
+    eps[i] = p.c * p.c * (1.0 / kappa_ratio[i] - 1.0);   // epsilon_pf, Eqs. (part_svel), (ke)
+    if (k_spring) ks[i] = k_spring[i];
+  }
+  const size_t r = ctx->real_size;
+  IC_CUDA(ctx, cudaMemcpy(s.q + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy(s.q_eq + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy(s.q_build + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  st = upload_real(ctx, (char *)s.m_e + r * first, m_e, 0.0, n);
+  if (!st) st = upload_real(ctx, (char *)s.eps + r * first, eps.data(), 0.0, n);
+  if (!st) st = upload_real(ctx, (char *)s.k_s + r * first, ks.data(), 0.0, n);
+  if (!st && u) st = upload_real(ctx, (char *)s.u + 3 * r * first, u, 0.0, 3 * size_t(n));
+  if (st) return st;
+  s.n = first + n;
+  if (!u) {
+    IC_CUDA(ctx, ic::launch_particle_velocity(ctx, first, n, ctx->U[ctx->cur]));
+  }
+  const int one = 1;
+  IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  invalidate_graphs(ctx);
+  if (first_id) *first_id = first;
+  return IC_OK;
+}
+
+ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w) {
+  if (!ctx || nsteps < 0) return IC_ERR_ARG;
+  if (nsteps == 0) return IC_OK;
+  if (w && nsteps > ctx->weights_cap) {
+    double *fresh = (double *)dev_alloc(ctx, size_t(nsteps) * sizeof(double));
+    if (!fresh) return fail(ctx, IC_ERR_OOM, "weights buffer");
+    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, ctx->d.weights);
+    ctx->d.weights = fresh;
+    cudaFreeHost(ctx->staging);
+    ctx->staging = nullptr;
+    IC_CUDA(ctx, cudaMallocHost(&ctx->staging, (size_t(nsteps) + 3) * sizeof(double)));
+    ctx->weights_cap = nsteps;
+    invalidate_graphs(ctx);
+  }
+  // Weights go through a pinned staging buffer (the caller's w is only read
+  // during this call); with w == NULL nothing is uploaded unless weights of an
+  // earlier call are still active.
+  if (w || ctx->host_wcount != 0) {
+    IC_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));   // previous upload has left the staging buffer
+    const int64_t hdr[2] = {ctx->host_step, w ? int64_t(nsteps) : 0};
+    std::memcpy(ctx->staging, hdr, sizeof(hdr));
+    size_t bytes = sizeof(hdr);
+    if (w) {
+      std::memcpy(ctx->staging + 2, w, size_t(nsteps) * sizeof(double));
+      IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.weights, ctx->staging + 2, size_t(nsteps) * sizeof(double),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    }
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.step + 1, ctx->staging, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    IC_CUDA(ctx, cudaEventRecord(ctx->staging_done, ctx->stream));
+    ctx->host_wcount = w ? nsteps : 0;
+  }
+  const bool use_graph = graphs_enabled() && !ctx->profiling;
+  for (int i = 0; i < nsteps; ++i) {
+    if (use_graph) {
+      cudaGraphExec_t &g = ctx->graph[ctx->cur];
+      if (!g) {
+        cudaGraph_t graph;
+        IC_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = enqueue_step(ctx, ctx->cur);
+        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "kernel launch during capture");
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        const cudaError_t ie = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+      }
+      IC_CUDA(ctx, cudaGraphLaunch(g, ctx->stream));
+    } else {
+      IC_CUDA(ctx, enqueue_step(ctx, ctx->cur));
+    }
+    ctx->cur = 1 - ctx->cur;
+  }
+  ctx->host_step += nsteps;
+  return IC_OK;
+}
+
+ic_status ic_sync(ic_ctx *ctx) {
+  if (!ctx) return IC_ERR_ARG;
+  return check_device_status(ctx);
+}
+
+ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q) {
+  if (!ctx) return IC_ERR_ARG;
+  const size_t n3 = 3 * size_t(ctx->ps.n);
+  if (ctx->ps.n > 0) {
+    ic_status st = IC_OK;
+    if (lambda) st = download_real(ctx, lambda, ctx->ps.lam, 0.0, n3);
+    if (!st && u) st = download_real(ctx, u, ctx->ps.u, 0.0, n3);
+    if (st) return st;
+    if (q) IC_CUDA(ctx, cudaMemcpyAsync(q, ctx->ps.q, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return check_device_status(ctx);
+}
+
+ic_status ic_time_average(ic_ctx *ctx, double *f_spring, double *lambda, double *a2, int reset) {
+  if (!ctx) return IC_ERR_ARG;
+  double sc[2];
+  IC_CUDA(ctx, cudaMemcpyAsync(sc, ctx->d.scalars, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
+  const size_t n = size_t(ctx->ps.n);
+  std::vector<double> acc(6 * n);
+  if (n) IC_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->ps.acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+  ic_status st = check_device_status(ctx);
+  if (st) return st;
+  if (!(sc[0] != 0.0)) return fail(ctx, IC_ERR_STATE, "time-average weights sum to zero");
+  for (size_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      if (f_spring) f_spring[3 * i + a] = acc[6 * i + a] / sc[0];
+      if (lambda) lambda[3 * i + a] = acc[6 * i + 3 + a] / sc[0];
+    }
+  if (a2) *a2 = sc[1] / sc[0];
+  if (reset) {
+    IC_CUDA(ctx, cudaMemsetAsync(ctx->d.scalars, 0, 2 * sizeof(double), ctx->stream));
+    if (n) IC_CUDA(ctx, cudaMemsetAsync(ctx->ps.acc, 0, acc.size() * sizeof(double), ctx->stream));
+    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return IC_OK;
+}
+
+ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step) {
+  if (!ctx) return IC_ERR_ARG;
+  double *sums = ctx->d.scalars + 8;
+  IC_CUDA(ctx, ic::launch_field_sums(ctx, ctx->U[ctx->cur], sums));
+  IC_CUDA(ctx, cudaMemsetAsync(ctx->d.scalars + 12, 0, 3 * sizeof(double), ctx->stream));
+  if (ctx->ps.n > 0) IC_CUDA(ctx, ic::launch_particle_momentum(ctx, ctx->d.scalars + 12));
+  double h[7];
+  IC_CUDA(ctx, cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  ic_status st = check_device_status(ctx);
+  if (st) return st;
+  const double vol = ctx->p.h * ctx->p.h * ctx->p.h;
+  if (p_total)
+    for (int a = 0; a < 3; ++a) p_total[a] = vol * h[a] + h[4 + a];
+  if (mode_amp) *mode_amp = 2.0 * h[3] / double(ctx->cells);
+  if (step) *step = ctx->host_step;
+  return IC_OK;
+}
+
+// ----------------------------------------------------------- checkpointing
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, precision, nx, ny, nz, np;
+  int64_t step;
+  double scalars[3];
+};
+
+size_t ckpt_size(const ic_ctx *ctx) {
+  const size_t r = ctx->real_size, n = size_t(ctx->ps.n);
+  return sizeof(CkptHeader) + 4 * size_t(ctx->cells) * r + n * (24 + 24 + 48) + n * r * (3 + 1 + 1 + 1 + 3 + 3);
+}
+}  // namespace
+
+ic_status ic_checkpoint(ic_ctx *ctx, void *buf, size_t *bytes) {
+  if (!ctx || !bytes) return IC_ERR_ARG;
+  const size_t need = ckpt_size(ctx);
+  if (!buf) {
+    *bytes = need;
+    return IC_OK;
+  }
+  if (*bytes < need) return fail(ctx, IC_ERR_ARG, "checkpoint buffer too small (%zu < %zu)", *bytes, need);
+  ic_status st = check_device_status(ctx);
+  if (st) return st;
+  CkptHeader hd{};
+  std::memcpy(hd.magic, "ICCKPT1", 8);
+  hd.version = 1;
+  hd.precision = ctx->p.precision;
+  hd.nx = ctx->p.nx;
+  hd.ny = ctx->p.ny;
+  hd.nz = ctx->p.nz;
+  hd.np = ctx->ps.n;
+  hd.step = ctx->host_step;
+  IC_CUDA(ctx, cudaMemcpy(hd.scalars, ctx->d.scalars, sizeof(hd.scalars), cudaMemcpyDeviceToHost));
+  char *out = static_cast<char *>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  out += sizeof(hd);
+  const size_t r = ctx->real_size, fb = size_t(ctx->cells) * r, n = size_t(ctx->ps.n);
+  for (int j = 0; j < 4; ++j, out += fb) IC_CUDA(ctx, cudaMemcpy(out, ctx->U[ctx->cur][j], fb, cudaMemcpyDeviceToHost));
+  const ic::ParticleStore &s = ctx->ps;
+  struct Item {
+    const void *src;
+    size_t len;
+  } items[] = {{s.q, 24 * n},     {s.q_eq, 24 * n},  {s.acc, 48 * n},   {s.u, 3 * r * n}, {s.m_e, r * n},
+               {s.eps, r * n},    {s.k_s, r * n},    {s.force, 3 * r * n}, {s.lam, 3 * r * n}};
+  for (const Item &it : items) {
+    if (it.len) IC_CUDA(ctx, cudaMemcpy(out, it.src, it.len, cudaMemcpyDeviceToHost));
+    out += it.len;
+  }
+  *bytes = need;
+  return IC_OK;
+}
+
+ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
+  if (!ctx || !buf || bytes < sizeof(CkptHeader)) return IC_ERR_ARG;
+  CkptHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "ICCKPT1", 8) != 0 || hd.version != 1)
+    return fail(ctx, IC_ERR_ARG, "not a libic checkpoint");
+  if (hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny || hd.nz != ctx->p.nz)
+    return fail(ctx, IC_ERR_ARG, "checkpoint grid or precision differs from this context");
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->ps.n = 0;
+  ic_status st = grow_particles(ctx, hd.np);
+  if (st) return st;
+  ctx->ps.n = hd.np;
+  if (bytes < ckpt_size(ctx)) return fail(ctx, IC_ERR_ARG, "checkpoint truncated");
+  const char *in = static_cast<const char *>(buf) + sizeof(hd);
+  ctx->cur = 0;
+  const size_t r = ctx->real_size, fb = size_t(ctx->cells) * r, n = size_t(hd.np);
+  for (int j = 0; j < 4; ++j, in += fb) IC_CUDA(ctx, cudaMemcpy(ctx->U[0][j], in, fb, cudaMemcpyHostToDevice));
+  ic::ParticleStore &s = ctx->ps;
+  struct Item {
+    void *dst;
+    size_t len;
+  } items[] = {{s.q, 24 * n},     {s.q_eq, 24 * n},  {s.acc, 48 * n},   {s.u, 3 * r * n}, {s.m_e, r * n},
+               {s.eps, r * n},    {s.k_s, r * n},    {s.force, 3 * r * n}, {s.lam, 3 * r * n}};
+  for (const Item &it : items) {
+    if (it.len) IC_CUDA(ctx, cudaMemcpy(it.dst, in, it.len, cudaMemcpyHostToDevice));
+    in += it.len;
+  }
+  if (n) IC_CUDA(ctx, cudaMemcpy(s.q_build, s.q, 24 * n, cudaMemcpyDeviceToDevice));
+  ctx->host_step = hd.step;
+  ctx->host_wcount = 0;
+  const int64_t steps[3] = {hd.step, hd.step, 0};
+  IC_CUDA(ctx, cudaMemcpy(ctx->d.step, steps, sizeof(steps), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy(ctx->d.scalars, hd.scalars, sizeof(hd.scalars), cudaMemcpyHostToDevice));
+  const int st2[2] = {0, 1};
+  IC_CUDA(ctx, cudaMemcpy(ctx->d.status, st2, sizeof(st2), cudaMemcpyHostToDevice));
+  invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+ic_status ic_device_views(ic_ctx *ctx, ic_views *out) {
+  if (!ctx || !out) return IC_ERR_ARG;
+  out->drho = ctx->U[ctx->cur][0];
+  out->gx = ctx->U[ctx->cur][1];
+  out->gy = ctx->U[ctx->cur][2];
+  out->gz = ctx->U[ctx->cur][3];
+  out->precision = ctx->p.precision;
+  out->n_particles = ctx->ps.n;
+  out->q = ctx->ps.q;
+  return IC_OK;
+}
+
+ic_status ic_profile(ic_ctx *ctx, int enable) {
+  if (!ctx) return IC_ERR_ARG;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->profiling = enable != 0;
+  ctx->timed.clear();
+  ctx->event_next = 0;
+  return IC_OK;
+}
+
+ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset) {
+  if (!ctx) return IC_ERR_ARG;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double acc[3] = {0, 0, 0};
+  int64_t cnt[3] = {0, 0, 0};
+  for (const auto &t : ctx->timed) {
+    float v = 0.f;
+    IC_CUDA(ctx, cudaEventElapsedTime(&v, t.a, t.b));
+    acc[t.cls] += v;
+    ++cnt[t.cls];
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (launches) launches[i] = cnt[i];
+  }
+  if (reset) {
+    ctx->timed.clear();
+    ctx->event_next = 0;
+  }
+  return IC_OK;
+}
+
+const char *ic_last_error(const ic_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void ic_destroy(ic_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  invalidate_graphs(ctx);
+  for (cudaEvent_t ev : ctx->event_pool) cudaEventDestroy(ev);
+  if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  if (ctx->staging) cudaFreeHost(ctx->staging);
+  while (ctx->n_allocs > 0) dev_free(ctx, ctx->allocs[ctx->n_allocs - 1]);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

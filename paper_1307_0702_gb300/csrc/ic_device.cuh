@@ -1,0 +1,155 @@
+// Device-side building blocks of libic: the counter-based generator, the
+// normal transform, the 3-point kernel weights and periodic index helpers.
+//
+// Random numbers.  The stochastic stress (Sec. 4.2) is drawn per cell and per
+// step from Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) with
+//   key     = (seed & 0xffffffff, seed >> 32)
+//   counter = (cell, step, (purpose << 16) | block, box).
+// For purpose 0 the 6 blocks give 24 words per cell and step; normal j
+// (j = 0..5: W_A components xx, yy, zz, xy, xz, yz; j = 6..11: W_B) takes its
+// high word from word j and its low word from word 12 + j.  Normals come in
+// Box-Muller pairs: (n_2i, n_2i+1) = r (cos 2 pi u_2i+1, sin 2 pi u_2i+1),
+// r = sqrt(-2 ln u_2i).  The FP64 path builds 52-bit uniforms
+// u = (2 m + 1) 2^-53, m = (hi << 20) | (lo >> 12); the FP32 path uses the
+// high word alone, u = (hi + 1/2) 2^-32, so its normals follow the FP64 ones
+// to about 1e-7 and need only blocks 0-2.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ic {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kPurposeStress = 0u;
+constexpr uint32_t kPurposeThermal = 1u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+struct RngKey {
+  uint32_t k0, k1, box;
+};
+
+__device__ __forceinline__ uint4 philox_block(const RngKey &key, uint32_t cell, uint32_t step,
+                                              uint32_t purpose, uint32_t block) {
+  return philox4x32_10(make_uint4(cell, step, (purpose << 16) | block, key.box), key.k0, key.k1);
+}
+
+__device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
+  const uint64_t m = (uint64_t(hi) << 20) | uint64_t(lo >> 12);
+  return double(2ull * m + 1ull) * 0x1p-53;
+}
+
+__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
+  const double r = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincos(2.0 * 3.141592653589793 * u2, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t h1, uint32_t h2, float &z0, float &z1) {
+  const float u1 = __fmaf_rn(__uint2float_rn(h1), 0x1p-32f, 0x1p-33f);
+  const float t = __fmaf_rn(__uint2float_rn(h2), 0x1p-32f, 0x1p-33f) - 0.5f;
+  const float r = sqrtf(-2.0f * __logf(u1));
+  float s, c;
+  __sincosf(6.2831853071795865f * t, &s, &c);   // 2 pi u = 2 pi t + pi
+  z0 = -r * c;
+  z1 = -r * s;
+}
+
+// The six combined normals W_A + beta W_B of one cell and step, ordered
+// xx, yy, zz, xy, xz, yz.  with_b = false skips stream B (beta = 0).
+__device__ __forceinline__ void stress_normals(const RngKey &key, uint32_t cell, uint32_t step,
+                                               bool with_b, double beta, double out[6]) {
+  const uint4 h0 = philox_block(key, cell, step, kPurposeStress, 0);
+  const uint4 h1 = philox_block(key, cell, step, kPurposeStress, 1);
+  const uint4 l0 = philox_block(key, cell, step, kPurposeStress, 3);
+  const uint4 l1 = philox_block(key, cell, step, kPurposeStress, 4);
+  double a[6];
+  box_muller(uniform52(h0.x, l0.x), uniform52(h0.y, l0.y), a[0], a[1]);
+  box_muller(uniform52(h0.z, l0.z), uniform52(h0.w, l0.w), a[2], a[3]);
+  box_muller(uniform52(h1.x, l1.x), uniform52(h1.y, l1.y), a[4], a[5]);
+  if (with_b) {
+    const uint4 h2 = philox_block(key, cell, step, kPurposeStress, 2);
+    const uint4 l2 = philox_block(key, cell, step, kPurposeStress, 5);
+    double b[6];
+    box_muller(uniform52(h1.z, l1.z), uniform52(h1.w, l1.w), b[0], b[1]);
+    box_muller(uniform52(h2.x, l2.x), uniform52(h2.y, l2.y), b[2], b[3]);
+    box_muller(uniform52(h2.z, l2.z), uniform52(h2.w, l2.w), b[4], b[5]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[j] = a[j] + beta * b[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[j] = a[j];
+  }
+}
+
+__device__ __forceinline__ void stress_normals(const RngKey &key, uint32_t cell, uint32_t step,
+                                               bool with_b, float beta, float out[6]) {
+  const uint4 h0 = philox_block(key, cell, step, kPurposeStress, 0);
+  const uint4 h1 = philox_block(key, cell, step, kPurposeStress, 1);
+  float a[6];
+  box_muller_f32(h0.x, h0.y, a[0], a[1]);
+  box_muller_f32(h0.z, h0.w, a[2], a[3]);
+  box_muller_f32(h1.x, h1.y, a[4], a[5]);
+  if (with_b) {
+    const uint4 h2 = philox_block(key, cell, step, kPurposeStress, 2);
+    float b[6];
+    box_muller_f32(h1.z, h1.w, b[0], b[1]);
+    box_muller_f32(h2.x, h2.y, b[2], b[3]);
+    box_muller_f32(h2.z, h2.w, b[4], b[5]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[j] = __fmaf_rn(beta, b[j], a[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[j] = a[j];
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+// 1D weights of the 3 points nearest to s (in grid units, already shifted by
+// the location-set offset): i0 = floor(s + 1/2), r = s - i0 in [-1/2, 1/2),
+// phi(i0-1 - s), phi(i0 - s), phi(i0+1 - s) of the Roma-Peskin function.
+// With S = sqrt(1 - 3 r^2): (2 - 3r - S)/6, (1 + S)/3, (2 + 3r - S)/6.
+template <typename real>
+__device__ __forceinline__ void peskin3(real r, real w[3]) {
+  const real s = sqrt(real(1) - real(3) * r * r);
+  w[0] = (real(2) - real(3) * r - s) / real(6);
+  w[1] = (real(1) + s) / real(3);
+  w[2] = (real(2) + real(3) * r - s) / real(6);
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// minimum-image integer offset b - a on a ring of n points
+__device__ __forceinline__ int ring_delta(int b, int a, int n) {
+  int d = (b - a) % n;
+  if (d < 0) d += n;
+  if (2 * d > n) d -= n;
+  return d;
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum(real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace ic

@@ -1,0 +1,523 @@
+// Fluid kernels of libic: one SSP-RK3 stage of compressible Landau-Lifshitz
+// fluctuating hydrodynamics on the periodic staggered grid (Sec. 4.2 and
+// App. A.2), the thermal initial state and the grid reductions.
+//
+// Discretisation (conservative flux form; the paper defers it to other work):
+//   d rho/dt   = -(1/h) sum_a (g^a_i - g^a_{i-a})
+//   d g^a/dt   = -(1/h) [T_aa(i+a) - T_aa(i) + sum_{b!=a} (T_ab(i) - T_ab(i-b))]
+//   T = g v + pi I - sigma - Sigma, diagonal at centres, off-diagonal on the
+//   (a,b) edge owned by cell i (at r_i + h/2 (e_a + e_b)), v^a = g^a / rho^a with
+//   the face density rho^a = (rho_i + rho_{i+a}) / 2;
+//   advective parts are products of two-point averages; sigma = eta (grad v +
+//   grad v^T) + (zeta - 2 eta/3) div v I; pi = c^2 rho + p_ext (the particle
+//   pressure S Omega enters through a sparse correction, see ic_particles.cu);
+//   Sigma_aa = sqrt2 S N_aa + sqrt2 (B - S/3) tr N, Sigma_ab = S N_ab with
+//   N = W_A + beta_s W_B (beta = -sqrt3, +sqrt3, 0 for stages 1..3).
+//   Stage s: U_{s+1} = a_s U^n + b_s (U_s + dt dU/dt(U_s, t_s)), (a, b) =
+//   (0, 1), (3/4, 1/4), (1/3, 2/3); t_s = t^n, t^{n+1}, t^{n+1/2}.
+//
+// Kernel layout.  A CTA owns a TX x TY column of cells and marches up a chunk
+// of z planes ("2.5D" blocking).  Its (TX+2) x (TY+2) threads also cover a
+// one-cell ring so that each thread computes the fluxes of one cell; the
+// in-plane neighbours come from shared memory and the z neighbours from
+// registers carried between planes.  Per plane: one load of the next plane,
+// one flux evaluation with the Philox noise regenerated in registers, and one
+// fused combination with U^n.  State stores delta rho = rho - rho0.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ic_device.cuh"
+#include "ic_internal.hpp"
+
+namespace ic {
+namespace {
+
+template <typename real>
+struct StageArgs {
+  const real *__restrict__ s[4];   // U_s
+  const real *__restrict__ n[4];   // U^n
+  real *__restrict__ o[4];         // U_{s+1}
+  FluidConsts c;
+  const int64_t *step;
+  double *partials;                // stage 3: per-CTA sum of delta rho cos(k x)
+  int zchunk;
+};
+
+template <typename real>
+struct PlaneVals {
+  real gx, gy, gz, vx, vy, vz, dr;
+  real nz[6];
+};
+
+constexpr double kStageTime[3] = {0.0, 1.0, 0.5};
+constexpr double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
+constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
+
+template <typename real, int TX, int TY, int STAGE, bool NOISE>
+__global__ void __launch_bounds__((TX + 2) * (TY + 2))
+    k_rk3_stage(const StageArgs<real> a) {
+  constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
+  enum { GX = 0, GY, GZ, VX, VY, VZ };
+  enum { TXX = 0, TYY, TXY, TYX, TZX, TZY };
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *sm = reinterpret_cast<real *>(smem_raw);
+  real *T = sm + 12 * EXY;
+  __shared__ double s_drive;
+
+  const FluidConsts &c = a.c;
+  const int NX = c.nx, NY = c.ny, NZ = c.nz;
+  const int t = threadIdx.x;
+  const int ex = t % EX, ey = t / EX;
+  const int gx_raw = int(blockIdx.x) * TX + ex - 1;
+  const int gy_raw = int(blockIdx.y) * TY + ey - 1;
+  const int x = wrap(gx_raw, NX), y = wrap(gy_raw, NY);
+  const int xp = (x + 1 == NX) ? 0 : x + 1;
+  const int yp = (y + 1 == NY) ? 0 : y + 1;
+  const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx_raw < NX && gy_raw < NY;
+  const int eXm = ey * EX + max(ex - 1, 0), eXp = ey * EX + min(ex + 1, EX - 1);
+  const int eYm = max(ey - 1, 0) * EX + ex, eYp = min(ey + 1, EY - 1) * EX + ex;
+  const int z0 = int(blockIdx.z) * a.zchunk;
+  const int z1 = min(z0 + a.zchunk, NZ);
+
+  const int64_t step = *a.step;
+  if (t == 0) {
+    const double tt = (double(step) + kStageTime[STAGE]) * c.dt;
+    s_drive = (c.forcing == IC_FORCE_NONE) ? 0.0 : c.force_amp * sin(c.omega * tt + c.phase);
+  }
+
+  const real rho0 = real(c.rho0), half = real(0.5), quarter = real(0.25);
+  const real inv_h = real(c.inv_h), c2 = real(c.c2), eta = real(c.eta), lam2 = real(c.lam2);
+  const real two_eta = real(2) * eta;
+  const real nd = real(c.noise_diag), nt = real(c.noise_trace), ne = real(c.noise_edge);
+  const real beta = STAGE == 0 ? real(-1.7320508075688772) : (STAGE == 1 ? real(1.7320508075688772) : real(0));
+  const RngKey key{c.k0, c.k1, c.box};
+  const uint32_t ustep = uint32_t(step);
+  const size_t plane = size_t(NX) * NY;
+
+  // cos(k x) along the wave axis (mode amplitude and MODE drive), and the
+  // drive profile: cos(k x) (MODE) or the indicator of the driven plane (PLANE)
+  const real cos_xy = c.wave_axis < 2 ? real(c.cos_table[c.wave_axis == 0 ? x : y]) : real(0);
+  auto cosw = [&](int kk) -> real {
+    return c.wave_axis < 2 ? cos_xy : real(c.cos_table[wrap(kk, NZ)]);
+  };
+  auto profile = [&](int kk) -> real {
+    if (c.forcing == IC_FORCE_MODE) return cosw(kk);
+    if (c.forcing == IC_FORCE_PLANE) {
+      const int coord = c.wave_axis == 0 ? x : (c.wave_axis == 1 ? y : wrap(kk, NZ));
+      return real(coord == c.plane_index ? 1 : 0);
+    }
+    return real(0);
+  };
+
+  auto load = [&](int kk) {
+    PlaneVals<real> v;
+    const int k = wrap(kk, NZ);
+    const int kp = (k + 1 == NZ) ? 0 : k + 1;
+    const size_t i = size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * k);
+    const size_t row = size_t(NX) * (size_t(y) + size_t(NY) * k);
+    v.dr = a.s[0][i];
+    const real drx = a.s[0][row + xp];
+    const real dry = a.s[0][size_t(x) + size_t(NX) * (size_t(yp) + size_t(NY) * k)];
+    const real drz = a.s[0][size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * kp)];
+    v.gx = a.s[1][i];
+    v.gy = a.s[2][i];
+    v.gz = a.s[3][i];
+    v.vx = v.gx / (rho0 + half * (v.dr + drx));
+    v.vy = v.gy / (rho0 + half * (v.dr + dry));
+    v.vz = v.gz / (rho0 + half * (v.dr + drz));
+    if (NOISE) {
+      stress_normals(key, uint32_t(i), ustep, STAGE != 2, beta, v.nz);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) v.nz[j] = real(0);
+    }
+    return v;
+  };
+  auto store_plane = [&](int buf, const PlaneVals<real> &v) {
+    real *B = sm + buf * 6 * EXY;
+    B[GX * EXY + t] = v.gx;
+    B[GY * EXY + t] = v.gy;
+    B[GZ * EXY + t] = v.gz;
+    B[VX * EXY + t] = v.vx;
+    B[VY * EXY + t] = v.vy;
+    B[VZ * EXY + t] = v.vz;
+  };
+
+  PlaneVals<real> P = load(z0 - 1);
+  store_plane((z0 - 1) & 1, P);
+  real vz_m = real(0), gz_m = real(0), txz_m = real(0), tyz_m = real(0), tzz_k = real(0);
+  real mode_acc = real(0);
+  const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
+  const real dt = real(c.dt);
+
+  for (int k = z0 - 1; k < z1; ++k) {
+    const PlaneVals<real> Q = load(k + 1);
+    store_plane((k + 1) & 1, Q);
+    __syncthreads();
+    const real *Pk = sm + (k & 1) * 6 * EXY;
+    const real *Pq = sm + ((k + 1) & 1) * 6 * EXY;
+    const real drive = real(s_drive);
+
+    const real gx_xm = Pk[GX * EXY + eXm], vx_xm = Pk[VX * EXY + eXm];
+    const real gy_ym = Pk[GY * EXY + eYm], vy_ym = Pk[VY * EXY + eYm];
+    const real gx_yp = Pk[GX * EXY + eYp], vx_yp = Pk[VX * EXY + eYp];
+    const real gy_xp = Pk[GY * EXY + eXp], vy_xp = Pk[VY * EXY + eXp];
+    const real gz_xp = Pk[GZ * EXY + eXp], vz_xp = Pk[VZ * EXY + eXp];
+    const real gz_yp = Pk[GZ * EXY + eYp], vz_yp = Pk[VZ * EXY + eYp];
+    const real vx1_xm = Pq[VX * EXY + eXm], vy1_ym = Pq[VY * EXY + eYm];
+
+    const real div_k = ((P.vx - vx_xm) + (P.vy - vy_ym) + (P.vz - vz_m)) * inv_h;
+    const real div_k1 = ((Q.vx - vx1_xm) + (Q.vy - vy1_ym) + (Q.vz - P.vz)) * inv_h;
+    const real pk = c2 * P.dr + drive * profile(k);
+    const real pk1 = c2 * Q.dr + drive * profile(k + 1);
+
+    const real tr_k = P.nz[0] + P.nz[1] + P.nz[2];
+    const real tr_k1 = Q.nz[0] + Q.nz[1] + Q.nz[2];
+    const real sxx = nd * P.nz[0] + nt * tr_k;
+    const real syy = nd * P.nz[1] + nt * tr_k;
+    const real szz1 = nd * Q.nz[2] + nt * tr_k1;
+    const real sxy = ne * P.nz[3], sxz = ne * P.nz[4], syz = ne * P.nz[5];
+
+    const real txx = quarter * (gx_xm + P.gx) * (vx_xm + P.vx) + pk -
+                     (two_eta * (P.vx - vx_xm) * inv_h + lam2 * div_k) - sxx;
+    const real tyy = quarter * (gy_ym + P.gy) * (vy_ym + P.vy) + pk -
+                     (two_eta * (P.vy - vy_ym) * inv_h + lam2 * div_k) - syy;
+    const real tzz1 = quarter * (P.gz + Q.gz) * (P.vz + Q.vz) + pk1 -
+                      (two_eta * (Q.vz - P.vz) * inv_h + lam2 * div_k1) - szz1;
+    const real visc_xy = eta * ((vx_yp - P.vx) + (vy_xp - P.vy)) * inv_h;
+    const real txy = quarter * (P.gx + gx_yp) * (P.vy + vy_xp) - visc_xy - sxy;
+    const real tyx = quarter * (P.gy + gy_xp) * (P.vx + vx_yp) - visc_xy - sxy;
+    const real visc_xz = eta * ((Q.vx - P.vx) + (vz_xp - P.vz)) * inv_h;
+    const real txz = quarter * (P.gx + Q.gx) * (P.vz + vz_xp) - visc_xz - sxz;
+    const real tzx = quarter * (P.gz + gz_xp) * (P.vx + Q.vx) - visc_xz - sxz;
+    const real visc_yz = eta * ((Q.vy - P.vy) + (vz_yp - P.vz)) * inv_h;
+    const real tyz = quarter * (P.gy + Q.gy) * (P.vz + vz_yp) - visc_yz - syz;
+    const real tzy = quarter * (P.gz + gz_yp) * (P.vy + Q.vy) - visc_yz - syz;
+
+    T[TXX * EXY + t] = txx;
+    T[TYY * EXY + t] = tyy;
+    T[TXY * EXY + t] = txy;
+    T[TYX * EXY + t] = tyx;
+    T[TZX * EXY + t] = tzx;
+    T[TZY * EXY + t] = tzy;
+    __syncthreads();
+
+    if (interior && k >= z0) {
+      const real r_rho = -((P.gx - gx_xm) + (P.gy - gy_ym) + (P.gz - gz_m)) * inv_h;
+      const real r_gx = -((T[TXX * EXY + eXp] - txx) + (txy - T[TXY * EXY + eYm]) + (txz - txz_m)) * inv_h;
+      const real r_gy = -((T[TYY * EXY + eYp] - tyy) + (tyx - T[TYX * EXY + eXm]) + (tyz - tyz_m)) * inv_h;
+      const real r_gz = -((tzz1 - tzz_k) + (tzx - T[TZX * EXY + eXm]) + (tzy - T[TZY * EXY + eYm])) * inv_h;
+      const size_t i = size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * k);
+      real o0 = P.dr + dt * r_rho, o1 = P.gx + dt * r_gx, o2 = P.gy + dt * r_gy, o3 = P.gz + dt * r_gz;
+      if (STAGE != 0) {
+        o0 = ca * a.n[0][i] + cb * o0;
+        o1 = ca * a.n[1][i] + cb * o1;
+        o2 = ca * a.n[2][i] + cb * o2;
+        o3 = ca * a.n[3][i] + cb * o3;
+      }
+      a.o[0][i] = o0;
+      a.o[1][i] = o1;
+      a.o[2][i] = o2;
+      a.o[3][i] = o3;
+      if (STAGE == 2) mode_acc += o0 * cosw(k);
+    }
+    vz_m = P.vz;
+    gz_m = P.gz;
+    txz_m = txz;
+    tyz_m = tyz;
+    tzz_k = tzz1;
+    P = Q;
+  }
+  (void)plane;
+
+  if (STAGE == 2) {
+    // per-CTA partial of sum (rho - rho0) cos(k x), fixed reduction order
+    double v = double(mode_acc);
+    v = warp_sum(v);
+    __shared__ double s_red[32];
+    const int lane = t & 31, wid = t >> 5;
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      const int nw = (EXY + 31) / 32;
+      for (int j = 0; j < nw; ++j) s += s_red[j];
+      const size_t b = blockIdx.x + size_t(gridDim.x) * (blockIdx.y + size_t(gridDim.y) * blockIdx.z);
+      a.partials[b] = s;
+    }
+  }
+}
+
+template <typename real>
+struct TileShape;
+template <>
+struct TileShape<float> {
+  static constexpr int TX = 32, TY = 8;
+};
+template <>
+struct TileShape<double> {
+  static constexpr int TX = 32, TY = 4;
+};
+
+int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, 16); }
+
+template <typename real>
+dim3 stage_grid(const ic_ctx *ctx) {
+  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  const int zc = zchunk_for(ctx);
+  return dim3((ctx->p.nx + TX - 1) / TX, (ctx->p.ny + TY - 1) / TY, (ctx->p.nz + zc - 1) / zc);
+}
+
+template <typename real, int STAGE, bool NOISE>
+cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const in_n[4],
+                           void *const out[4]) {
+  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  constexpr int EXY = (TX + 2) * (TY + 2);
+  StageArgs<real> a;
+  for (int j = 0; j < 4; ++j) {
+    a.s[j] = static_cast<const real *>(in_s[j]);
+    a.n[j] = static_cast<const real *>(in_n[j]);
+    a.o[j] = static_cast<real *>(out[j]);
+  }
+  a.c = fluid_consts(ctx);
+  a.step = ctx->d.step;
+  a.partials = ctx->d.partials;
+  a.zchunk = zchunk_for(ctx);
+  const size_t smem = 18 * EXY * sizeof(real);
+  static_assert(18 * EXY * sizeof(real) <= 48 * 1024, "stage tile must fit the default shared memory");
+  auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
+  kern<<<stage_grid<real>(ctx), EXY, smem, ctx->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_stage_r(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+                           void *const out[4]) {
+  const bool noise = ctx->p.kT > 0.0;
+  switch (stage * 2 + (noise ? 1 : 0)) {
+    case 0: return launch_stage_t<real, 0, false>(ctx, in_s, in_n, out);
+    case 1: return launch_stage_t<real, 0, true>(ctx, in_s, in_n, out);
+    case 2: return launch_stage_t<real, 1, false>(ctx, in_s, in_n, out);
+    case 3: return launch_stage_t<real, 1, true>(ctx, in_s, in_n, out);
+    case 4: return launch_stage_t<real, 2, false>(ctx, in_s, in_n, out);
+    default: return launch_stage_t<real, 2, true>(ctx, in_s, in_n, out);
+  }
+}
+
+// ------------------------------------------------------------ thermal state
+// Two passes over the cells: partial sums of the fluctuations, then the
+// update with the means removed (the normals are regenerated, not stored).
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+__device__ void thermal_values(const RngKey &key, uint32_t cell, double sd_rho, double sd_g,
+                               double out[4]) {
+  const uint4 h = philox_block(key, cell, 0, kPurposeThermal, 0);
+  const uint4 l = philox_block(key, cell, 0, kPurposeThermal, 1);
+  double z[4];
+  box_muller(uniform52(h.x, l.x), uniform52(h.y, l.y), z[0], z[1]);
+  box_muller(uniform52(h.z, l.z), uniform52(h.w, l.w), z[2], z[3]);
+  out[0] = sd_rho * z[0];
+  out[1] = sd_g * z[1];
+  out[2] = sd_g * z[2];
+  out[3] = sd_g * z[3];
+}
+
+template <int NV>
+__device__ void block_reduce_store(double v[NV], double *dst) {
+  __shared__ double s[NV][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const double r = warp_sum(v[j]);
+    if (lane == 0) s[j][wid] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double acc = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) acc += s[threadIdx.x][w];
+    dst[size_t(blockIdx.x) * NV + threadIdx.x] = acc;
+  }
+}
+
+__global__ void k_thermal_sums(RngKey key, int64_t cells, double sd_rho, double sd_g, double *partials) {
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cells;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    double v[4];
+    thermal_values(key, uint32_t(i), sd_rho, sd_g, v);
+    for (int j = 0; j < 4; ++j) acc[j] += v[j];
+  }
+  block_reduce_store<4>(acc, partials);
+}
+
+// final fixed-order reduction of nb blocks x nv values into out[nv] (one block)
+__global__ void k_reduce_partials(const double *partials, int nb, int nv, double *out, double scale) {
+  __shared__ double s[kRedThreads];
+  for (int j = 0; j < nv; ++j) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[size_t(b) * nv + j];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = s[0] * scale;
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__global__ void k_thermal_apply(RngKey key, int64_t cells, double sd_rho, double sd_g,
+                                const double *mean, int add, real *dr, real *gx, real *gy, real *gz) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cells;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    double v[4];
+    thermal_values(key, uint32_t(i), sd_rho, sd_g, v);
+    real *f[4] = {dr, gx, gy, gz};
+    for (int j = 0; j < 4; ++j) {
+      const double fl = v[j] - mean[j];
+      f[j][i] = add ? real(double(f[j][i]) + fl) : real(fl);
+    }
+  }
+}
+
+// sums of g (3 components) and of delta rho cos(k x) over the grid
+template <typename real>
+__global__ void k_field_sums(int nx, int ny, int nz, int axis, const double *cos_table,
+                             const real *dr, const real *gx, const real *gy, const real *gz,
+                             double *partials) {
+  const int64_t cells = int64_t(nx) * ny * nz;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cells;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    acc[0] += double(gx[i]);
+    acc[1] += double(gy[i]);
+    acc[2] += double(gz[i]);
+    if (cos_table) {
+      const int64_t x = i % nx, y = (i / nx) % ny, z = i / (int64_t(nx) * ny);
+      acc[3] += double(dr[i]) * cos_table[axis == 0 ? x : (axis == 1 ? y : z)];
+    }
+  }
+  block_reduce_store<4>(acc, partials);
+}
+
+// End of step: A(t) from the stage-3 partials, weighted accumulation, the
+// non-finite check and the step counter (one block).
+__global__ void k_end_of_step(const double *partials, int nb, double inv_cells, int has_mode,
+                              int64_t *step, const double *weights, double *scalars, int *status) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[b];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double A = has_mode ? 2.0 * s[0] * inv_cells : 0.0;
+    const int64_t n = step[0], j = n - step[1];
+    const double w = (j >= 0 && j < step[2]) ? weights[j] : 0.0;
+    if (!isfinite(s[0])) atomicOr(status, kStatusNonfinite);
+    scalars[0] += w;
+    scalars[1] += w * A * A;
+    scalars[2] = A;
+    *step = n + 1;
+  }
+}
+
+}  // namespace
+
+FluidConsts fluid_consts(const ic_ctx *ctx) {
+  const ic_grid_params &p = ctx->p;
+  FluidConsts c{};
+  c.nx = p.nx;
+  c.ny = p.ny;
+  c.nz = p.nz;
+  c.rho0 = p.rho0;
+  c.c2 = p.c * p.c;
+  c.inv_h = 1.0 / p.h;
+  c.dt = p.dt;
+  c.eta = p.eta;
+  c.lam2 = p.zeta - 2.0 * p.eta / 3.0;
+  const double vol_dt = p.h * p.h * p.h * p.dt;
+  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
+  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
+  c.noise_diag = std::sqrt(2.0) * S;
+  c.noise_trace = std::sqrt(2.0) * (B - S / 3.0);
+  c.noise_edge = S;
+  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
+  c.wave_axis = p.wave_axis;
+  c.plane_index = p.plane_index;
+  c.force_amp = ctx->force_amp;
+  c.omega = ctx->omega;
+  c.phase = p.wave_phase;
+  c.cos_table = ctx->cos_table;
+  c.k0 = uint32_t(p.seed & 0xffffffffull);
+  c.k1 = uint32_t(p.seed >> 32);
+  c.box = p.box;
+  c.noise = p.kT > 0.0;
+  return c;
+}
+
+size_t fluid_num_partials(const ic_ctx *ctx) {
+  const dim3 g = ctx->p.precision == IC_FP32 ? stage_grid<float>(ctx) : stage_grid<double>(ctx);
+  return std::max<size_t>(size_t(g.x) * g.y * g.z, size_t(kRedBlocks) * 4);
+}
+
+cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+                         void *const out[4]) {
+  if (ctx->p.precision == IC_FP32) return launch_stage_r<float>(ctx, stage, in_s, in_n, out);
+  return launch_stage_r<double>(ctx, stage, in_s, in_n, out);
+}
+
+cudaError_t launch_thermal(ic_ctx *ctx, uint64_t seed, int add) {
+  const ic_grid_params &p = ctx->p;
+  const RngKey key{uint32_t(seed & 0xffffffffull), uint32_t(seed >> 32), p.box};
+  const double vol = p.h * p.h * p.h;
+  const double sd_rho = std::sqrt(p.rho0 * p.kT / (p.c * p.c * vol));
+  const double sd_g = std::sqrt(p.rho0 * p.kT / vol);
+  double *mean = ctx->d.scalars + 4;   // scratch slots 4..7
+  k_thermal_sums<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(key, ctx->cells, sd_rho, sd_g, ctx->d.partials);
+  k_reduce_partials<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d.partials, kRedBlocks, 4, mean,
+                                                        1.0 / double(ctx->cells));
+  void *const *U = ctx->U[ctx->cur];
+  if (p.precision == IC_FP32)
+    k_thermal_apply<float><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
+        key, ctx->cells, sd_rho, sd_g, mean, add, (float *)U[0], (float *)U[1], (float *)U[2], (float *)U[3]);
+  else
+    k_thermal_apply<double><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
+        key, ctx->cells, sd_rho, sd_g, mean, add, (double *)U[0], (double *)U[1], (double *)U[2], (double *)U[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_sums(ic_ctx *ctx, void *const U[4], double *dev_out4) {
+  const ic_grid_params &p = ctx->p;
+  const double *tab = ctx->cos_table;
+  if (p.precision == IC_FP32)
+    k_field_sums<float><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
+        p.nx, p.ny, p.nz, p.wave_axis, tab, (const float *)U[0], (const float *)U[1], (const float *)U[2],
+        (const float *)U[3], ctx->d.partials);
+  else
+    k_field_sums<double><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
+        p.nx, p.ny, p.nz, p.wave_axis, tab, (const double *)U[0], (const double *)U[1],
+        (const double *)U[2], (const double *)U[3], ctx->d.partials);
+  k_reduce_partials<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d.partials, kRedBlocks, 4, dev_out4, 1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_end_of_step(ic_ctx *ctx) {
+  const dim3 g = ctx->p.precision == IC_FP32 ? stage_grid<float>(ctx) : stage_grid<double>(ctx);
+  const int nb = int(g.x * g.y * g.z);
+  const int has_mode = 1;
+  k_end_of_step<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d.partials, nb, 1.0 / double(ctx->cells), has_mode,
+                                                    ctx->d.step, ctx->d.weights, ctx->d.scalars,
+                                                    ctx->d.status);
+  return cudaGetLastError();
+}
+
+}  // namespace ic

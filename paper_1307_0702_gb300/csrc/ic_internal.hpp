@@ -1,0 +1,115 @@
+// Host-side context of libic and the launch interfaces between its files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ic.h"
+
+namespace ic {
+
+constexpr int kMaxNeighbours = 64;     // per-particle neighbour table width
+constexpr double kSkin = 1.0;          // neighbour-list skin in units of h
+constexpr int kStatusNonfinite = 1;    // device status bits
+constexpr int kStatusNbrOverflow = 2;
+constexpr int kStatusSkin = 4;
+
+// Per-stage constants of the fluid kernel (derived on the host in FP64).
+struct FluidConsts {
+  int nx, ny, nz;
+  double rho0, c2, inv_h, dt, eta, lam2;        // lam2 = zeta - 2 eta / 3
+  double noise_diag, noise_trace, noise_edge;   // sqrt2 S, sqrt2 (B - S/3), S
+  int forcing, wave_axis, plane_index;
+  double force_amp, omega, phase;               // P (or Delta p0), omega, phi
+  const double *cos_table;                      // cos(k x_i) along the wave axis
+  uint32_t k0, k1, box;                         // Philox key and box
+  int noise;
+};
+
+// Device pointers of the particle arrays; element type of the void* arrays
+// is the context's real type (double or float).
+struct ParticleStore {
+  int n = 0, cap = 0;
+  double *q = nullptr, *q_eq = nullptr, *q_build = nullptr, *q_half = nullptr;  // n*3
+  double *acc = nullptr;     // n*6: sum w F, sum w lambda
+  void *u = nullptr;         // n*3
+  void *m_e = nullptr, *eps = nullptr, *k_s = nullptr;   // n
+  void *w = nullptr;         // n*18: centre weights [axis][3], own-axis face weights [axis][3]
+  void *jv_n = nullptr;      // n*3: J^{n+1/2} v^n
+  void *omega = nullptr;     // 2*n: Omega for the current / next RK stage
+  void *force = nullptr;     // n*3: F^{n+1/2}
+  void *dg = nullptr;        // n*3: impulse dg
+  void *lam = nullptr;       // n*3: lambda
+  int *base = nullptr;       // n*6: centre base (x,y,z), own-axis face base (x,y,z)
+  int *nbr = nullptr;        // n*kMaxNeighbours, ascending indices
+  int *nnbr = nullptr;       // n
+};
+
+struct Device {
+  int64_t *step = nullptr;        // [0] step counter n, [1] step of weights[0], [2] number of weights
+  double *weights = nullptr;      // averaging weights of the current ic_step call (0 outside)
+  double *scalars = nullptr;      // [0] sum w, [1] sum w A^2, [2] A of the last step
+  int *status = nullptr;          // error bits
+  int *rebuild = nullptr;         // neighbour list must be rebuilt
+  double *partials = nullptr;     // per-CTA partial sums
+};
+
+}  // namespace ic
+
+struct ic_ctx {
+  ic_grid_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t cells = 0;
+  size_t real_size = 8;
+  void *U[3][4] = {};      // three state buffers (delta rho, gx, gy, gz)
+  int cur = 0;             // buffer holding U^n (0 or 1); buffer 2 holds U^{n+1/2}
+  ic::Device d{};
+  ic::ParticleStore ps{};
+  double *cos_table = nullptr;
+  size_t n_partials = 0;
+  int weights_cap = 0;
+  int64_t host_step = 0;
+  int64_t host_wcount = 0;          // weights count currently on the device
+  double *staging = nullptr;        // pinned host staging for weights (cap + 3)
+  cudaEvent_t staging_done = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
+  std::string err;
+  double omega = 0, force_amp = 0, kwave = 0;
+  // kernel timing (ic_profile): event pairs per kernel class
+  bool profiling = false;
+  struct Timed {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next = 0;
+  // every device allocation, for ic_destroy
+  void *allocs[64] = {};
+  size_t alloc_bytes[64] = {};
+  int n_allocs = 0;
+};
+
+namespace ic {
+void *dev_alloc(ic_ctx *ctx, size_t bytes);
+void dev_free(ic_ctx *ctx, void *p);
+
+// fluid (ic_fluid.cu)
+FluidConsts fluid_consts(const ic_ctx *ctx);
+size_t fluid_num_partials(const ic_ctx *ctx);
+cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+                         void *const out[4]);
+cudaError_t launch_thermal(ic_ctx *ctx, uint64_t seed, int add);
+cudaError_t launch_field_sums(ic_ctx *ctx, void *const state[4], double *dev_out4);
+cudaError_t launch_end_of_step(ic_ctx *ctx);
+
+// particles (ic_particles.cu)
+enum ParticlePhase { kHalfStep = 0, kStageCorrection = 1, kImpulse = 2, kSpread = 3, kFinal = 4 };
+cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *const cur[4],
+                             void *const tgt[4]);
+cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]);
+cudaError_t launch_particle_momentum(ic_ctx *ctx, double *dev_out3);
+}  // namespace ic

@@ -1,0 +1,204 @@
+"""Python binding of libic: the C calls of include/ic.h with numpy marshalling.
+
+Every step of the method runs in the CUDA library; this module only converts
+arguments.  Device memory comes from PyTorch's caching allocator and work is
+ordered on a torch CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import IC_FORCE_MODE, IC_FORCE_NONE, IC_FORCE_PLANE, IC_FP32, IC_FP64
+
+_FORCING = {"none": IC_FORCE_NONE, "mode": IC_FORCE_MODE, "plane": IC_FORCE_PLANE}
+_PRECISION = {"fp64": IC_FP64, "fp32": IC_FP32}
+
+
+class ICError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libic error {status}: {message}")
+        self.status = status
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_lib.PD)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a if shape is None else a.reshape(shape)
+
+
+class Grid:
+    """One simulation box (an ic_ctx).
+
+    params: dict with the keys of ``workloads.grid_params`` (nx, ny, nz, h,
+    rho0, c, eta, zeta, kT, dt, seed, forcing, wave_axis, wave_amp,
+    wave_nlambda, plane_index, wave_phase, precision) plus optional ``box``.
+    """
+
+    def __init__(self, params, device=None, stream=None, allocator="torch"):
+        import torch
+
+        self._lib = _lib.load()
+        self.params = dict(params)
+        self.shape = (int(params["nz"]), int(params["ny"]), int(params["nx"]))
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        gp = _lib.GridParams()
+        for k in ("nx", "ny", "nz", "wave_axis", "wave_nlambda", "plane_index"):
+            setattr(gp, k, int(params.get(k, 0)))
+        for k in ("h", "rho0", "c", "eta", "zeta", "kT", "dt", "wave_amp", "wave_phase"):
+            setattr(gp, k, float(params.get(k, 0.0)))
+        gp.wave_nlambda = int(params.get("wave_nlambda", 1))
+        gp.seed = int(params.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+        gp.box = int(params.get("box", 0))
+        gp.precision = _PRECISION[params.get("precision", "fp64")]
+        gp.forcing = _FORCING[params.get("forcing", "none")]
+        gp.stream = self.stream.cuda_stream
+        if allocator == "torch":
+            dev, strm = self.device.index, self.stream
+
+            def _alloc(nbytes, _ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+
+            def _free(ptr, _nbytes, _ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = _lib.ALLOC_FN(_alloc)
+            self._free_cb = _lib.FREE_FN(_free)
+            gp.alloc, gp.free = self._alloc_cb, self._free_cb
+        self._gp = gp
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self._lib.ic_create_grid(ctypes.byref(gp), ctypes.byref(self._ctx))
+        if st != 0:
+            raise ICError(st, "ic_create_grid rejected the parameters" if st == -1 else "ic_create_grid failed")
+        self.n_particles = 0
+
+    # ------------------------------------------------------------------ utils
+    def _check(self, st):
+        if st != 0:
+            msg = self._lib.ic_last_error(self._ctx)
+            raise ICError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.ic_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ state
+    def set_state(self, rho, g=None):
+        rho = _f64(rho, self.shape)
+        g = [None] * 3 if g is None else [_f64(a, self.shape) for a in g]
+        self._check(self._lib.ic_set_state(self._ctx, _ptr(rho), _ptr(g[0]), _ptr(g[1]), _ptr(g[2])))
+
+    def get_state(self):
+        rho = np.empty(self.shape)
+        g = [np.empty(self.shape) for _ in range(3)]
+        self._check(self._lib.ic_get_state(self._ctx, _ptr(rho), _ptr(g[0]), _ptr(g[1]), _ptr(g[2])))
+        return rho, g
+
+    def init_thermal(self, seed, add=True):
+        self._check(self._lib.ic_init_thermal(self._ctx, int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if add else 0))
+
+    def add_particles(self, q, m_e, kappa_ratio, k_spring=None, u=None):
+        q = _f64(q).reshape(-1, 3)
+        n = q.shape[0]
+        m_e = _f64(np.broadcast_to(np.asarray(m_e, float), (n,)))
+        kr = _f64(np.broadcast_to(np.asarray(kappa_ratio, float), (n,)))
+        ks = None if k_spring is None else _f64(np.broadcast_to(np.asarray(k_spring, float), (n,)))
+        u = None if u is None else _f64(u).reshape(n, 3)
+        first = ctypes.c_int()
+        self._check(self._lib.ic_add_particles(self._ctx, n, _ptr(q), _ptr(u), _ptr(m_e), _ptr(kr), _ptr(ks),
+                                               ctypes.byref(first)))
+        self.n_particles += n
+        return first.value
+
+    def step(self, nsteps=1, weights=None):
+        w = None if weights is None else _f64(weights)
+        if w is not None and w.size != nsteps:
+            raise ValueError("weights must have nsteps entries")
+        self._check(self._lib.ic_step(self._ctx, int(nsteps), _ptr(w)))
+
+    def sync(self):
+        self._check(self._lib.ic_sync(self._ctx))
+
+    def forces(self, out=None):
+        """(lambda, u, q), each (n, 3); ``out`` may give preallocated arrays."""
+        n = self.n_particles
+        lam, u, q = out if out is not None else (np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3)))
+        self._check(self._lib.ic_forces(self._ctx, _ptr(lam), _ptr(u), _ptr(q)))
+        return lam, u, q
+
+    def time_average(self, reset=False):
+        """(<F_spring>_w, <lambda>_w, <A^2>_w)."""
+        n = self.n_particles
+        f, lam, a2 = np.empty((n, 3)), np.empty((n, 3)), ctypes.c_double()
+        self._check(self._lib.ic_time_average(self._ctx, _ptr(f), _ptr(lam), ctypes.byref(a2), 1 if reset else 0))
+        return f, lam, a2.value
+
+    def stats(self):
+        """(total momentum (3,), driven-mode amplitude A, step)."""
+        p = np.empty(3)
+        a = ctypes.c_double()
+        s = ctypes.c_int64()
+        self._check(self._lib.ic_stats(self._ctx, _ptr(p), ctypes.byref(a), ctypes.byref(s)))
+        return p, a.value, s.value
+
+    def checkpoint(self):
+        size = ctypes.c_size_t()
+        self._check(self._lib.ic_checkpoint(self._ctx, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(self._lib.ic_checkpoint(self._ctx, buf, ctypes.byref(size)))
+        return buf.raw[:size.value]
+
+    def restore(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self._lib.ic_restore(self._ctx, buf, len(blob)))
+        self.n_particles = int(np.frombuffer(blob[28:32], dtype=np.int32)[0])
+
+    def profile(self, enable=True):
+        """Kernel timing on/off (graphs are off while it is on)."""
+        self._check(self._lib.ic_profile(self._ctx, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        """{class: (ms, launches)} for 'fluid', 'particles', 'end' since the last reset."""
+        ms = np.empty(3)
+        n = (ctypes.c_int64 * 3)()
+        self._check(self._lib.ic_profile_read(self._ctx, _ptr(ms), n, 1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("fluid", "particles", "end"))}
+
+    def views(self):
+        """Zero-copy torch tensors over the current device state (delta rho, g, q)."""
+        import torch
+
+        v = _lib.Views()
+        self._check(self._lib.ic_device_views(self._ctx, ctypes.byref(v)))
+        typestr = "<f4" if v.precision == IC_FP32 else "<f8"
+
+        class _Arr:
+            def __init__(self, ptr, shape, ts):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": ts, "data": (ptr, False),
+                                                 "version": 3, "strides": None}
+
+        out = {k: torch.as_tensor(_Arr(getattr(v, k), self.shape, typestr), device=self.device)
+               for k in ("drho", "gx", "gy", "gz")}
+        if v.n_particles:
+            out["q"] = torch.as_tensor(_Arr(v.q, (v.n_particles, 3), "<f8"), device=self.device)
+        return out

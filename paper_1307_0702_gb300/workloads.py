@@ -17,13 +17,14 @@ KERNEL_VOLUME_CELLS = 8.0   # V / h^3 of the 3-point kernel
 
 def grid_params(n, *, h=1.0, rho0=1.0, c=4.0, eta=0.5, zeta=0.0, kT=0.0, dt=None,
                 seed=0, forcing="mode", wave_axis=0, wave_amp=1e-3, wave_nlambda=1,
-                precision="fp64", plane_index=0):
+                precision="fp64", plane_index=0, wave_phase=0.0):
     nx, ny, nz = (n, n, n) if np.isscalar(n) else n
     return dict(nx=int(nx), ny=int(ny), nz=int(nz), h=float(h), rho0=float(rho0), c=float(c),
                 eta=float(eta), zeta=float(zeta), kT=float(kT),
                 dt=float(0.1 * h / c if dt is None else dt), seed=int(seed),
                 forcing=forcing, wave_axis=int(wave_axis), wave_amp=float(wave_amp),
-                wave_nlambda=int(wave_nlambda), precision=precision, plane_index=int(plane_index))
+                wave_nlambda=int(wave_nlambda), precision=precision, plane_index=int(plane_index),
+                wave_phase=float(wave_phase))
 
 
 def standing_wave_fields(gp):
@@ -37,6 +38,23 @@ def standing_wave_fields(gp):
     bshape[2 - gp["wave_axis"]] = n_ax
     rho = gp["rho0"] + np.broadcast_to(prof.reshape(bshape), shape)
     return np.ascontiguousarray(rho), [np.zeros(shape) for _ in range(3)]
+
+
+def velocity_phase_wave_fields(gp):
+    """The same standing wave a quarter period later: rho = rho0 and
+    g = c A sin(k x) on the faces normal to the wave axis (drive phase pi/2).
+    A particle started at rest in this state oscillates about its start."""
+    shape = (gp["nz"], gp["ny"], gp["nx"])
+    ax = gp["wave_axis"]
+    n_ax = (gp["nx"], gp["ny"], gp["nz"])[ax]
+    k = 2.0 * np.pi * gp["wave_nlambda"] / (n_ax * gp["h"])
+    xf = (np.arange(n_ax) + 0.5 - gp["plane_index"]) * gp["h"]
+    prof = gp["c"] * gp["wave_amp"] * np.sin(k * xf)
+    bshape = [1, 1, 1]
+    bshape[2 - ax] = n_ax
+    g = [np.zeros(shape) for _ in range(3)]
+    g[ax] = np.ascontiguousarray(np.broadcast_to(prof.reshape(bshape), shape))
+    return np.full(shape, gp["rho0"]), g
 
 
 def random_fields(gp, seed, amp_rho=1e-3, amp_g=1e-3):
@@ -92,18 +110,25 @@ def place_uniform(n_particles, lengths, seed, min_sep=0.0):
     return out
 
 
-def single_particle_config(n=32, steps=2000):
-    """Deterministic standing wave with one tethered particle (kT = 0, FP64).
+def single_particle_config(n=32, steps=2000, k_spring=1.0, mirror=False, mass_ratio=1.5,
+                           kappa_ratio=0.5):
+    """Deterministic standing wave with a tethered particle (kT = 0, FP64).
 
     32^3 grid, wave along x with density amplitude 1e-3 rho0 and wavelength L;
     one particle at (L/8, L/2, L/2) (sin 2kx = 1) with m_p = 1.5 rho0 V and
-    kappa_p = 0.5 kappa_f, tethered by a spring k_s = 1; seed 0.
+    kappa_p = 0.5 kappa_f, tethered by a spring; seed 0.  ``mirror`` adds its
+    mirror image at (7L/8, L/2, L/2), whose spring force is opposite, so the
+    springs inject no net momentum (the paper's two-particle layout, Sec. 6).
+    The drive phase is pi/2 so that ``velocity_phase_wave_fields`` is the
+    matching initial state.
     """
-    gp = grid_params(n, wave_amp=1e-3, seed=0)
+    gp = grid_params(n, wave_amp=1e-3, seed=0, wave_phase=0.5 * np.pi)
     L = n * gp["h"]
-    parts = dict(q=np.array([[L / 8.0, L / 2.0, L / 2.0]]),
-                 m_e=np.array([0.5 * KERNEL_VOLUME_CELLS * gp["rho0"] * gp["h"] ** 3]),
-                 kappa_ratio=np.array([0.5]), k_spring=np.array([1.0]))
+    q = [[L / 8.0, L / 2.0, L / 2.0]] + ([[7.0 * L / 8.0, L / 2.0, L / 2.0]] if mirror else [])
+    npart = len(q)
+    vol = KERNEL_VOLUME_CELLS * gp["h"] ** 3
+    parts = dict(q=np.array(q), m_e=np.full(npart, (mass_ratio - 1.0) * gp["rho0"] * vol),
+                 kappa_ratio=np.full(npart, kappa_ratio), k_spring=np.full(npart, k_spring))
     return gp, parts, steps
 
 
