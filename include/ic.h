@@ -94,7 +94,8 @@ typedef struct {
   void *drho, *gx, *gy, *gz;
   int precision;
   int n_particles;
-  double *q;            /* n*3 device positions (FP64 in both precisions) */
+  void *q;              /* n*3 device positions: FP64 length units (IC_FP64) or 64-bit
+                           fixed point q/h in units of 2^-40 (IC_FP32) */
 } ic_views;
 
 /* Creates a context: validates params (IC_ERR_ARG), allocates the three
@@ -136,6 +137,11 @@ ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w);
 /* Latest step's particle data to host n*3 arrays (NULL skips): lambda, the
  * fluid force on each particle (substep 4: dg = dt (lambda + F)); u; q. */
 ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q);
+
+/* Kernel-averaged fluid density J rho^{n+1} at q^{n+1/2} of the latest step
+ * (n values; m_f = V J rho, App. A.2 substep 4), to a host array.  Its
+ * equilibrium variance is rho0 kT / (c_p^2 V) (Eq. (eq:densityVariance)). */
+ic_status ic_particle_density(ic_ctx *ctx, double *jrho);
 
 /* Weighted time averages since the last reset: spring force <F>_w and fluid
  * force <lambda>_w (n*3 each, NULL skips) and <A^2>_w of the driven-mode

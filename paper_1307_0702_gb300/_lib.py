@@ -43,6 +43,7 @@ SIGNATURES = {
     "ic_add_particles": (c_int, [c_void_p, c_int, PD, PD, PD, PD, PD, POINTER(c_int)]),
     "ic_step": (c_int, [c_void_p, c_int, PD]),
     "ic_forces": (c_int, [c_void_p, PD, PD, PD]),
+    "ic_particle_density": (c_int, [c_void_p, PD]),
     "ic_time_average": (c_int, [c_void_p, PD, PD, PD, c_int]),
     "ic_stats": (c_int, [c_void_p, PD, PD, POINTER(c_int64)]),
     "ic_sync": (c_int, [c_void_p]),

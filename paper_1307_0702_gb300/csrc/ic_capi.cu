@@ -18,7 +18,7 @@ namespace ic {
 
 void *dev_alloc(ic_ctx *ctx, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  if (ctx->n_allocs >= 64) return nullptr;
+  if (ctx->n_allocs >= 128) return nullptr;
   void *p = nullptr;
   if (ctx->p.alloc) {
     p = ctx->p.alloc(bytes, ctx->p.alloc_ctx);
@@ -124,14 +124,18 @@ cudaError_t enqueue_step(ic_ctx *ctx, int cur) {
   do {                                      \
     if ((e = (x)) != cudaSuccess) return e; \
   } while (0)
+  const bool springs = parts && ctx->any_spring;
   if (parts) IC_TRY(part(ic::kHalfStep, 0, U0));
+  if (parts) IC_TRY(part(ic::kPressure, 0, U0));
   IC_TRY(fluid(0, U0, U0, U1));
-  if (parts) IC_TRY(part(ic::kStageCorrection, 0, U1));
+  if (springs) IC_TRY(part(ic::kForce, 0, U1));
+  if (parts) IC_TRY(part(ic::kPressure, 1, U1));
   IC_TRY(fluid(1, U1, U0, U2));
-  if (parts) IC_TRY(part(ic::kStageCorrection, 1, U2));
+  if (springs) IC_TRY(part(ic::kForce, 1, U2));
+  if (parts) IC_TRY(part(ic::kPressure, 2, U2));
   IC_TRY(fluid(2, U2, U0, U1));
   if (parts) {
-    IC_TRY(part(ic::kStageCorrection, 2, U1));
+    if (springs) IC_TRY(part(ic::kForce, 2, U1));
     IC_TRY(part(ic::kImpulse, 0, U1));
     IC_TRY(part(ic::kSpread, 0, U1));
     IC_TRY(part(ic::kFinal, 0, U1));
@@ -207,8 +211,9 @@ std::vector<PArray> particle_arrays(ic_ctx *ctx) {
   return {{(void **)&s.q, 24},       {(void **)&s.q_eq, 24},     {(void **)&s.q_build, 24},
           {(void **)&s.q_half, 24},  {(void **)&s.acc, 48},      {&s.u, 3 * r},
           {&s.m_e, r},               {&s.eps, r},                {&s.k_s, r},
-          {&s.w, 18 * r},            {&s.jv_n, 3 * r},           {&s.omega, 2 * r},
+          {&s.w, 18 * r},            {&s.jv_n, 3 * r},
           {&s.force, 3 * r},         {&s.dg, 3 * r},             {&s.lam, 3 * r},
+          {&s.jrho, r},
           {(void **)&s.base, 6 * sizeof(int)},
           {(void **)&s.nbr, ic::kMaxNeighbours * sizeof(int)},
           {(void **)&s.nnbr, sizeof(int)}};
@@ -232,6 +237,15 @@ ic_status grow_particles(ic_ctx *ctx, int need) {
   }
   s.cap = cap;
   invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+ic_status upload_drive(ic_ctx *ctx, int64_t step) {
+  double d[3];
+  ic::drive_amplitudes(ctx, step, d);
+  const float f[3] = {float(d[0]), float(d[1]), float(d[2])};
+  IC_CUDA(ctx, cudaMemcpy(ctx->drive, d, sizeof(d), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy(ctx->drive_f, f, sizeof(f), cudaMemcpyHostToDevice));
   return IC_OK;
 }
 
@@ -284,24 +298,40 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
       if (!ctx->U[b][j]) return bail(IC_ERR_OOM);
       if (cudaMemsetAsync(ctx->U[b][j], 0, fbytes, ctx->stream) != cudaSuccess) return bail(IC_ERR_CUDA);
     }
+  ctx->pp = dev_alloc(ctx, fbytes);
+  if (!ctx->pp) return bail(IC_ERR_OOM);
+  if (p.kT > 0.0)
+    for (int j = 0; j < 12; ++j)
+      if (!(ctx->noise[j] = dev_alloc(ctx, fbytes))) return bail(IC_ERR_OOM);
+  if (cudaMemsetAsync(ctx->pp, 0, fbytes, ctx->stream) != cudaSuccess) return bail(IC_ERR_CUDA);
   ctx->n_partials = ic::fluid_num_partials(ctx);
   ctx->d.partials = (double *)dev_alloc(ctx, ctx->n_partials * sizeof(double));
   ctx->d.step = (int64_t *)dev_alloc(ctx, 4 * sizeof(int64_t));
   ctx->d.scalars = (double *)dev_alloc(ctx, 16 * sizeof(double));
   ctx->d.status = (int *)dev_alloc(ctx, 2 * sizeof(int));
   ctx->cos_table = (double *)dev_alloc(ctx, n_ax * sizeof(double));
+  ctx->cos_table_f = (float *)dev_alloc(ctx, n_ax * sizeof(float));
+  ctx->drive = (double *)dev_alloc(ctx, 3 * sizeof(double));
+  ctx->drive_f = (float *)dev_alloc(ctx, 3 * sizeof(float));
   ctx->weights_cap = 1024;
   ctx->d.weights = (double *)dev_alloc(ctx, ctx->weights_cap * sizeof(double));
-  if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->cos_table || !ctx->d.weights)
+  if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->cos_table || !ctx->d.weights ||
+      !ctx->cos_table_f || !ctx->drive || !ctx->drive_f)
     return bail(IC_ERR_OOM);
   if (cudaMallocHost(&ctx->staging, (ctx->weights_cap + 3) * sizeof(double)) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(IC_ERR_OOM);
   ctx->d.rebuild = ctx->d.status + 1;
   std::vector<double> tab(n_ax);
-  for (int i = 0; i < n_ax; ++i) tab[i] = std::cos(ctx->kwave * i * p.h);
+  std::vector<float> tab_f(n_ax);
+  for (int i = 0; i < n_ax; ++i) {
+    tab[i] = std::cos(ctx->kwave * i * p.h);
+    tab_f[i] = float(tab[i]);
+  }
   const int zero_rebuild[2] = {0, 1};
-  if (cudaMemcpyAsync(ctx->cos_table, tab.data(), n_ax * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
+  if (upload_drive(ctx, 0) != IC_OK ||
+      cudaMemcpyAsync(ctx->cos_table, tab.data(), n_ax * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
+      cudaMemcpyAsync(ctx->cos_table_f, tab_f.data(), n_ax * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaMemsetAsync(ctx->d.step, 0, 4 * sizeof(int64_t), ctx->stream) ||
       cudaMemsetAsync(ctx->d.scalars, 0, 16 * sizeof(double), ctx->stream) ||
       cudaMemsetAsync(ctx->d.weights, 0, ctx->weights_cap * sizeof(double), ctx->stream) ||
@@ -376,11 +406,15 @@ ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u,
     }
     eps[i] = p.c * p.c * (1.0 / kappa_ratio[i] - 1.0);   // epsilon_pf, Eqs. (part_svel), (ke)
     if (k_spring) ks[i] = k_spring[i];
+    if (ks[i] != 0.0) ctx->any_spring = true;
   }
   const size_t r = ctx->real_size;
-  IC_CUDA(ctx, cudaMemcpy(s.q + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
-  IC_CUDA(ctx, cudaMemcpy(s.q_eq + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
-  IC_CUDA(ctx, cudaMemcpy(s.q_build + 3 * first, qw.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  std::vector<long long> qdev(3 * size_t(n));   // 8 bytes per component in both representations
+  ic::positions_to_device(ctx, qw.data(), 3 * size_t(n), qdev.data());
+  IC_CUDA(ctx, cudaMemcpy((char *)s.q + 24 * size_t(first), qdev.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy((char *)s.q_eq + 24 * size_t(first), qdev.data(), 24 * size_t(n), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, cudaMemcpy((char *)s.q_build + 24 * size_t(first), qdev.data(), 24 * size_t(n),
+                          cudaMemcpyHostToDevice));
   st = upload_real(ctx, (char *)s.m_e + r * first, m_e, 0.0, n);
   if (!st) st = upload_real(ctx, (char *)s.eps + r * first, eps.data(), 0.0, n);
   if (!st) st = upload_real(ctx, (char *)s.k_s + r * first, ks.data(), 0.0, n);
@@ -468,7 +502,21 @@ ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q) {
     if (lambda) st = download_real(ctx, lambda, ctx->ps.lam, 0.0, n3);
     if (!st && u) st = download_real(ctx, u, ctx->ps.u, 0.0, n3);
     if (st) return st;
-    if (q) IC_CUDA(ctx, cudaMemcpyAsync(q, ctx->ps.q, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (q) {
+      std::vector<long long> qdev(n3);
+      IC_CUDA(ctx, cudaMemcpyAsync(qdev.data(), ctx->ps.q, n3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      ic::positions_to_host(ctx, qdev.data(), n3, q);
+    }
+  }
+  return check_device_status(ctx);
+}
+
+ic_status ic_particle_density(ic_ctx *ctx, double *jrho) {
+  if (!ctx || !jrho) return IC_ERR_ARG;
+  if (ctx->ps.n > 0) {
+    ic_status st = download_real(ctx, jrho, ctx->ps.jrho, 0.0, size_t(ctx->ps.n));
+    if (st) return st;
   }
   return check_device_status(ctx);
 }
@@ -599,11 +647,25 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
     in += it.len;
   }
   if (n) IC_CUDA(ctx, cudaMemcpy(s.q_build, s.q, 24 * n, cudaMemcpyDeviceToDevice));
+  IC_CUDA(ctx, cudaMemset(ctx->pp, 0, fb));
+  {
+    // a tether anywhere switches the stage force source on
+    const char *ks = static_cast<const char *>(buf) + sizeof(hd) + 4 * fb + n * (24 + 24 + 48) + n * r * (3 + 1 + 1);
+    ctx->any_spring = false;
+    for (size_t i = 0; i < n; ++i) {
+      double v = (r == 4) ? double(reinterpret_cast<const float *>(ks)[i]) : reinterpret_cast<const double *>(ks)[i];
+      if (v != 0.0) ctx->any_spring = true;
+    }
+  }
   ctx->host_step = hd.step;
   ctx->host_wcount = 0;
   const int64_t steps[3] = {hd.step, hd.step, 0};
   IC_CUDA(ctx, cudaMemcpy(ctx->d.step, steps, sizeof(steps), cudaMemcpyHostToDevice));
   IC_CUDA(ctx, cudaMemcpy(ctx->d.scalars, hd.scalars, sizeof(hd.scalars), cudaMemcpyHostToDevice));
+  {
+    const ic_status st3 = upload_drive(ctx, hd.step);
+    if (st3) return st3;
+  }
   const int st2[2] = {0, 1};
   IC_CUDA(ctx, cudaMemcpy(ctx->d.status, st2, sizeof(st2), cudaMemcpyHostToDevice));
   invalidate_graphs(ctx);

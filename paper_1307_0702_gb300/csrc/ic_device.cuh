@@ -11,8 +11,9 @@
 // Box-Muller pairs: (n_2i, n_2i+1) = r (cos 2 pi u_2i+1, sin 2 pi u_2i+1),
 // r = sqrt(-2 ln u_2i).  The FP64 path builds 52-bit uniforms
 // u = (2 m + 1) 2^-53, m = (hi << 20) | (lo >> 12); the FP32 path uses the
-// high word alone, u = (hi + 1/2) 2^-32, so its normals follow the FP64 ones
-// to about 1e-7 and need only blocks 0-2.
+// high words alone (radius uniform (hi + 1/2) 2^-32, angle uniform from the
+// top 23 bits), so its normals follow the FP64 ones to about 1e-6 and need
+// only blocks 0-2.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,9 +30,10 @@ constexpr uint32_t kPurposeThermal = 1u;
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    // one widening multiply gives both halves of each 64-bit product
+    const uint64_t p0 = uint64_t(kPhiloxM0) * c.x;
+    const uint64_t p1 = uint64_t(kPhiloxM1) * c.z;
+    c = make_uint4(uint32_t(p1 >> 32) ^ c.y ^ k0, uint32_t(p1), uint32_t(p0 >> 32) ^ c.w ^ k1, uint32_t(p0));
     k0 += kPhiloxW0;
     k1 += kPhiloxW1;
   }
@@ -61,11 +63,14 @@ __device__ __forceinline__ void box_muller(double u1, double u2, double &z0, dou
 }
 
 __device__ __forceinline__ void box_muller_f32(uint32_t h1, uint32_t h2, float &z0, float &z1) {
+  // radius uniform u1 = (h1 + 1/2) 2^-32 resolved down to 2^-33 (tails to 6.8 sigma)
   const float u1 = __fmaf_rn(__uint2float_rn(h1), 0x1p-32f, 0x1p-33f);
-  const float t = __fmaf_rn(__uint2float_rn(h2), 0x1p-32f, 0x1p-33f) - 0.5f;
-  const float r = sqrtf(-2.0f * __logf(u1));
+  // angle uniform from the top 23 bits: t = u2 - 1/2 in [-1/2, 1/2)
+  const float t = __uint_as_float(0x3f800000u | (h2 >> 9)) - 1.5f;
+  const float x = fmaxf(-2.0f * __logf(u1), 1e-30f);
+  const float r = x * rsqrtf(x);
   float s, c;
-  __sincosf(6.2831853071795865f * t, &s, &c);   // 2 pi u = 2 pi t + pi
+  __sincosf(6.2831853071795865f * t, &s, &c);   // 2 pi u2 = 2 pi t + pi
   z0 = -r * c;
   z1 = -r * s;
 }
@@ -119,6 +124,37 @@ __device__ __forceinline__ void stress_normals(const RngKey &key, uint32_t cell,
   }
 }
 
+// Both streams of one cell and step, uncombined: W_A and W_B, each ordered
+// xx, yy, zz, xy, xz, yz.
+__device__ __forceinline__ void stress_normals_ab(const RngKey &key, uint32_t cell, uint32_t step, double a[6],
+                                                  double b[6]) {
+  const uint4 h0 = philox_block(key, cell, step, kPurposeStress, 0);
+  const uint4 h1 = philox_block(key, cell, step, kPurposeStress, 1);
+  const uint4 h2 = philox_block(key, cell, step, kPurposeStress, 2);
+  const uint4 l0 = philox_block(key, cell, step, kPurposeStress, 3);
+  const uint4 l1 = philox_block(key, cell, step, kPurposeStress, 4);
+  const uint4 l2 = philox_block(key, cell, step, kPurposeStress, 5);
+  box_muller(uniform52(h0.x, l0.x), uniform52(h0.y, l0.y), a[0], a[1]);
+  box_muller(uniform52(h0.z, l0.z), uniform52(h0.w, l0.w), a[2], a[3]);
+  box_muller(uniform52(h1.x, l1.x), uniform52(h1.y, l1.y), a[4], a[5]);
+  box_muller(uniform52(h1.z, l1.z), uniform52(h1.w, l1.w), b[0], b[1]);
+  box_muller(uniform52(h2.x, l2.x), uniform52(h2.y, l2.y), b[2], b[3]);
+  box_muller(uniform52(h2.z, l2.z), uniform52(h2.w, l2.w), b[4], b[5]);
+}
+
+__device__ __forceinline__ void stress_normals_ab(const RngKey &key, uint32_t cell, uint32_t step, float a[6],
+                                                  float b[6]) {
+  const uint4 h0 = philox_block(key, cell, step, kPurposeStress, 0);
+  const uint4 h1 = philox_block(key, cell, step, kPurposeStress, 1);
+  const uint4 h2 = philox_block(key, cell, step, kPurposeStress, 2);
+  box_muller_f32(h0.x, h0.y, a[0], a[1]);
+  box_muller_f32(h0.z, h0.w, a[2], a[3]);
+  box_muller_f32(h1.x, h1.y, a[4], a[5]);
+  box_muller_f32(h1.z, h1.w, b[0], b[1]);
+  box_muller_f32(h2.x, h2.y, b[2], b[3]);
+  box_muller_f32(h2.z, h2.w, b[4], b[5]);
+}
+
 // ---------------------------------------------------------------- kernel
 // 1D weights of the 3 points nearest to s (in grid units, already shifted by
 // the location-set offset): i0 = floor(s + 1/2), r = s - i0 in [-1/2, 1/2),
@@ -144,6 +180,11 @@ __device__ __forceinline__ int ring_delta(int b, int a, int n) {
   if (2 * d > n) d -= n;
   return d;
 }
+
+// a / b: FP32 uses the fast reciprocal-multiply (2 ulp; operands are face
+// densities near rho0), FP64 the exact division
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 template <typename real>
 __device__ __forceinline__ real warp_sum(real v) {

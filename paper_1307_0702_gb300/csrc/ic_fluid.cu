@@ -9,8 +9,9 @@
 //   (a,b) edge owned by cell i (at r_i + h/2 (e_a + e_b)), v^a = g^a / rho^a with
 //   the face density rho^a = (rho_i + rho_{i+a}) / 2;
 //   advective parts are products of two-point averages; sigma = eta (grad v +
-//   grad v^T) + (zeta - 2 eta/3) div v I; pi = c^2 rho + p_ext (the particle
-//   pressure S Omega enters through a sparse correction, see ic_particles.cu);
+//   grad v^T) + (zeta - 2 eta/3) div v I; pi = c^2 (rho - rho0) + S Omega + p_ext
+//   with the particle pressure S Omega read from a field written by
+//   ic_particles.cu before each stage;
 //   Sigma_aa = sqrt2 S N_aa + sqrt2 (B - S/3) tr N, Sigma_ab = S N_ab with
 //   N = W_A + beta_s W_B (beta = -sqrt3, +sqrt3, 0 for stages 1..3).
 //   Stage s: U_{s+1} = a_s U^n + b_s (U_s + dt dU/dt(U_s, t_s)), (a, b) =
@@ -39,7 +40,10 @@ struct StageArgs {
   const real *__restrict__ s[4];   // U_s
   const real *__restrict__ n[4];   // U^n
   real *__restrict__ o[4];         // U_{s+1}
-  FluidConsts c;
+  const real *__restrict__ pp;     // particle pressure S Omega_s at centres, or null
+  const real *__restrict__ noise_in[6];   // stages 2-3: stored W_s (xx, yy, zz, xy, xz, yz)
+  real *__restrict__ noise_out[12];       // stage 1: stores W_2 = W_A + sqrt3 W_B and W_3 = W_A
+  FluidConsts<real> c;
   const int64_t *step;
   double *partials;                // stage 3: per-CTA sum of delta rho cos(k x)
   int zchunk;
@@ -47,7 +51,7 @@ struct StageArgs {
 
 template <typename real>
 struct PlaneVals {
-  real gx, gy, gz, vx, vy, vz, dr;
+  real gx, gy, gz, vx, vy, vz, dr, pp;
   real nz[6];
 };
 
@@ -55,8 +59,20 @@ constexpr double kStageTime[3] = {0.0, 1.0, 0.5};
 constexpr double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
 constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
 
+// Tile shape and register budget of the FP32 stage kernel (tuned on GB300).
+#ifndef IC_FP32_TILE_Y
+#define IC_FP32_TILE_Y 8
+#endif
+#ifndef IC_FP32_MIN_CTAS
+#define IC_FP32_MIN_CTAS 2
+#endif
+
+// CTAs per SM the register budget is sized for
+template <typename real>
+constexpr int min_ctas() { return sizeof(real) == 4 ? IC_FP32_MIN_CTAS : 1; }
+
 template <typename real, int TX, int TY, int STAGE, bool NOISE>
-__global__ void __launch_bounds__((TX + 2) * (TY + 2))
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     k_rk3_stage(const StageArgs<real> a) {
   constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
   enum { GX = 0, GY, GZ, VX, VY, VZ };
@@ -64,9 +80,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *sm = reinterpret_cast<real *>(smem_raw);
   real *T = sm + 12 * EXY;
-  __shared__ double s_drive;
-
-  const FluidConsts &c = a.c;
+  const FluidConsts<real> &c = a.c;
   const int NX = c.nx, NY = c.ny, NZ = c.nz;
   const int t = threadIdx.x;
   const int ex = t % EX, ey = t / EX;
@@ -80,17 +94,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
   const int eYm = max(ey - 1, 0) * EX + ex, eYp = min(ey + 1, EY - 1) * EX + ex;
   const int z0 = int(blockIdx.z) * a.zchunk;
   const int z1 = min(z0 + a.zchunk, NZ);
+  const auto zwrap = [NZ](int kk) { return kk < 0 ? kk + NZ : (kk >= NZ ? kk - NZ : kk); };
 
   const int64_t step = *a.step;
-  if (t == 0) {
-    const double tt = (double(step) + kStageTime[STAGE]) * c.dt;
-    s_drive = (c.forcing == IC_FORCE_NONE) ? 0.0 : c.force_amp * sin(c.omega * tt + c.phase);
-  }
-
-  const real rho0 = real(c.rho0), half = real(0.5), quarter = real(0.25);
-  const real inv_h = real(c.inv_h), c2 = real(c.c2), eta = real(c.eta), lam2 = real(c.lam2);
+  const real drive = c.drive[STAGE];
+  const real rho0 = c.rho0, half = real(0.5), quarter = real(0.25);
+  const real inv_h = c.inv_h, c2 = c.c2, eta = c.eta, lam2 = c.lam2;
   const real two_eta = real(2) * eta;
-  const real nd = real(c.noise_diag), nt = real(c.noise_trace), ne = real(c.noise_edge);
+  const real nd = c.noise_diag, nt = c.noise_trace, ne = c.noise_edge;
   const real beta = STAGE == 0 ? real(-1.7320508075688772) : (STAGE == 1 ? real(1.7320508075688772) : real(0));
   const RngKey key{c.k0, c.k1, c.box};
   const uint32_t ustep = uint32_t(step);
@@ -98,14 +109,12 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
 
   // cos(k x) along the wave axis (mode amplitude and MODE drive), and the
   // drive profile: cos(k x) (MODE) or the indicator of the driven plane (PLANE)
-  const real cos_xy = c.wave_axis < 2 ? real(c.cos_table[c.wave_axis == 0 ? x : y]) : real(0);
-  auto cosw = [&](int kk) -> real {
-    return c.wave_axis < 2 ? cos_xy : real(c.cos_table[wrap(kk, NZ)]);
-  };
+  const real cos_xy = c.wave_axis < 2 ? c.cos_table[c.wave_axis == 0 ? x : y] : real(0);
+  auto cosw = [&](int kk) -> real { return c.wave_axis < 2 ? cos_xy : c.cos_table[zwrap(kk)]; };
   auto profile = [&](int kk) -> real {
     if (c.forcing == IC_FORCE_MODE) return cosw(kk);
     if (c.forcing == IC_FORCE_PLANE) {
-      const int coord = c.wave_axis == 0 ? x : (c.wave_axis == 1 ? y : wrap(kk, NZ));
+      const int coord = c.wave_axis == 0 ? x : (c.wave_axis == 1 ? y : zwrap(kk));
       return real(coord == c.plane_index ? 1 : 0);
     }
     return real(0);
@@ -113,7 +122,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
 
   auto load = [&](int kk) {
     PlaneVals<real> v;
-    const int k = wrap(kk, NZ);
+    const int k = zwrap(kk);
     const int kp = (k + 1 == NZ) ? 0 : k + 1;
     const size_t i = size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * k);
     const size_t row = size_t(NX) * (size_t(y) + size_t(NY) * k);
@@ -124,11 +133,26 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
     v.gx = a.s[1][i];
     v.gy = a.s[2][i];
     v.gz = a.s[3][i];
-    v.vx = v.gx / (rho0 + half * (v.dr + drx));
-    v.vy = v.gy / (rho0 + half * (v.dr + dry));
-    v.vz = v.gz / (rho0 + half * (v.dr + drz));
-    if (NOISE) {
-      stress_normals(key, uint32_t(i), ustep, STAGE != 2, beta, v.nz);
+    v.pp = a.pp ? a.pp[i] : real(0);
+    v.vx = fdiv(v.gx, rho0 + half * (v.dr + drx));
+    v.vy = fdiv(v.gy, rho0 + half * (v.dr + dry));
+    v.vz = fdiv(v.gz, rho0 + half * (v.dr + drz));
+    if (NOISE && STAGE == 0) {
+      // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
+      real wa[6], wb[6];
+      stress_normals_ab(key, uint32_t(i), ustep, wa, wb);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) v.nz[j] = wa[j] + beta * wb[j];
+      if (interior && kk >= z0 && kk < z1) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          a.noise_out[j][i] = wa[j] + real(1.7320508075688772) * wb[j];
+          a.noise_out[6 + j][i] = wa[j];
+        }
+      }
+    } else if (NOISE) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) v.nz[j] = a.noise_in[j][i];
     } else {
 #pragma unroll
       for (int j = 0; j < 6; ++j) v.nz[j] = real(0);
@@ -150,7 +174,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
   real vz_m = real(0), gz_m = real(0), txz_m = real(0), tyz_m = real(0), tzz_k = real(0);
   real mode_acc = real(0);
   const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
-  const real dt = real(c.dt);
+  const real dt = c.dt;
 
   for (int k = z0 - 1; k < z1; ++k) {
     const PlaneVals<real> Q = load(k + 1);
@@ -158,7 +182,6 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
     __syncthreads();
     const real *Pk = sm + (k & 1) * 6 * EXY;
     const real *Pq = sm + ((k + 1) & 1) * 6 * EXY;
-    const real drive = real(s_drive);
 
     const real gx_xm = Pk[GX * EXY + eXm], vx_xm = Pk[VX * EXY + eXm];
     const real gy_ym = Pk[GY * EXY + eYm], vy_ym = Pk[VY * EXY + eYm];
@@ -170,8 +193,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
 
     const real div_k = ((P.vx - vx_xm) + (P.vy - vy_ym) + (P.vz - vz_m)) * inv_h;
     const real div_k1 = ((Q.vx - vx1_xm) + (Q.vy - vy1_ym) + (Q.vz - P.vz)) * inv_h;
-    const real pk = c2 * P.dr + drive * profile(k);
-    const real pk1 = c2 * Q.dr + drive * profile(k + 1);
+    const real pk = c2 * P.dr + P.pp + drive * profile(k);
+    const real pk1 = c2 * Q.dr + Q.pp + drive * profile(k + 1);
 
     const real tr_k = P.nz[0] + P.nz[1] + P.nz[2];
     const real tr_k1 = Q.nz[0] + Q.nz[1] + Q.nz[2];
@@ -234,16 +257,15 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
 
   if (STAGE == 2) {
     // per-CTA partial of sum (rho - rho0) cos(k x), fixed reduction order
-    double v = double(mode_acc);
-    v = warp_sum(v);
-    __shared__ double s_red[32];
+    const real v = warp_sum(mode_acc);
+    __shared__ real s_red[32];
     const int lane = t & 31, wid = t >> 5;
     if (lane == 0) s_red[wid] = v;
     __syncthreads();
     if (t == 0) {
       double s = 0.0;
       const int nw = (EXY + 31) / 32;
-      for (int j = 0; j < nw; ++j) s += s_red[j];
+      for (int j = 0; j < nw; ++j) s += double(s_red[j]);
       const size_t b = blockIdx.x + size_t(gridDim.x) * (blockIdx.y + size_t(gridDim.y) * blockIdx.z);
       a.partials[b] = s;
     }
@@ -251,10 +273,46 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2))
 }
 
 template <typename real>
+FluidConsts<real> fluid_consts(const ic_ctx *ctx) {
+  const ic_grid_params &p = ctx->p;
+  FluidConsts<real> c{};
+  c.nx = p.nx;
+  c.ny = p.ny;
+  c.nz = p.nz;
+  c.rho0 = real(p.rho0);
+  c.c2 = real(p.c * p.c);
+  c.inv_h = real(1.0 / p.h);
+  c.dt = real(p.dt);
+  c.eta = real(p.eta);
+  c.lam2 = real(p.zeta - 2.0 * p.eta / 3.0);
+  const double vol_dt = p.h * p.h * p.h * p.dt;
+  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
+  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
+  c.noise_diag = real(std::sqrt(2.0) * S);
+  c.noise_trace = real(std::sqrt(2.0) * (B - S / 3.0));
+  c.noise_edge = real(S);
+  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
+  c.wave_axis = p.wave_axis;
+  c.plane_index = p.plane_index;
+  if constexpr (sizeof(real) == 4) {
+    c.cos_table = ctx->cos_table_f;
+    c.drive = ctx->drive_f;
+  } else {
+    c.cos_table = ctx->cos_table;
+    c.drive = ctx->drive;
+  }
+  c.k0 = uint32_t(p.seed & 0xffffffffull);
+  c.k1 = uint32_t(p.seed >> 32);
+  c.box = p.box;
+  c.noise = p.kT > 0.0;
+  return c;
+}
+
+template <typename real>
 struct TileShape;
 template <>
 struct TileShape<float> {
-  static constexpr int TX = 32, TY = 8;
+  static constexpr int TX = 32, TY = IC_FP32_TILE_Y;
 };
 template <>
 struct TileShape<double> {
@@ -281,13 +339,17 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
     a.n[j] = static_cast<const real *>(in_n[j]);
     a.o[j] = static_cast<real *>(out[j]);
   }
-  a.c = fluid_consts(ctx);
+  a.pp = ctx->ps.n > 0 ? static_cast<const real *>(ctx->pp) : nullptr;
+  for (int j = 0; j < 12; ++j) a.noise_out[j] = STAGE == 0 ? static_cast<real *>(ctx->noise[j]) : nullptr;
+  for (int j = 0; j < 6; ++j)
+    a.noise_in[j] = STAGE == 0 ? nullptr : static_cast<const real *>(ctx->noise[(STAGE == 1 ? 0 : 6) + j]);
+  a.c = fluid_consts<real>(ctx);
   a.step = ctx->d.step;
   a.partials = ctx->d.partials;
   a.zchunk = zchunk_for(ctx);
   const size_t smem = 18 * EXY * sizeof(real);
-  static_assert(18 * EXY * sizeof(real) <= 48 * 1024, "stage tile must fit the default shared memory");
   auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   kern<<<stage_grid<real>(ctx), EXY, smem, ctx->stream>>>(a);
   return cudaGetLastError();
 }
@@ -406,10 +468,13 @@ __global__ void k_field_sums(int nx, int ny, int nz, int axis, const double *cos
 }
 
 // End of step: A(t) from the stage-3 partials, weighted accumulation, the
-// non-finite check and the step counter (one block).
+// non-finite check, the step counter and the drive amplitudes of the next
+// step (one block).
 __global__ void k_end_of_step(const double *partials, int nb, double inv_cells, int has_mode,
-                              int64_t *step, const double *weights, double *scalars, int *status) {
+                              int64_t *step, const double *weights, double *scalars, int *status,
+                              double amp, double omega, double dt, double phase, double *drive, float *drive_f) {
   __shared__ double s[kRedThreads];
+  const int64_t n0 = step[0];   // read by every thread before thread 0 advances it
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[b];
   s[threadIdx.x] = acc;
@@ -420,48 +485,33 @@ __global__ void k_end_of_step(const double *partials, int nb, double inv_cells, 
   }
   if (threadIdx.x == 0) {
     const double A = has_mode ? 2.0 * s[0] * inv_cells : 0.0;
-    const int64_t n = step[0], j = n - step[1];
+    const int64_t j = n0 - step[1];
     const double w = (j >= 0 && j < step[2]) ? weights[j] : 0.0;
     if (!isfinite(s[0])) atomicOr(status, kStatusNonfinite);
     scalars[0] += w;
     scalars[1] += w * A * A;
     scalars[2] = A;
-    *step = n + 1;
+    step[0] = n0 + 1;
+  }
+  if (threadIdx.x < 3) {
+    // drive amplitudes of the RK stages of the next step (t^n, t^{n+1}, t^{n+1/2})
+    const double frac = threadIdx.x == 0 ? 0.0 : (threadIdx.x == 1 ? 1.0 : 0.5);
+    const double t = (double(n0 + 1) + frac) * dt;
+    const double d = amp * sin(omega * t + phase);
+    drive[threadIdx.x] = d;
+    drive_f[threadIdx.x] = float(d);
   }
 }
 
 }  // namespace
 
-FluidConsts fluid_consts(const ic_ctx *ctx) {
+void drive_amplitudes(const ic_ctx *ctx, int64_t step, double out[3]) {
   const ic_grid_params &p = ctx->p;
-  FluidConsts c{};
-  c.nx = p.nx;
-  c.ny = p.ny;
-  c.nz = p.nz;
-  c.rho0 = p.rho0;
-  c.c2 = p.c * p.c;
-  c.inv_h = 1.0 / p.h;
-  c.dt = p.dt;
-  c.eta = p.eta;
-  c.lam2 = p.zeta - 2.0 * p.eta / 3.0;
-  const double vol_dt = p.h * p.h * p.h * p.dt;
-  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
-  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
-  c.noise_diag = std::sqrt(2.0) * S;
-  c.noise_trace = std::sqrt(2.0) * (B - S / 3.0);
-  c.noise_edge = S;
-  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
-  c.wave_axis = p.wave_axis;
-  c.plane_index = p.plane_index;
-  c.force_amp = ctx->force_amp;
-  c.omega = ctx->omega;
-  c.phase = p.wave_phase;
-  c.cos_table = ctx->cos_table;
-  c.k0 = uint32_t(p.seed & 0xffffffffull);
-  c.k1 = uint32_t(p.seed >> 32);
-  c.box = p.box;
-  c.noise = p.kT > 0.0;
-  return c;
+  for (int s = 0; s < 3; ++s) {
+    const double t = (double(step) + kStageTime[s]) * p.dt;
+    out[s] = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0
+                                                                : ctx->force_amp * std::sin(ctx->omega * t + p.wave_phase);
+  }
 }
 
 size_t fluid_num_partials(const ic_ctx *ctx) {
@@ -514,9 +564,11 @@ cudaError_t launch_end_of_step(ic_ctx *ctx) {
   const dim3 g = ctx->p.precision == IC_FP32 ? stage_grid<float>(ctx) : stage_grid<double>(ctx);
   const int nb = int(g.x * g.y * g.z);
   const int has_mode = 1;
+  const ic_grid_params &p = ctx->p;
+  const double amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;
   k_end_of_step<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d.partials, nb, 1.0 / double(ctx->cells), has_mode,
-                                                    ctx->d.step, ctx->d.weights, ctx->d.scalars,
-                                                    ctx->d.status);
+                                                    ctx->d.step, ctx->d.weights, ctx->d.scalars, ctx->d.status,
+                                                    amp, ctx->omega, p.dt, p.wave_phase, ctx->drive, ctx->drive_f);
   return cudaGetLastError();
 }
 

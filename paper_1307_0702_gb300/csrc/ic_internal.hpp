@@ -16,15 +16,17 @@ constexpr int kStatusNonfinite = 1;    // device status bits
 constexpr int kStatusNbrOverflow = 2;
 constexpr int kStatusSkin = 4;
 
-// Per-stage constants of the fluid kernel (derived on the host in FP64).
+// Per-stage constants of the fluid kernel, derived on the host in FP64 and
+// handed to the kernel in its working precision.
+template <typename real>
 struct FluidConsts {
   int nx, ny, nz;
-  double rho0, c2, inv_h, dt, eta, lam2;        // lam2 = zeta - 2 eta / 3
-  double noise_diag, noise_trace, noise_edge;   // sqrt2 S, sqrt2 (B - S/3), S
+  real rho0, c2, inv_h, dt, eta, lam2;        // lam2 = zeta - 2 eta / 3
+  real noise_diag, noise_trace, noise_edge;   // sqrt2 S, sqrt2 (B - S/3), S
   int forcing, wave_axis, plane_index;
-  double force_amp, omega, phase;               // P (or Delta p0), omega, phi
-  const double *cos_table;                      // cos(k x_i) along the wave axis
-  uint32_t k0, k1, box;                         // Philox key and box
+  const real *cos_table;                      // cos(k x_i) along the wave axis
+  const real *drive;                          // drive amplitude of each RK stage of the current step
+  uint32_t k0, k1, box;                       // Philox key and box
   int noise;
 };
 
@@ -38,10 +40,10 @@ struct ParticleStore {
   void *m_e = nullptr, *eps = nullptr, *k_s = nullptr;   // n
   void *w = nullptr;         // n*18: centre weights [axis][3], own-axis face weights [axis][3]
   void *jv_n = nullptr;      // n*3: J^{n+1/2} v^n
-  void *omega = nullptr;     // 2*n: Omega for the current / next RK stage
   void *force = nullptr;     // n*3: F^{n+1/2}
   void *dg = nullptr;        // n*3: impulse dg
   void *lam = nullptr;       // n*3: lambda
+  void *jrho = nullptr;      // n: J rho^{n+1} at q^{n+1/2}
   int *base = nullptr;       // n*6: centre base (x,y,z), own-axis face base (x,y,z)
   int *nbr = nullptr;        // n*kMaxNeighbours, ascending indices
   int *nnbr = nullptr;       // n
@@ -68,7 +70,13 @@ struct ic_ctx {
   int cur = 0;             // buffer holding U^n (0 or 1); buffer 2 holds U^{n+1/2}
   ic::Device d{};
   ic::ParticleStore ps{};
-  double *cos_table = nullptr;
+  void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
+  void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
+  bool any_spring = false;  // some particle is tethered: the stage force source is launched
+  double *cos_table = nullptr;      // cos(k x_i) along the wave axis, FP64
+  float *cos_table_f = nullptr;     // the same in FP32
+  double *drive = nullptr;          // [0..2] FP64 drive amplitude of each RK stage of the current step
+  float *drive_f = nullptr;         // [0..2] the same in FP32
   size_t n_partials = 0;
   int weights_cap = 0;
   int64_t host_step = 0;
@@ -88,8 +96,8 @@ struct ic_ctx {
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
   // every device allocation, for ic_destroy
-  void *allocs[64] = {};
-  size_t alloc_bytes[64] = {};
+  void *allocs[128] = {};
+  size_t alloc_bytes[128] = {};
   int n_allocs = 0;
 };
 
@@ -98,7 +106,7 @@ void *dev_alloc(ic_ctx *ctx, size_t bytes);
 void dev_free(ic_ctx *ctx, void *p);
 
 // fluid (ic_fluid.cu)
-FluidConsts fluid_consts(const ic_ctx *ctx);
+void drive_amplitudes(const ic_ctx *ctx, int64_t step, double out[3]);
 size_t fluid_num_partials(const ic_ctx *ctx);
 cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
                          void *const out[4]);
@@ -107,9 +115,11 @@ cudaError_t launch_field_sums(ic_ctx *ctx, void *const state[4], double *dev_out
 cudaError_t launch_end_of_step(ic_ctx *ctx);
 
 // particles (ic_particles.cu)
-enum ParticlePhase { kHalfStep = 0, kStageCorrection = 1, kImpulse = 2, kSpread = 3, kFinal = 4 };
+enum ParticlePhase { kHalfStep = 0, kPressure = 1, kForce = 2, kImpulse = 3, kSpread = 4, kFinal = 5 };
 cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *const cur[4],
                              void *const tgt[4]);
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]);
 cudaError_t launch_particle_momentum(ic_ctx *ctx, double *dev_out3);
+void positions_to_device(const ic_ctx *ctx, const double *q, size_t n3, void *out);
+void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q);
 }  // namespace ic

@@ -3,26 +3,31 @@
 // 0..26 own the 27 points of a location set.
 //
 // Per step (the fluid stages run in ic_fluid.cu between these launches):
-//   kHalfStep        substeps 1-2: J^n v^n at q^n -> q^{n+1/2}; F^{n+1/2};
-//                    stencils at q^{n+1/2}; J^{n+1/2} v^n; Omega of stage 1
-//   kStageCorrection after each RK stage s: adds b_s dt times the particle
-//                    part of the momentum rate, -(1/h) grad(S Omega_s) + S F,
-//                    to the stage output, then gathers Omega_{s+1}
-//   kImpulse         substeps 4-5: dg, u^{n+1}, lambda from J v~^{n+1}
-//   kSpread          substep 6: g^{n+1} = g~^{n+1} - S dg
-//   kFinal           substep 7: q^{n+1}; weighted force sums
+//   kHalfStep   substeps 1-2: J^n v^n at q^n -> q^{n+1/2}; F^{n+1/2};
+//               stencils at q^{n+1/2}; J^{n+1/2} v^n
+//   kPressure   before each RK stage s: the particle pressure S Omega_s on the
+//               centre cells (read by the stage kernel as part of pi)
+//   kForce      after each RK stage s, only with tethers: b_s dt S F
+//   kImpulse    substeps 4-5: dg, u^{n+1}, lambda from J v~^{n+1}
+//   kSpread     substep 6: g^{n+1} = g~^{n+1} - S dg
+//   kFinal      substep 7: q^{n+1}; weighted force sums; clears the pressure
 //
-// Spreading is deterministic and free of atomics: each grid face near
-// particles is updated by exactly one particle (its "owner": the lowest
-// index among the particles whose footprint holds the face), which sums the
-// contributions of itself and its neighbours in ascending index order.  The
-// footprint of a particle is the 4 x 3 x 3 block of a-faces around its centre
-// stencil for each axis a: every face that its pressure gradient, its force
-// or its impulse can reach.  Neighbour lists (|dq_a| < 4h + skin on every
-// axis) are rebuilt when a particle has moved more than a quarter skin.
+// Spreading is deterministic and free of atomics: each grid point near
+// particles is written by exactly one particle (its "owner": the lowest index
+// among the particles whose stencil holds the point), which sums the
+// contributions of itself and its neighbours in ascending index order.
+// Neighbour lists (|dq_a| < 4h + skin on every axis) are rebuilt when a
+// particle has moved more than a quarter skin.
+//
+// Positions.  The FP64 path keeps positions in length units (double).  The
+// FP32 path keeps them in 64-bit fixed point, q / h in units of 2^-40, so
+// that no FP64 arithmetic runs in its kernels (GB300's FP64 rate is a small
+// fraction of its FP32 rate) while a tethered particle's 1e-6 h displacement
+// stays resolved; its weights and forces are FP32.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "ic_device.cuh"
 #include "ic_internal.hpp"
@@ -31,31 +36,103 @@ namespace ic {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kFixBits = 40;
 
+template <typename real>
 struct PConsts {
   int n[3];
-  double h, inv_h, L[3], dt, rho0, vol;
-  double cutoff;      // neighbour cutoff per axis
-  double rebuild_at;  // displacement since build that triggers a rebuild
-  double skin_limit;  // displacement at which a list is no longer valid
+  real h, inv_h, dt, rho0, vol, inv_h3;
+  real L[3];
+  long long span[3];   // n << kFixBits (FP32 positions)
+  real cutoff;         // neighbour cutoff per axis (length)
+  real rebuild_at;     // displacement since build that triggers a rebuild
+  real skin_limit;     // displacement at which a list is no longer valid
+};
+
+template <typename real>
+struct Pos;
+
+// FP64 positions: length units, wrapped into [0, L).
+template <>
+struct Pos<double> {
+  using T = double;
+  __device__ static void axis(T q, const PConsts<double> &pc, int a, int &bc, double &rc, int &bf, double &rf) {
+    const int n = a == 0 ? pc.n[0] : (a == 1 ? pc.n[1] : pc.n[2]);
+    const double s = q / pc.h;
+    const double fc = floor(s + 0.5);
+    rc = s - fc;
+    bc = wrap(int(fc), n);
+    const double sf = s - 0.5;
+    const double ff = floor(sf + 0.5);
+    rf = sf - ff;
+    bf = wrap(int(ff), n);
+  }
+  __device__ static T advance(T q, double dq, const PConsts<double> &pc, int a) {
+    const double L = a == 0 ? pc.L[0] : (a == 1 ? pc.L[1] : pc.L[2]);
+    double r = fmod(q + dq, L);
+    if (r < 0.0) r += L;
+    if (r >= L) r -= L;
+    return r;
+  }
+  __device__ static double diff(T x, T y, const PConsts<double> &pc, int a) {   // minimum image x - y
+    const double L = a == 0 ? pc.L[0] : (a == 1 ? pc.L[1] : pc.L[2]);
+    const double d = x - y;
+    return d - L * rint(d / L);
+  }
+};
+
+// FP32 positions: fixed point q / h in units of 2^-40, wrapped into [0, n 2^40).
+template <>
+struct Pos<float> {
+  using T = long long;
+  __device__ static void axis(T q, const PConsts<float> &pc, int a, int &bc, float &rc, int &bf, float &rf) {
+    const int n = a == 0 ? pc.n[0] : (a == 1 ? pc.n[1] : pc.n[2]);
+    const int cell = int(q >> kFixBits);
+    const float frac = __uint2float_rn(uint32_t(q >> (kFixBits - 24)) & 0xFFFFFFu) * 0x1p-24f;   // [0, 1)
+    // centre set: s = cell + frac, i0 = floor(s + 1/2); face set: i0 = floor(s) = cell
+    const bool up = frac >= 0.5f;
+    bc = up ? (cell + 1 == n ? 0 : cell + 1) : cell;
+    rc = up ? frac - 1.0f : frac;
+    bf = cell;
+    rf = frac - 0.5f;
+  }
+  __device__ static T advance(T q, float dq, const PConsts<float> &pc, int a) {
+    const long long span = a == 0 ? pc.span[0] : (a == 1 ? pc.span[1] : pc.span[2]);
+    T r = q + __float2ll_rn(dq * pc.inv_h * 0x1p40f);
+    if (r < 0) r += span;
+    if (r >= span) r -= span;
+    return r;
+  }
+  __device__ static float diff(T x, T y, const PConsts<float> &pc, int a) {   // minimum image x - y (length)
+    const long long span = a == 0 ? pc.span[0] : (a == 1 ? pc.span[1] : pc.span[2]);
+    long long d = x - y;
+    if (2 * d >= span) d -= span;
+    if (2 * d < -span) d += span;
+    // d = hi 2^32 + lo: two exact 32-bit conversions instead of an int64 one
+    const float cells = __int2float_rn(int(d >> 32)) * 0x1p-8f + __uint2float_rn(uint32_t(d)) * 0x1p-40f;
+    return cells * pc.h;
+  }
 };
 
 template <typename real>
 struct PV {
+  using P = typename Pos<real>::T;
   int n;
-  double *q, *q_eq, *q_build, *q_half, *acc;
-  real *u, *m_e, *eps, *k_s, *w, *jv_n, *omega, *force, *dg, *lam;
+  P *q, *q_eq, *q_build, *q_half;
+  double *acc;
+  real *u, *m_e, *eps, *k_s, *w, *jv_n, *force, *dg, *lam, *jrho;
   int *base, *nbr, *nnbr;
 };
 
 template <typename real>
 PV<real> view(const ParticleStore &s) {
+  using P = typename Pos<real>::T;
   PV<real> v;
   v.n = s.n;
-  v.q = s.q;
-  v.q_eq = s.q_eq;
-  v.q_build = s.q_build;
-  v.q_half = s.q_half;
+  v.q = (P *)s.q;
+  v.q_eq = (P *)s.q_eq;
+  v.q_build = (P *)s.q_build;
+  v.q_half = (P *)s.q_half;
   v.acc = s.acc;
   v.u = (real *)s.u;
   v.m_e = (real *)s.m_e;
@@ -63,10 +140,10 @@ PV<real> view(const ParticleStore &s) {
   v.k_s = (real *)s.k_s;
   v.w = (real *)s.w;
   v.jv_n = (real *)s.jv_n;
-  v.omega = (real *)s.omega;
   v.force = (real *)s.force;
   v.dg = (real *)s.dg;
   v.lam = (real *)s.lam;
+  v.jrho = (real *)s.jrho;
   v.base = s.base;
   v.nbr = s.nbr;
   v.nnbr = s.nnbr;
@@ -78,32 +155,38 @@ struct Grid4 {
   real *f[4];   // delta rho, g_x, g_y, g_z
 };
 
-__device__ __forceinline__ double wrap_pos(double x, double L) {
-  double r = fmod(x, L);
-  if (r < 0.0) r += L;
-  if (r >= L) r -= L;
-  return r;
+template <typename real>
+__device__ __forceinline__ int n_of(const PConsts<real> &pc, int a) {
+  return a == 0 ? pc.n[0] : (a == 1 ? pc.n[1] : pc.n[2]);
 }
 
-__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
-
-// Stencil of a particle at q: centre base and weights, own-axis face base and weights.
+// Stencil of a particle (lane a < 3 holds the position component q_a): centre
+// base and weights, own-axis face base and weights, broadcast to the warp.
 template <typename real>
-__device__ void stencil_at(const double q[3], const PConsts &pc, int base[6], real w[18]) {
+__device__ void stencil_warp(typename Pos<real>::T qa, int lane, const PConsts<real> &pc, int base[6],
+                             real w[18]) {
+  int bc = 0, bf = 0;
+  real wc[3] = {real(0), real(0), real(0)}, wf[3] = {real(0), real(0), real(0)};
+  if (lane < 3) {
+    real rc, rf;
+    Pos<real>::axis(qa, pc, lane, bc, rc, bf, rf);
+    peskin3(rc, wc);
+    peskin3(rf, wf);
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double s = q[a] / pc.h;
-    const double fc = floor(s + 0.5);
-    peskin3(real(s - fc), &w[3 * a]);
-    base[a] = wrap(int(fc), pc.n[a]);
-    const double sf = s - 0.5;
-    const double ff = floor(sf + 0.5);
-    peskin3(real(sf - ff), &w[9 + 3 * a]);
-    base[3 + a] = wrap(int(ff), pc.n[a]);
+    base[a] = __shfl_sync(0xffffffffu, bc, a);
+    base[3 + a] = __shfl_sync(0xffffffffu, bf, a);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      w[3 * a + j] = __shfl_sync(0xffffffffu, wc[j], a);
+      w[9 + 3 * a + j] = __shfl_sync(0xffffffffu, wf[j], a);
+    }
   }
 }
 
-__device__ __forceinline__ size_t cell_index(int x, int y, int z, const PConsts &pc) {
+template <typename real>
+__device__ __forceinline__ size_t cell_index(int x, int y, int z, const PConsts<real> &pc) {
   return size_t(x) + size_t(pc.n[0]) * (size_t(y) + size_t(pc.n[1]) * size_t(z));
 }
 
@@ -114,34 +197,42 @@ __device__ __forceinline__ int step_coord(int b, int d, int n) {
   return v;
 }
 
-// Warp gather at one stencil: J delta rho (out[0]) and J v^a (out[1+a]).
 template <typename real>
-__device__ void gather(const Grid4<real> &G, const int base[6], const real w[18], const PConsts &pc,
+__device__ __forceinline__ real sel3(const real *w3, int d) {   // w3[d + 1], d in {-1, 0, 1}
+  return d < 0 ? w3[0] : (d == 0 ? w3[1] : w3[2]);
+}
+
+// Warp gather at one stencil: J delta rho (out[0]) and J v^a (out[1+a]).
+// Lane l < 27 owns the point (l % 3, (l / 3) % 3, l / 9) - 1 of each location set.
+template <typename real>
+__device__ void gather(const Grid4<real> &G, const int base[6], const real w[18], const PConsts<real> &pc,
                        int lane, bool want_rho, bool want_v, real out[4]) {
   real acc[4] = {real(0), real(0), real(0), real(0)};
   if (lane < 27) {
-    const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-    int cc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) cc[a] = step_coord(base[a], d[a], pc.n[a]);
-    if (want_rho)
-      acc[0] = w[d[0] + 1] * w[3 + d[1] + 1] * w[6 + d[2] + 1] * G.f[0][cell_index(cc[0], cc[1], cc[2], pc)];
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    const int cx = step_coord(base[0], dx, pc.n[0]), cy = step_coord(base[1], dy, pc.n[1]),
+              cz = step_coord(base[2], dz, pc.n[2]);
+    const real wcx = sel3(w + 0, dx), wcy = sel3(w + 3, dy), wcz = sel3(w + 6, dz);
+    if (want_rho) acc[0] = wcx * wcy * wcz * G.f[0][cell_index(cx, cy, cz, pc)];
     if (want_v) {
-      const real rho0 = real(pc.rho0);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int fc[3] = {cc[0], cc[1], cc[2]};
-        fc[a] = step_coord(base[3 + a], d[a], pc.n[a]);
-        real wt = w[9 + 3 * a + d[a] + 1];
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-          if (b != a) wt *= w[3 * b + d[b] + 1];
-        const size_t i = cell_index(fc[0], fc[1], fc[2], pc);
-        int up[3] = {fc[0], fc[1], fc[2]};
-        up[a] = (up[a] + 1 == pc.n[a]) ? 0 : up[a] + 1;
-        const size_t iu = cell_index(up[0], up[1], up[2], pc);
-        const real rf = rho0 + real(0.5) * (G.f[0][i] + G.f[0][iu]);
-        acc[1 + a] = wt * (G.f[1 + a][i] / rf);
+      const real rho0 = pc.rho0, half = real(0.5);
+      {  // x faces
+        const int fx = step_coord(base[3], dx, pc.n[0]);
+        const int fxp = (fx + 1 == pc.n[0]) ? 0 : fx + 1;
+        const size_t i = cell_index(fx, cy, cz, pc), iu = cell_index(fxp, cy, cz, pc);
+        acc[1] = sel3(w + 9, dx) * wcy * wcz * fdiv(G.f[1][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
+      }
+      {  // y faces
+        const int fy = step_coord(base[4], dy, pc.n[1]);
+        const int fyp = (fy + 1 == pc.n[1]) ? 0 : fy + 1;
+        const size_t i = cell_index(cx, fy, cz, pc), iu = cell_index(cx, fyp, cz, pc);
+        acc[2] = wcx * sel3(w + 12, dy) * wcz * fdiv(G.f[2][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
+      }
+      {  // z faces
+        const int fz = step_coord(base[5], dz, pc.n[2]);
+        const int fzp = (fz + 1 == pc.n[2]) ? 0 : fz + 1;
+        const size_t i = cell_index(cx, cy, fz, pc), iu = cell_index(cx, cy, fzp, pc);
+        acc[3] = wcx * wcy * sel3(w + 15, dz) * fdiv(G.f[3][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
       }
     }
   }
@@ -157,116 +248,138 @@ __device__ __forceinline__ void load_stencil(const PV<real> &P, int p, int base[
   for (int j = 0; j < 18; ++j) w[j] = P.w[18 * p + j];
 }
 
-// centre-set weight of particle m at cell c (0 outside its stencil)
-template <typename real>
-__device__ __forceinline__ real centre_weight(const PV<real> &P, int m, const int c[3], const PConsts &pc) {
-  real wt = real(1);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int d = ring_delta(c[b], P.base[6 * m + b], pc.n[b]);
-    if (d < -1 || d > 1) return real(0);
-    wt *= P.w[18 * m + 3 * b + d + 1];
-  }
-  return wt;
-}
-
-// a-face weight of particle m at face f (0 outside its stencil)
-template <typename real>
-__device__ __forceinline__ real face_weight(const PV<real> &P, int m, int a, const int f[3], const PConsts &pc) {
-  real wt = real(1);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int bb = (b == a) ? 3 + b : b;
-    const int d = ring_delta(f[b], P.base[6 * m + bb], pc.n[b]);
-    if (d < -1 || d > 1) return real(0);
-    wt *= P.w[18 * m + (b == a ? 9 : 0) + 3 * b + d + 1];
-  }
-  return wt;
+// signed offset b - a on a ring of n points, for |b - a| < n (no division)
+__device__ __forceinline__ int ring_d(int b, int a, int n) {
+  int d = b - a;
+  if (2 * d > n) d -= n;
+  if (2 * d < -n) d += n;
+  return d;
 }
 
 template <typename real>
-__device__ __forceinline__ bool in_footprint(const PV<real> &P, int m, int a, const int f[3], const PConsts &pc) {
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int d = ring_delta(f[b], P.base[6 * m + b], pc.n[b]);
-    if (b == a ? (d < -2 || d > 1) : (d < -1 || d > 1)) return false;
-  }
-  return true;
+__device__ __forceinline__ real w1(const real *w3, int d) {
+  return (unsigned(d + 1) < 3u) ? w3[d + 1] : real(0);
 }
 
-// The owner-computes face update.  KIND 0: stage correction
-// coef * [-(Omega_m / h^4)(W_c(c+) - W_c(c-)) + W_a(f) F_m / h^3];
-// KIND 1: impulse, -W_a(f) dg_m / h^3.
-template <typename real, int KIND>
-__device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int p, int lane,
-                                   const real *omega, real coef, const PConsts &pc) {
+template <typename real>
+__device__ __forceinline__ real pick3(const real v[4], int a) {
+  return a == 0 ? v[1] : (a == 1 ? v[2] : v[3]);
+}
+
+// Per-warp staging of one member particle for the face updates.
+template <typename real>
+struct Member {
+  int base[6];
+  real w[18];
+  real vec[3];
+};
+
+// Owner-computes update of the faces of particle p's three face stencils (for
+// each axis a, the 3 x 3 x 3 a-faces around its a-face base): every such face
+// is updated by exactly one particle, the lowest-index one whose face stencils
+// hold it, which adds  scale * sum_m W_a(m, f) vec_m[a] / h^3  over the
+// particles m whose stencils reach the face, in ascending particle index.
+// vec is the tether force (stage source S F) or the impulse (-S dg).
+template <typename real>
+__device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int p, int lane, const real *vec,
+                                   real scale, const PConsts<real> &pc, Member<real> *sm) {
   const int nn = P.nnbr[p];
   const int *nb = P.nbr + size_t(p) * kMaxNeighbours;
-  const real inv_h3 = real(pc.inv_h * pc.inv_h * pc.inv_h);
-  const real inv_h4 = inv_h3 * real(pc.inv_h);
-  for (int t = lane; t < 108; t += 32) {
-    const int a = t / 36, r = t % 36;
-    const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
-    int f[3];
-    f[a] = step_coord(P.base[6 * p + a], r % 4 - 2, pc.n[a]);
-    f[b1] = step_coord(P.base[6 * p + b1], (r / 4) % 3 - 1, pc.n[b1]);
-    f[b2] = step_coord(P.base[6 * p + b2], r / 12 - 1, pc.n[b2]);
-    bool owner = true;
-    for (int j = 0; j < nn && owner; ++j) {
-      const int m = nb[j];
-      if (m >= p) break;
-      if (in_footprint(P, m, a, f, pc)) owner = false;
+  int pb[6];
+#pragma unroll
+  for (int b = 0; b < 6; ++b) pb[b] = P.base[6 * p + b];
+
+  // this lane's faces: t = lane + 32 j < 81; axis a = t / 27, point (t % 27)
+  int fa[3], fA[3], fB1[3], fB2[3];
+  bool owner[3];
+  real total[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int t = lane + 32 * j;
+    const int a = (t < 81) ? t / 27 : 0, r = t % 27;
+    const int b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
+    const int pa = a == 0 ? pb[3] : (a == 1 ? pb[4] : pb[5]);     // face base along a
+    const int p1 = b1 == 0 ? pb[0] : (b1 == 1 ? pb[1] : pb[2]);
+    const int p2 = b2 == 0 ? pb[0] : (b2 == 1 ? pb[1] : pb[2]);
+    fa[j] = a;
+    fA[j] = step_coord(pa, r % 3 - 1, n_of(pc, a));
+    fB1[j] = step_coord(p1, (r / 3) % 3 - 1, n_of(pc, b1));
+    fB2[j] = step_coord(p2, r / 9 - 1, n_of(pc, b2));
+    owner[j] = t < 81;
+    total[j] = real(0);
+  }
+
+  int j_nb = 0;
+  bool self_done = false;
+  while (true) {
+    int m;
+    if (!self_done && (j_nb >= nn || nb[j_nb] > p)) {
+      m = p;
+      self_done = true;
+    } else if (j_nb < nn) {
+      m = nb[j_nb++];
+    } else {
+      break;
     }
-    if (!owner) continue;
-    int cp[3] = {f[0], f[1], f[2]};
-    cp[a] = (cp[a] + 1 == pc.n[a]) ? 0 : cp[a] + 1;
-    // contributions of p and its neighbours, in ascending particle index
-    real total = real(0);
-    bool self_done = false;
-    int j = 0;
-    while (true) {
-      int m;
-      if (!self_done && (j >= nn || nb[j] > p)) {
-        m = p;
-        self_done = true;
-      } else if (j < nn) {
-        m = nb[j++];
-      } else {
-        break;
-      }
-      if (KIND == 0) {
-        const real wp = centre_weight(P, m, cp, pc), wm = centre_weight(P, m, f, pc);
-        const real wf = face_weight(P, m, a, f, pc);
-        total += -(omega[m] * inv_h4) * (wp - wm) + wf * P.force[3 * m + a] * inv_h3;
-      } else {
-        const real wf = face_weight(P, m, a, f, pc);
-        total += -wf * P.dg[3 * m + a] * inv_h3;
-      }
+    // face stencils of two particles can share a face only if their centre
+    // bases are within 3 cells on every axis
+    bool far = false;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int d = ring_d(P.base[6 * m + b], pb[b], pc.n[b]);
+      far = far || d > 3 || d < -3;
     }
-    const size_t i = cell_index(f[0], f[1], f[2], pc);
-    G.f[1 + a][i] += coef * total;
+    if (far) continue;
+    __syncwarp();
+    if (lane < 6) sm->base[lane] = P.base[6 * m + lane];
+    if (lane < 18) sm->w[lane] = P.w[18 * m + lane];
+    if (lane < 3) sm->vec[lane] = vec[3 * m + lane];
+    __syncwarp();
+    const bool lower = m < p;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int a = fa[j], b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
+      const int df = ring_d(fA[j], sm->base[3 + a], n_of(pc, a));
+      const int d1 = ring_d(fB1[j], sm->base[b1], n_of(pc, b1));
+      const int d2 = ring_d(fB2[j], sm->base[b2], n_of(pc, b2));
+      const bool inside = df >= -1 && df <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1;
+      if (lower && inside) owner[j] = false;
+      const real wt = w1(sm->w + 9 + 3 * a, df) * w1(sm->w + 3 * b1, d1) * w1(sm->w + 3 * b2, d2);
+      total[j] += wt * sm->vec[a] * pc.inv_h3;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (owner[j]) {
+      const int a = fa[j];
+      const int x = a == 0 ? fA[j] : (a == 1 ? fB2[j] : fB1[j]);
+      const int y = a == 1 ? fA[j] : (a == 2 ? fB2[j] : fB1[j]);
+      const int z = a == 2 ? fA[j] : (a == 0 ? fB2[j] : fB1[j]);
+      G.f[1 + a][cell_index(x, y, z, pc)] += scale * total[j];
+    }
   }
 }
 
 // ------------------------------------------------------------------ kernels
 template <typename real>
-__global__ void k_half_step(PV<real> P, Grid4<real> G, PConsts pc, int *rebuild, int *status) {
+__global__ void k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc, int *rebuild, int *status) {
+  using PosT = Pos<real>;
+  using T = typename PosT::T;
   const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= P.n) return;
-  double q[3] = {P.q[3 * p], P.q[3 * p + 1], P.q[3 * p + 2]};
 
   if (*rebuild) {
     // neighbour list from q^n, in ascending index order
+    const T q0 = P.q[3 * p], q1 = P.q[3 * p + 1], q2 = P.q[3 * p + 2];
     int count = 0;
     for (int j0 = 0; j0 < P.n; j0 += 32) {
       const int j = j0 + lane;
       bool hit = false;
       if (j < P.n && j != p) {
-        hit = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          hit = hit && fabs(min_image(P.q[3 * j + a] - q[a], pc.L[a])) < pc.cutoff;
+        hit = fabs(PosT::diff(P.q[3 * j], q0, pc, 0)) < pc.cutoff &&
+              fabs(PosT::diff(P.q[3 * j + 1], q1, pc, 1)) < pc.cutoff &&
+              fabs(PosT::diff(P.q[3 * j + 2], q2, pc, 2)) < pc.cutoff;
       }
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) {
@@ -278,63 +391,113 @@ __global__ void k_half_step(PV<real> P, Grid4<real> G, PConsts pc, int *rebuild,
     if (lane == 0) {
       if (count > kMaxNeighbours) atomicOr(status, kStatusNbrOverflow);
       P.nnbr[p] = min(count, kMaxNeighbours);
-      for (int a = 0; a < 3; ++a) P.q_build[3 * p + a] = q[a];
     }
+    if (lane < 3) P.q_build[3 * p + lane] = P.q[3 * p + lane];
   }
 
-  // substep 1: q^{n+1/2} = q^n + dt/2 J^n v^n
+  // substep 1: q^{n+1/2} = q^n + dt/2 J^n v^n (lane a < 3 owns axis a)
+  const T q_l = lane < 3 ? P.q[3 * p + lane] : T(0);
   int base[6];
   real w[18];
-  stencil_at(q, pc, base, w);
+  stencil_warp<real>(q_l, lane, pc, base, w);
   real g4[4];
   gather(G, base, w, pc, lane, false, true, g4);
-  double qh[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) qh[a] = wrap_pos(q[a] + 0.5 * pc.dt * double(g4[1 + a]), pc.L[a]);
+  T qh_l = T(0);
+  real F_l = real(0);
+  if (lane < 3) {
+    qh_l = PosT::advance(q_l, real(0.5) * pc.dt * pick3(g4, lane), pc, lane);
+    // substep 2: tether force at q^{n+1/2}
+    F_l = -P.k_s[p] * real(PosT::diff(qh_l, P.q_eq[3 * p + lane], pc, lane));
+  }
 
-  // substep 2: tether force at q^{n+1/2}
-  real F[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) F[a] = real(-double(P.k_s[p]) * min_image(qh[a] - P.q_eq[3 * p + a], pc.L[a]));
-
-  // stencil at q^{n+1/2}; J^{n+1/2} v^n and J^{n+1/2} rho^n
-  stencil_at(qh, pc, base, w);
-  gather(G, base, w, pc, lane, true, true, g4);
+  // stencil at q^{n+1/2}; J^{n+1/2} v^n
+  stencil_warp<real>(qh_l, lane, pc, base, w);
+  gather(G, base, w, pc, lane, false, true, g4);
+  if (lane < 3) {
+    P.q_half[3 * p + lane] = qh_l;
+    P.force[3 * p + lane] = F_l;
+    P.jv_n[3 * p + lane] = pick3(g4, lane);
+    if (fabs(PosT::diff(qh_l, P.q_build[3 * p + lane], pc, lane)) > pc.skin_limit) atomicOr(status, kStatusSkin);
+  }
   if (lane == 0) {
-    for (int a = 0; a < 3; ++a) {
-      P.q_half[3 * p + a] = qh[a];
-      P.force[3 * p + a] = F[a];
-      P.jv_n[3 * p + a] = g4[1 + a];
-      const double d = fabs(min_image(qh[a] - P.q_build[3 * p + a], pc.L[a]));
-      if (d > pc.skin_limit) atomicOr(status, kStatusSkin);
-    }
+#pragma unroll
     for (int j = 0; j < 6; ++j) P.base[6 * p + j] = base[j];
+#pragma unroll
     for (int j = 0; j < 18; ++j) P.w[18 * p + j] = w[j];
-    P.omega[p] = P.eps[p] * real(pc.vol) * g4[0];   // Omega = eps V (J rho - rho0)
   }
 }
 
+// Particle pressure of one RK stage (Eqs. (eq:pressure), (omega)): writes
+// PP(c) = sum_m W_c(m, c) Omega_m / h^3, Omega_m = eps_m V J_m(rho_s - rho0),
+// on the 27 centre cells of particle p, for the cells p owns (no lower-index
+// particle's centre stencil holds them).  The Omega of the particles whose
+// stencils reach p's cells are regathered here, so one launch suffices.
 template <typename real>
-__global__ void k_stage_correction(PV<real> P, Grid4<real> G, PConsts pc, int stage, real coef,
-                                   int *rebuild) {
+__global__ void k_pressure(PV<real> P, Grid4<real> G, PConsts<real> pc, real *pp, int *rebuild) {
   const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (stage == 0 && blockIdx.x == 0 && threadIdx.x == 0) *rebuild = 0;
+  // the neighbour lists were rebuilt (if flagged) by the half step: clear the flag
+  if (rebuild && blockIdx.x == 0 && threadIdx.x == 0) *rebuild = 0;
   if (p >= P.n) return;
-  const real *om = P.omega + size_t(stage & 1) * P.n;
-  update_owned_faces<real, 0>(P, G, p, lane, om, coef, pc);
-  if (stage < 2) {
-    int base[6];
-    real w[18];
-    load_stencil(P, p, base, w);
+  const int nn = P.nnbr[p];
+  const int *nb = P.nbr + size_t(p) * kMaxNeighbours;
+  int pb[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) pb[b] = P.base[6 * p + b];
+  // this lane's cell of p's centre stencil
+  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+  const int cx = step_coord(pb[0], dx, pc.n[0]), cy = step_coord(pb[1], dy, pc.n[1]),
+            cz = step_coord(pb[2], dz, pc.n[2]);
+  bool owner = lane < 27;
+  real total = real(0);
+  int j_nb = 0;
+  bool self_done = false;
+  while (true) {
+    int m;
+    if (!self_done && (j_nb >= nn || nb[j_nb] > p)) {
+      m = p;
+      self_done = true;
+    } else if (j_nb < nn) {
+      m = nb[j_nb++];
+    } else {
+      break;
+    }
+    int mb[6];
+    real mw[18];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) mb[b] = P.base[6 * m + b];
+    bool far = false;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int d = ring_d(mb[b], pb[b], pc.n[b]);
+      far = far || d > 2 || d < -2;
+    }
+    if (far) continue;
+    load_stencil(P, m, mb, mw);
     real g4[4];
-    gather(G, base, w, pc, lane, true, false, g4);
-    if (lane == 0) P.omega[size_t((stage + 1) & 1) * P.n + p] = P.eps[p] * real(pc.vol) * g4[0];
+    gather(G, mb, mw, pc, lane, true, false, g4);
+    const real omega = P.eps[m] * pc.vol * g4[0];
+    const int ex = ring_d(cx, mb[0], pc.n[0]), ey = ring_d(cy, mb[1], pc.n[1]), ez = ring_d(cz, mb[2], pc.n[2]);
+    const bool inside = ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1;
+    if (m < p && inside) owner = false;
+    if (inside) total += sel3(mw + 0, ex) * sel3(mw + 3, ey) * sel3(mw + 6, ez) * omega;
   }
+  if (owner) pp[cell_index(cx, cy, cz, pc)] = total * pc.inv_h3;
+}
+
+// Spring-force source of RK stage s (b_s dt S F) or the impulse (-S dg).
+template <typename real, int KIND>
+__global__ void k_face_update(PV<real> P, Grid4<real> G, PConsts<real> pc, real scale) {
+  __shared__ Member<real> sm[kWarpsPerBlock];
+  const int warp = threadIdx.x / 32;
+  const int p = blockIdx.x * kWarpsPerBlock + warp;
+  const int lane = threadIdx.x & 31;
+  if (p >= P.n) return;
+  update_owned_faces<real>(P, G, p, lane, KIND == 0 ? P.force : P.dg, scale, pc, &sm[warp]);
 }
 
 template <typename real>
-__global__ void k_impulse(PV<real> P, Grid4<real> G, PConsts pc) {
+__global__ void k_impulse(PV<real> P, Grid4<real> G, PConsts<real> pc) {
   const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= P.n) return;
@@ -343,31 +506,23 @@ __global__ void k_impulse(PV<real> P, Grid4<real> G, PConsts pc) {
   load_stencil(P, p, base, w);
   real g4[4];
   gather(G, base, w, pc, lane, true, true, g4);
-  if (lane == 0) {
-    const real mf = real(pc.vol) * (real(pc.rho0) + g4[0]);   // m_f = V J rho^{n+1}
+  if (lane < 3) {
+    const real mf = pc.vol * (pc.rho0 + g4[0]);   // m_f = V J rho^{n+1}
     const real me = P.m_e[p];
-    for (int a = 0; a < 3; ++a) {
-      const real u = P.u[3 * p + a];
-      const real rel = g4[1 + a] - u;
-      const real dg = me * mf / (me + mf) * rel;
-      P.dg[3 * p + a] = dg;
-      P.u[3 * p + a] = u + mf / (me + mf) * rel;
-      P.lam[3 * p + a] = dg / real(pc.dt) - P.force[3 * p + a];
-    }
+    const real u = P.u[3 * p + lane];
+    const real rel = pick3(g4, lane) - u;
+    const real dg = me * mf / (me + mf) * rel;
+    P.dg[3 * p + lane] = dg;
+    P.u[3 * p + lane] = u + mf / (me + mf) * rel;
+    P.lam[3 * p + lane] = dg / pc.dt - P.force[3 * p + lane];
+    if (lane == 0) P.jrho[p] = pc.rho0 + g4[0];
   }
 }
 
 template <typename real>
-__global__ void k_spread(PV<real> P, Grid4<real> G, PConsts pc) {
-  const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (p >= P.n) return;
-  update_owned_faces<real, 1>(P, G, p, lane, nullptr, real(1), pc);
-}
-
-template <typename real>
-__global__ void k_final(PV<real> P, Grid4<real> G, PConsts pc, const int64_t *step, const double *weights,
-                        int *rebuild) {
+__global__ void k_final(PV<real> P, Grid4<real> G, PConsts<real> pc, const int64_t *step, const double *weights,
+                        int *rebuild, real *pp) {
+  using PosT = Pos<real>;
   const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= P.n) return;
@@ -376,35 +531,40 @@ __global__ void k_final(PV<real> P, Grid4<real> G, PConsts pc, const int64_t *st
   load_stencil(P, p, base, w);
   real g4[4];
   gather(G, base, w, pc, lane, false, true, g4);
-  if (lane == 0) {
+  // the particle pressure of this step is consumed: clear p's 27 cells
+  if (lane < 27)
+    pp[cell_index(step_coord(base[0], lane % 3 - 1, pc.n[0]), step_coord(base[1], (lane / 3) % 3 - 1, pc.n[1]),
+                  step_coord(base[2], lane / 9 - 1, pc.n[2]), pc)] = real(0);
+  bool move = false;
+  if (lane < 3) {
+    const typename PosT::T qn = PosT::advance(
+        P.q[3 * p + lane], real(0.5) * pc.dt * (pick3(g4, lane) + P.jv_n[3 * p + lane]), pc, lane);
+    P.q[3 * p + lane] = qn;
+    move = fabs(PosT::diff(qn, P.q_build[3 * p + lane], pc, lane)) > pc.rebuild_at;
+  }
+  if (__any_sync(0xffffffffu, move) && lane == 0) *rebuild = 1;
+  // weighted sums in FP64, one value per lane: lanes 0-2 the tether force, 3-5 lambda
+  if (lane < 6) {
     const int64_t jw = step[0] - step[1];
     const double wt = (jw >= 0 && jw < step[2]) ? weights[jw] : 0.0;
-    bool move = false;
-    for (int a = 0; a < 3; ++a) {
-      const double qn = wrap_pos(P.q[3 * p + a] + 0.5 * pc.dt * (double(g4[1 + a]) + double(P.jv_n[3 * p + a])),
-                                 pc.L[a]);
-      P.q[3 * p + a] = qn;
-      P.acc[6 * p + a] += wt * double(P.force[3 * p + a]);
-      P.acc[6 * p + 3 + a] += wt * double(P.lam[3 * p + a]);
-      if (fabs(min_image(qn - P.q_build[3 * p + a], pc.L[a])) > pc.rebuild_at) move = true;
-    }
-    if (move) *rebuild = 1;
+    const real v = lane < 3 ? P.force[3 * p + lane] : P.lam[3 * p + lane - 3];
+    P.acc[6 * p + lane] += wt * double(v);
   }
 }
 
 template <typename real>
-__global__ void k_init_velocity(PV<real> P, Grid4<real> G, PConsts pc, int first, int n) {
+__global__ void k_init_velocity(PV<real> P, Grid4<real> G, PConsts<real> pc, int first, int n) {
+  using T = typename Pos<real>::T;
   const int p = first + blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= first + n) return;
-  double q[3] = {P.q[3 * p], P.q[3 * p + 1], P.q[3 * p + 2]};
+  const T q_l = lane < 3 ? P.q[3 * p + lane] : T(0);
   int base[6];
   real w[18];
-  stencil_at(q, pc, base, w);
+  stencil_warp<real>(q_l, lane, pc, base, w);
   real g4[4];
   gather(G, base, w, pc, lane, false, true, g4);
-  if (lane == 0)
-    for (int a = 0; a < 3; ++a) P.u[3 * p + a] = g4[1 + a];
+  if (lane < 3) P.u[3 * p + lane] = pick3(g4, lane);
 }
 
 template <typename real>
@@ -424,23 +584,25 @@ __global__ void k_particle_momentum(PV<real> P, double *out3) {
     for (int a = 0; a < 3; ++a) out3[a] = s[a][0];
 }
 
-PConsts particle_consts(const ic_ctx *ctx) {
+template <typename real>
+PConsts<real> particle_consts(const ic_ctx *ctx) {
   const ic_grid_params &p = ctx->p;
-  PConsts c{};
-  c.n[0] = p.nx;
-  c.n[1] = p.ny;
-  c.n[2] = p.nz;
-  c.h = p.h;
-  c.inv_h = 1.0 / p.h;
-  c.L[0] = p.nx * p.h;
-  c.L[1] = p.ny * p.h;
-  c.L[2] = p.nz * p.h;
-  c.dt = p.dt;
-  c.rho0 = p.rho0;
-  c.vol = 8.0 * p.h * p.h * p.h;   // V = 1 / (J S) = 8 h^3 (Eq. (kvol))
-  c.cutoff = (4.0 + kSkin) * p.h;
-  c.rebuild_at = 0.25 * kSkin * p.h;
-  c.skin_limit = 0.5 * kSkin * p.h;
+  PConsts<real> c{};
+  const int n[3] = {p.nx, p.ny, p.nz};
+  for (int a = 0; a < 3; ++a) {
+    c.n[a] = n[a];
+    c.L[a] = real(n[a] * p.h);
+    c.span[a] = (long long)n[a] << kFixBits;
+  }
+  c.h = real(p.h);
+  c.inv_h = real(1.0 / p.h);
+  c.inv_h3 = real(1.0 / (p.h * p.h * p.h));
+  c.dt = real(p.dt);
+  c.rho0 = real(p.rho0);
+  c.vol = real(8.0 * p.h * p.h * p.h);   // V = 1 / (J S) = 8 h^3 (Eq. (kvol))
+  c.cutoff = real((4.0 + kSkin) * p.h);
+  c.rebuild_at = real(0.25 * kSkin * p.h);
+  c.skin_limit = real(0.5 * kSkin * p.h);
   return c;
 }
 
@@ -456,26 +618,31 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
                                void *const tgt[4]) {
   const PV<real> P = view<real>(ctx->ps);
   if (P.n == 0) return cudaSuccess;
-  const PConsts pc = particle_consts(ctx);
+  const PConsts<real> pc = particle_consts<real>(ctx);
   const dim3 grid((P.n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
   static const double kCoef[3] = {1.0, 0.25, 2.0 / 3.0};
+  real *pp = static_cast<real *>(ctx->pp);
   switch (phase) {
     case kHalfStep:
       k_half_step<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(cur), pc, ctx->d.rebuild, ctx->d.status);
       break;
-    case kStageCorrection:
-      k_stage_correction<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, stage,
-                                                                real(kCoef[stage] * ctx->p.dt), ctx->d.rebuild);
+    case kPressure:
+      k_pressure<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, pp,
+                                                        stage == 0 ? ctx->d.rebuild : nullptr);
+      break;
+    case kForce:
+      k_face_update<real, 0><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc,
+                                                                real(kCoef[stage] * ctx->p.dt));
       break;
     case kImpulse:
       k_impulse<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc);
       break;
     case kSpread:
-      k_spread<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc);
+      k_face_update<real, 1><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, real(-1));
       break;
     case kFinal:
       k_final<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, ctx->d.step, ctx->d.weights,
-                                                     ctx->d.rebuild);
+                                                     ctx->d.rebuild, pp);
       break;
   }
   return cudaGetLastError();
@@ -490,14 +657,13 @@ cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *
 }
 
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]) {
-  const PConsts pc = particle_consts(ctx);
   const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
   if (ctx->p.precision == IC_FP32)
-    k_init_velocity<float><<<grid, block, 0, ctx->stream>>>(view<float>(ctx->ps), grid4<float>(state), pc,
-                                                            first, n);
+    k_init_velocity<float><<<grid, block, 0, ctx->stream>>>(view<float>(ctx->ps), grid4<float>(state),
+                                                            particle_consts<float>(ctx), first, n);
   else
-    k_init_velocity<double><<<grid, block, 0, ctx->stream>>>(view<double>(ctx->ps), grid4<double>(state), pc,
-                                                             first, n);
+    k_init_velocity<double><<<grid, block, 0, ctx->stream>>>(view<double>(ctx->ps), grid4<double>(state),
+                                                             particle_consts<double>(ctx), first, n);
   return cudaGetLastError();
 }
 
@@ -507,6 +673,34 @@ cudaError_t launch_particle_momentum(ic_ctx *ctx, double *dev_out3) {
   else
     k_particle_momentum<double><<<1, 256, 0, ctx->stream>>>(view<double>(ctx->ps), dev_out3);
   return cudaGetLastError();
+}
+
+// Host conversions of positions to and from the device representation.
+void positions_to_device(const ic_ctx *ctx, const double *q, size_t n3, void *out) {
+  const ic_grid_params &p = ctx->p;
+  const int n[3] = {p.nx, p.ny, p.nz};
+  if (p.precision == IC_FP32) {
+    long long *o = static_cast<long long *>(out);
+    for (size_t i = 0; i < n3; ++i) {
+      const long long span = (long long)n[i % 3] << kFixBits;
+      long long v = std::llround(q[i] / p.h * 0x1p40);
+      v %= span;
+      if (v < 0) v += span;
+      o[i] = v;
+    }
+  } else {
+    std::memcpy(out, q, n3 * sizeof(double));
+  }
+}
+
+void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q) {
+  const ic_grid_params &p = ctx->p;
+  if (p.precision == IC_FP32) {
+    const long long *v = static_cast<const long long *>(in);
+    for (size_t i = 0; i < n3; ++i) q[i] = double(v[i]) * 0x1p-40 * p.h;
+  } else {
+    std::memcpy(q, in, n3 * sizeof(double));
+  }
 }
 
 }  // namespace ic

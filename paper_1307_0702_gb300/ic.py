@@ -146,6 +146,12 @@ class Grid:
         self._check(self._lib.ic_forces(self._ctx, _ptr(lam), _ptr(u), _ptr(q)))
         return lam, u, q
 
+    def particle_density(self):
+        """J rho^{n+1} per particle (n,)."""
+        out = np.empty(self.n_particles)
+        self._check(self._lib.ic_particle_density(self._ctx, _ptr(out)))
+        return out
+
     def time_average(self, reset=False):
         """(<F_spring>_w, <lambda>_w, <A^2>_w)."""
         n = self.n_particles
@@ -200,5 +206,7 @@ class Grid:
         out = {k: torch.as_tensor(_Arr(getattr(v, k), self.shape, typestr), device=self.device)
                for k in ("drho", "gx", "gy", "gz")}
         if v.n_particles:
-            out["q"] = torch.as_tensor(_Arr(v.q, (v.n_particles, 3), "<f8"), device=self.device)
+            # FP64: positions in length units; FP32: int64 fixed point q/h * 2^40
+            out["q"] = torch.as_tensor(_Arr(v.q, (v.n_particles, 3), "<i8" if v.precision == IC_FP32 else "<f8"),
+                                       device=self.device)
         return out

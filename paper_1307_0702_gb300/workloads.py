@@ -161,11 +161,11 @@ def many_particle_config(n, n_particles, *, kT=1e-3, wave_amp=5e-3, wave_nlambda
 
 
 def large_box_config(n=128, n_particles=10000):
-    """128^3 FP32 box, 1e4 particles (min separation 2h, host RNG seed 3),
+    """128^3 FP32 box, 1e4 free particles (min separation 2h, host RNG seed 3),
     contrasts of the single-particle case (m_p = 1.5 rho0 V, kappa_p = 0.5
-    kappa_f, spring k_s = 1), kT = 1e-3, two wavelengths along x, A = 1e-3."""
+    kappa_f), kT = 1e-3, two wavelengths along x, A = 1e-3."""
     return many_particle_config(n, n_particles, kT=1e-3, wave_amp=1e-3, wave_nlambda=2, seed=3,
-                                min_sep=2.0, fixed_contrast=(1.5, 0.5), k_spring=1.0,
+                                min_sep=2.0, fixed_contrast=(1.5, 0.5), k_spring=0.0,
                                 precision="fp32", place_seed=3)
 
 
