@@ -176,6 +176,27 @@ ic_status ic_device_views(ic_ctx *ctx, ic_views *out);
 ic_status ic_profile(ic_ctx *ctx, int enable);
 ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset);
 
+/* One SSP-RK3 step of the fluid alone (no particles) that allocates no
+ * device memory.  The paper has no counterpart: this is for callers that
+ * cannot allocate when they step -- code running inside another framework's
+ * stream capture (cudaMalloc is not allowed there), hosts whose device memory
+ * is all reserved by their own pool, plug-ins that may not allocate after
+ * start-up.  params: as for ic_create_grid (stream is used; alloc, free and
+ * alloc_ctx are ignored); in / out: device pointers to delta rho, g_x, g_y,
+ * g_z of nx*ny*nz values each in the params' precision, out distinct from
+ * in; step: the step index n (Philox counter and drive phase).  The same
+ * kernels as ic_step, without the particle terms.  Scratch lives in one static
+ * device array of 5.5 MiB held by every GPU that loads the library, so
+ * nx*ny*nz must not exceed IC_NOALLOC_MAX_CELLS (else IC_ERR_CAPACITY).  Its
+ * device address is looked up on the first call on each device: make that
+ * first call before any stream capture.  Calls share the array (it keeps the
+ * last call's contents), so calls that overlap on the GPU race.  Returns
+ * IC_ERR_ARG on invalid parameters or pointers, IC_ERR_CUDA if the symbol
+ * lookup or a launch fails; work is enqueued on params->stream. */
+#define IC_NOALLOC_MAX_CELLS 32768
+ic_status ic_fluid_step_noalloc(const ic_grid_params *params, const void *const in[4], void *const out[4],
+                                int64_t step);
+
 const char *ic_last_error(const ic_ctx *ctx);
 void ic_destroy(ic_ctx *ctx);
 

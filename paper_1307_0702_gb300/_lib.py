@@ -52,6 +52,7 @@ SIGNATURES = {
     "ic_device_views": (c_int, [c_void_p, POINTER(Views)]),
     "ic_profile": (c_int, [c_void_p, c_int]),
     "ic_profile_read": (c_int, [c_void_p, PD, POINTER(c_int64), c_int]),
+    "ic_fluid_step_noalloc": (c_int, [POINTER(GridParams), POINTER(c_void_p), POINTER(c_void_p), c_int64]),
     "ic_last_error": (c_char_p, [c_void_p]),
     "ic_destroy": (None, [c_void_p]),
 }

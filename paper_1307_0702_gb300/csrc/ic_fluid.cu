@@ -525,6 +525,68 @@ cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void
   return launch_stage_r<double>(ctx, stage, in_s, in_n, out);
 }
 
+template <typename real>
+cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> &c, int stage,
+                               const void *const in_s[4], const void *const in_n[4], void *const out[4],
+                               void *const noise[12], const int64_t *step, double *partials,
+                               cudaStream_t stream) {
+  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  constexpr int EXY = (TX + 2) * (TY + 2);
+  StageArgs<real> a;
+  for (int j = 0; j < 4; ++j) {
+    a.s[j] = static_cast<const real *>(in_s[j]);
+    a.n[j] = static_cast<const real *>(in_n[j]);
+    a.o[j] = static_cast<real *>(out[j]);
+  }
+  a.pp = nullptr;
+  for (int j = 0; j < 12; ++j) a.noise_out[j] = stage == 0 ? static_cast<real *>(noise[j]) : nullptr;
+  for (int j = 0; j < 6; ++j)
+    a.noise_in[j] = stage == 0 ? nullptr : static_cast<const real *>(noise[(stage == 1 ? 0 : 6) + j]);
+  a.c = c;
+  a.step = step;
+  a.partials = partials;
+  a.zchunk = std::min<int>(p.nz, 16);
+  const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + a.zchunk - 1) / a.zchunk);
+  const size_t smem = 18 * EXY * sizeof(real);
+  const bool noise_on = p.kT > 0.0;
+  switch (stage * 2 + (noise_on ? 1 : 0)) {
+#define IC_RAW(S, N)                                                                       \
+  {                                                                                        \
+    auto kern = k_rk3_stage<real, TX, TY, S, N>;                                            \
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+    kern<<<grid, EXY, smem, stream>>>(a);                                                   \
+  } break;
+    case 0: IC_RAW(0, false)
+    case 1: IC_RAW(0, true)
+    case 2: IC_RAW(1, false)
+    case 3: IC_RAW(1, true)
+    case 4: IC_RAW(2, false)
+    default: IC_RAW(2, true)
+#undef IC_RAW
+  }
+  return cudaGetLastError();
+}
+
+size_t stage_ctas_raw(const ic_grid_params &p) {
+  const int zc = std::min<int>(p.nz, 16);
+  if (p.precision == IC_FP32) {
+    constexpr int TX = TileShape<float>::TX, TY = TileShape<float>::TY;
+    return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
+  }
+  constexpr int TX = TileShape<double>::TX, TY = TileShape<double>::TY;
+  return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
+}
+
+cudaError_t launch_stage_raw(const ic_grid_params &p, const void *consts, int stage, const void *const in_s[4],
+                             const void *const in_n[4], void *const out[4], void *const noise[12],
+                             const int64_t *step, double *partials, cudaStream_t stream) {
+  if (p.precision == IC_FP32)
+    return launch_stage_raw_t<float>(p, *static_cast<const FluidConsts<float> *>(consts), stage, in_s, in_n, out,
+                                     noise, step, partials, stream);
+  return launch_stage_raw_t<double>(p, *static_cast<const FluidConsts<double> *>(consts), stage, in_s, in_n, out,
+                                    noise, step, partials, stream);
+}
+
 cudaError_t launch_thermal(ic_ctx *ctx, uint64_t seed, int add) {
   const ic_grid_params &p = ctx->p;
   const RngKey key{uint32_t(seed & 0xffffffffull), uint32_t(seed >> 32), p.box};

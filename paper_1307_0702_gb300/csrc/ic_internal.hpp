@@ -113,6 +113,11 @@ cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void
 cudaError_t launch_thermal(ic_ctx *ctx, uint64_t seed, int add);
 cudaError_t launch_field_sums(ic_ctx *ctx, void *const state[4], double *dev_out4);
 cudaError_t launch_end_of_step(ic_ctx *ctx);
+// context-free stage launch (consts points to a FluidConsts<real> of the params' precision)
+cudaError_t launch_stage_raw(const ic_grid_params &p, const void *consts, int stage, const void *const in_s[4],
+                             const void *const in_n[4], void *const out[4], void *const noise[12],
+                             const int64_t *step, double *partials, cudaStream_t stream);
+size_t stage_ctas_raw(const ic_grid_params &p);
 
 // particles (ic_particles.cu)
 enum ParticlePhase { kHalfStep = 0, kPressure = 1, kForce = 2, kImpulse = 3, kSpread = 4, kFinal = 5 };
