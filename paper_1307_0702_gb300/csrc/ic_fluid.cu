@@ -55,6 +55,12 @@ struct PlaneVals {
   real nz[6];
 };
 
+// the global loads of one plane, issued one iteration before they are used
+template <typename real>
+struct PlaneRaw {
+  real dr, drx, dry, drz, gx, gy, gz, pp;
+};
+
 constexpr double kStageTime[3] = {0.0, 1.0, 0.5};
 constexpr double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
 constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -120,25 +126,41 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     return real(0);
   };
 
-  auto load = [&](int kk) {
-    PlaneVals<real> v;
+  // 32-bit cell offsets: in-plane offsets fixed per thread, plus k * plane
+  const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
+  const uint32_t o_c = uint32_t(x) + uint32_t(NX) * uint32_t(y);
+  const uint32_t o_xp = uint32_t(xp) + uint32_t(NX) * uint32_t(y);
+  const uint32_t o_yp = uint32_t(x) + uint32_t(NX) * uint32_t(yp);
+  auto cell_of = [&](int kk) { return o_c + uint32_t(zwrap(kk)) * plane_n; };
+  auto fetch = [&](int kk) {
+    PlaneRaw<real> r;
     const int k = zwrap(kk);
-    const int kp = (k + 1 == NZ) ? 0 : k + 1;
-    const size_t i = size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * k);
-    const size_t row = size_t(NX) * (size_t(y) + size_t(NY) * k);
-    v.dr = a.s[0][i];
-    const real drx = a.s[0][row + xp];
-    const real dry = a.s[0][size_t(x) + size_t(NX) * (size_t(yp) + size_t(NY) * k)];
-    const real drz = a.s[0][size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * kp)];
-    v.gx = a.s[1][i];
-    v.gy = a.s[2][i];
-    v.gz = a.s[3][i];
-    v.pp = a.pp ? a.pp[i] : real(0);
-    v.vx = fdiv(v.gx, rho0 + half * (v.dr + drx));
-    v.vy = fdiv(v.gy, rho0 + half * (v.dr + dry));
-    v.vz = fdiv(v.gz, rho0 + half * (v.dr + drz));
+    const uint32_t kb = uint32_t(k) * plane_n;
+    const uint32_t kpb = (k + 1 == NZ) ? 0u : kb + plane_n;
+    const uint32_t i = o_c + kb;
+    r.dr = a.s[0][i];
+    r.drx = a.s[0][o_xp + kb];
+    r.dry = a.s[0][o_yp + kb];
+    r.drz = a.s[0][o_c + kpb];
+    r.gx = a.s[1][i];
+    r.gy = a.s[2][i];
+    r.gz = a.s[3][i];
+    r.pp = a.pp ? a.pp[i] : real(0);
+    return r;
+  };
+  auto finish = [&](int kk, const PlaneRaw<real> &r) {
+    PlaneVals<real> v;
+    v.dr = r.dr;
+    v.gx = r.gx;
+    v.gy = r.gy;
+    v.gz = r.gz;
+    v.pp = r.pp;
+    v.vx = fdiv(v.gx, rho0 + half * (v.dr + r.drx));
+    v.vy = fdiv(v.gy, rho0 + half * (v.dr + r.dry));
+    v.vz = fdiv(v.gz, rho0 + half * (v.dr + r.drz));
     if (NOISE && STAGE == 0) {
       // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
+      const uint32_t i = cell_of(kk);
       real wa[6], wb[6];
       stress_normals_ab(key, uint32_t(i), ustep, wa, wb);
 #pragma unroll
@@ -151,6 +173,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
         }
       }
     } else if (NOISE) {
+      const uint32_t i = cell_of(kk);
 #pragma unroll
       for (int j = 0; j < 6; ++j) v.nz[j] = a.noise_in[j][i];
     } else {
@@ -169,15 +192,27 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     B[VZ * EXY + t] = v.vz;
   };
 
-  PlaneVals<real> P = load(z0 - 1);
+  PlaneVals<real> P = finish(z0 - 1, fetch(z0 - 1));
   store_plane((z0 - 1) & 1, P);
+  PlaneRaw<real> R = fetch(z0);
   real vz_m = real(0), gz_m = real(0), txz_m = real(0), tyz_m = real(0), tzz_k = real(0);
   real mode_acc = real(0);
   const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
   const real dt = c.dt;
 
   for (int k = z0 - 1; k < z1; ++k) {
-    const PlaneVals<real> Q = load(k + 1);
+    // prefetch plane k + 2 (the last plane any flux of this chunk needs is z1)
+    PlaneRaw<real> Rn;
+    if (k + 2 <= z1) Rn = fetch(k + 2);
+    // and U^n of the output plane k
+    const bool out_here = interior && k >= z0;
+    const uint32_t i_out = cell_of(k);
+    real un[4] = {real(0), real(0), real(0), real(0)};
+    if (STAGE != 0 && out_here) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) un[j] = a.n[j][i_out];
+    }
+    const PlaneVals<real> Q = finish(k + 1, R);
     store_plane((k + 1) & 1, Q);
     __syncthreads();
     const real *Pk = sm + (k & 1) * 6 * EXY;
@@ -227,18 +262,18 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     T[TZY * EXY + t] = tzy;
     __syncthreads();
 
-    if (interior && k >= z0) {
+    if (out_here) {
       const real r_rho = -((P.gx - gx_xm) + (P.gy - gy_ym) + (P.gz - gz_m)) * inv_h;
       const real r_gx = -((T[TXX * EXY + eXp] - txx) + (txy - T[TXY * EXY + eYm]) + (txz - txz_m)) * inv_h;
       const real r_gy = -((T[TYY * EXY + eYp] - tyy) + (tyx - T[TYX * EXY + eXm]) + (tyz - tyz_m)) * inv_h;
       const real r_gz = -((tzz1 - tzz_k) + (tzx - T[TZX * EXY + eXm]) + (tzy - T[TZY * EXY + eYm])) * inv_h;
-      const size_t i = size_t(x) + size_t(NX) * (size_t(y) + size_t(NY) * k);
+      const uint32_t i = i_out;
       real o0 = P.dr + dt * r_rho, o1 = P.gx + dt * r_gx, o2 = P.gy + dt * r_gy, o3 = P.gz + dt * r_gz;
       if (STAGE != 0) {
-        o0 = ca * a.n[0][i] + cb * o0;
-        o1 = ca * a.n[1][i] + cb * o1;
-        o2 = ca * a.n[2][i] + cb * o2;
-        o3 = ca * a.n[3][i] + cb * o3;
+        o0 = ca * un[0] + cb * o0;
+        o1 = ca * un[1] + cb * o1;
+        o2 = ca * un[2] + cb * o2;
+        o3 = ca * un[3] + cb * o3;
       }
       a.o[0][i] = o0;
       a.o[1][i] = o1;
@@ -252,6 +287,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     tyz_m = tyz;
     tzz_k = tzz1;
     P = Q;
+    R = Rn;
   }
   (void)plane;
 
