@@ -355,7 +355,11 @@ struct TileShape<double> {
   static constexpr int TX = 32, TY = 4;
 };
 
-int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, 16); }
+// planes per CTA along z (32 balances the 2.5D prologue against the tail wave at 128^3)
+#ifndef IC_ZCHUNK
+#define IC_ZCHUNK 32
+#endif
+int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, IC_ZCHUNK); }
 
 template <typename real>
 dim3 stage_grid(const ic_ctx *ctx) {
@@ -581,7 +585,7 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
   a.c = c;
   a.step = step;
   a.partials = partials;
-  a.zchunk = std::min<int>(p.nz, 16);
+  a.zchunk = std::min<int>(p.nz, IC_ZCHUNK);
   const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + a.zchunk - 1) / a.zchunk);
   const size_t smem = 18 * EXY * sizeof(real);
   const bool noise_on = p.kT > 0.0;
@@ -604,7 +608,7 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
 }
 
 size_t stage_ctas_raw(const ic_grid_params &p) {
-  const int zc = std::min<int>(p.nz, 16);
+  const int zc = std::min<int>(p.nz, IC_ZCHUNK);
   if (p.precision == IC_FP32) {
     constexpr int TX = TileShape<float>::TX, TY = TileShape<float>::TY;
     return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
