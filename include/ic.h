@@ -167,6 +167,21 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes);
 
 ic_status ic_device_views(ic_ctx *ctx, ic_views *out);
 
+/* Batched ensemble: many independent boxes (contexts on the current device,
+ * each with its own stream, e.g. different sizes, seeds or boxes ids) advanced
+ * together.  ic_batch_step captures the whole ensemble step -- every box's
+ * kernels as parallel branches -- into one CUDA graph per buffer parity and
+ * launches it once per step; each box evolves exactly as under its own
+ * ic_step (the observables of the method are ensemble averages, Sec. 6).
+ * The batch does not own the contexts; modifying a context (adding
+ * particles, restoring) makes the batch re-capture.  All boxes must be at the
+ * same step parity (stepped the same number of times).  w: nsteps weights
+ * applied to every box, or NULL. */
+typedef struct ic_batch ic_batch;
+ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out);
+ic_status ic_batch_step(ic_batch *batch, int nsteps, const double *w);
+void ic_batch_destroy(ic_batch *batch);
+
 /* Kernel timing for measurement.  While enabled, ic_step launches without
  * CUDA graphs and brackets every kernel with CUDA events on the context's
  * stream.  ic_profile_read synchronises and returns, per kernel class

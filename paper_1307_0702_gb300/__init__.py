@@ -12,7 +12,7 @@ from . import workloads  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Grid", "ICError"):
+    if name in ("Grid", "ICError", "Batch"):
         from . import ic
         return getattr(ic, name)
     raise AttributeError(name)

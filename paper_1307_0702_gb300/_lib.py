@@ -50,6 +50,9 @@ SIGNATURES = {
     "ic_checkpoint": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
     "ic_restore": (c_int, [c_void_p, c_void_p, c_size_t]),
     "ic_device_views": (c_int, [c_void_p, POINTER(Views)]),
+    "ic_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+    "ic_batch_step": (c_int, [c_void_p, c_int, PD]),
+    "ic_batch_destroy": (None, [c_void_p]),
     "ic_profile": (c_int, [c_void_p, c_int]),
     "ic_profile_read": (c_int, [c_void_p, PD, POINTER(c_int64), c_int]),
     "ic_fluid_step_noalloc": (c_int, [POINTER(GridParams), POINTER(c_void_p), POINTER(c_void_p), c_int64]),

@@ -78,6 +78,7 @@ ic_status cuda_fail(ic_ctx *ctx, cudaError_t e, const char *where) {
   } while (0)
 
 void invalidate_graphs(ic_ctx *ctx) {
+  ++ctx->generation;
   for (int i = 0; i < 2; ++i)
     if (ctx->graph[i]) {
       cudaGraphExecDestroy(ctx->graph[i]);
@@ -237,6 +238,38 @@ ic_status grow_particles(ic_ctx *ctx, int need) {
   }
   s.cap = cap;
   invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+// Weights of the next nsteps steps (or none) through a pinned staging buffer
+// (the caller's w is only read during the call).
+ic_status upload_weights(ic_ctx *ctx, int nsteps, const double *w) {
+  if (w && nsteps > ctx->weights_cap) {
+    double *fresh = (double *)dev_alloc(ctx, size_t(nsteps) * sizeof(double));
+    if (!fresh) return fail(ctx, IC_ERR_OOM, "weights buffer");
+    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, ctx->d.weights);
+    ctx->d.weights = fresh;
+    cudaFreeHost(ctx->staging);
+    ctx->staging = nullptr;
+    IC_CUDA(ctx, cudaMallocHost(&ctx->staging, (size_t(nsteps) + 3) * sizeof(double)));
+    ctx->weights_cap = nsteps;
+    invalidate_graphs(ctx);
+  }
+  if (w || ctx->host_wcount != 0) {
+    IC_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));   // previous upload has left the staging buffer
+    const int64_t hdr[2] = {ctx->host_step, w ? int64_t(nsteps) : 0};
+    std::memcpy(ctx->staging, hdr, sizeof(hdr));
+    size_t bytes = sizeof(hdr);
+    if (w) {
+      std::memcpy(ctx->staging + 2, w, size_t(nsteps) * sizeof(double));
+      IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.weights, ctx->staging + 2, size_t(nsteps) * sizeof(double),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    }
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.step + 1, ctx->staging, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    IC_CUDA(ctx, cudaEventRecord(ctx->staging_done, ctx->stream));
+    ctx->host_wcount = w ? nsteps : 0;
+  }
   return IC_OK;
 }
 
@@ -435,34 +468,9 @@ ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u,
 ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w) {
   if (!ctx || nsteps < 0) return IC_ERR_ARG;
   if (nsteps == 0) return IC_OK;
-  if (w && nsteps > ctx->weights_cap) {
-    double *fresh = (double *)dev_alloc(ctx, size_t(nsteps) * sizeof(double));
-    if (!fresh) return fail(ctx, IC_ERR_OOM, "weights buffer");
-    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    dev_free(ctx, ctx->d.weights);
-    ctx->d.weights = fresh;
-    cudaFreeHost(ctx->staging);
-    ctx->staging = nullptr;
-    IC_CUDA(ctx, cudaMallocHost(&ctx->staging, (size_t(nsteps) + 3) * sizeof(double)));
-    ctx->weights_cap = nsteps;
-    invalidate_graphs(ctx);
-  }
-  // Weights go through a pinned staging buffer (the caller's w is only read
-  // during this call); with w == NULL nothing is uploaded unless weights of an
-  // earlier call are still active.
-  if (w || ctx->host_wcount != 0) {
-    IC_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));   // previous upload has left the staging buffer
-    const int64_t hdr[2] = {ctx->host_step, w ? int64_t(nsteps) : 0};
-    std::memcpy(ctx->staging, hdr, sizeof(hdr));
-    size_t bytes = sizeof(hdr);
-    if (w) {
-      std::memcpy(ctx->staging + 2, w, size_t(nsteps) * sizeof(double));
-      IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.weights, ctx->staging + 2, size_t(nsteps) * sizeof(double),
-                                   cudaMemcpyHostToDevice, ctx->stream));
-    }
-    IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.step + 1, ctx->staging, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    IC_CUDA(ctx, cudaEventRecord(ctx->staging_done, ctx->stream));
-    ctx->host_wcount = w ? nsteps : 0;
+  {
+    const ic_status st = upload_weights(ctx, nsteps, w);
+    if (st) return st;
   }
   const bool use_graph = graphs_enabled() && !ctx->profiling;
   for (int i = 0; i < nsteps; ++i) {
@@ -670,6 +678,116 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
   IC_CUDA(ctx, cudaMemcpy(ctx->d.status, st2, sizeof(st2), cudaMemcpyHostToDevice));
   invalidate_graphs(ctx);
   return IC_OK;
+}
+
+}  // extern "C"
+
+struct ic_batch {
+  std::vector<ic_ctx *> ctxs;
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<uint64_t> gens[2];
+};
+
+namespace {
+void batch_drop_graphs(ic_batch *b) {
+  for (int i = 0; i < 2; ++i)
+    if (b->graph[i]) {
+      cudaGraphExecDestroy(b->graph[i]);
+      b->graph[i] = nullptr;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out) {
+  if (!ctxs || n <= 0 || !out) return IC_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return IC_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return IC_ERR_ARG;   // distinct streams
+  }
+  ic_batch *b = new ic_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->joins.resize(n, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < n; ++i) ok = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    ic_batch_destroy(b);
+    return IC_ERR_CUDA;
+  }
+  *out = b;
+  return IC_OK;
+}
+
+ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
+  if (!b || nsteps < 0) return IC_ERR_ARG;
+  if (nsteps == 0) return IC_OK;
+  const int parity = b->ctxs[0]->cur;
+  for (ic_ctx *c : b->ctxs) {
+    if (c->cur != parity || c->profiling) return fail(c, IC_ERR_STATE, "batched boxes must share the step parity");
+    const ic_status st = upload_weights(c, nsteps, w);
+    if (st) return st;
+  }
+  // the boxes' own work (weight uploads, earlier steps) precedes the batch graph
+  for (ic_ctx *c : b->ctxs) {
+    if (cudaEventRecord(b->joins[0], c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->main, b->joins[0], 0) != cudaSuccess)
+      return IC_ERR_CUDA;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const int par = b->ctxs[0]->cur;
+    bool stale = !b->graph[par] || b->gens[par].size() != b->ctxs.size();
+    for (size_t i = 0; !stale && i < b->ctxs.size(); ++i) stale = b->gens[par][i] != b->ctxs[i]->generation;
+    if (stale) {
+      if (b->graph[par]) {
+        cudaGraphExecDestroy(b->graph[par]);
+        b->graph[par] = nullptr;
+      }
+      cudaGraph_t graph;
+      if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return IC_ERR_CUDA;
+      cudaError_t e = cudaEventRecord(b->fork, b->main);
+      for (size_t i = 0; e == cudaSuccess && i < b->ctxs.size(); ++i) {
+        ic_ctx *c = b->ctxs[i];
+        e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+        if (e == cudaSuccess) e = enqueue_step(c, c->cur);
+        if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->joins[i], 0);
+      }
+      const cudaError_t ce = cudaStreamEndCapture(b->main, &graph);
+      if (e != cudaSuccess || ce != cudaSuccess) return IC_ERR_CUDA;
+      const cudaError_t ie = cudaGraphInstantiate(&b->graph[par], graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return IC_ERR_CUDA;
+      b->gens[par].clear();
+      for (ic_ctx *c : b->ctxs) b->gens[par].push_back(c->generation);
+    }
+    if (cudaGraphLaunch(b->graph[par], b->main) != cudaSuccess) return IC_ERR_CUDA;
+    for (ic_ctx *c : b->ctxs) c->cur = 1 - c->cur;
+  }
+  // later calls on any box are ordered after the batch
+  if (cudaEventRecord(b->fork, b->main) != cudaSuccess) return IC_ERR_CUDA;
+  for (ic_ctx *c : b->ctxs) {
+    if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) return IC_ERR_CUDA;
+    c->host_step += nsteps;
+  }
+  return IC_OK;
+}
+
+void ic_batch_destroy(ic_batch *b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  batch_drop_graphs(b);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->main) cudaStreamDestroy(b->main);
+  delete b;
 }
 
 ic_status ic_device_views(ic_ctx *ctx, ic_views *out) {

@@ -84,6 +84,7 @@ struct ic_ctx {
   double *staging = nullptr;        // pinned host staging for weights (cap + 3)
   cudaEvent_t staging_done = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
+  uint64_t generation = 0;                          // bumped whenever the captured step changes
   std::string err;
   double omega = 0, force_amp = 0, kwave = 0;
   // kernel timing (ic_profile): event pairs per kernel class

@@ -210,3 +210,42 @@ class Grid:
             out["q"] = torch.as_tensor(_Arr(v.q, (v.n_particles, 3), "<i8" if v.precision == IC_FP32 else "<f8"),
                                        device=self.device)
         return out
+
+
+class Batch:
+    """An ensemble of Grids advanced together: one CUDA graph launch per step
+    holds every box's kernels as parallel branches (ic_batch_*).  The Grids
+    stay usable on their own; the batch does not own them."""
+
+    def __init__(self, grids):
+        self._lib = _lib.load()
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g._ctx.value for g in self.grids])
+        self._b = ctypes.c_void_p()
+        st = self._lib.ic_batch_create(arr, len(self.grids), ctypes.byref(self._b))
+        if st != 0:
+            raise ICError(st, "ic_batch_create failed (grids must have distinct streams)")
+
+    def step(self, nsteps=1, weights=None):
+        w = None if weights is None else _f64(weights)
+        st = self._lib.ic_batch_step(self._b, int(nsteps), _ptr(w))
+        if st != 0:
+            msg = self._lib.ic_last_error(self.grids[0]._ctx)
+            raise ICError(st, msg.decode() if msg else "ic_batch_step failed")
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._lib.ic_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
