@@ -170,6 +170,86 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+ENSEMBLE_METRIC = "cell-updates/s and particle-steps/s (ensemble of 256 boxes, edges 16/24/32/48, 1-200 particles)"
+
+
+def run_ensemble(args):
+    """Batched ensemble: 256 FP32 boxes advanced by ic_batch_step (one CUDA graph
+    launch per step), after ic_batch_autotune; beside it the same ensemble with
+    the default tiling and unbatched (one ic_step per box per step)."""
+    import torch
+
+    from paper_1307_0702_gb300 import Batch, workloads as W
+
+    cfg = W.ensemble_config(args.boxes)
+    grids = [setup_box(gp, parts, seed_thermal=5000 + b) for b, (gp, parts) in enumerate(cfg)]
+    cells = sum(g.shape[0] * g.shape[1] * g.shape[2] for g in grids)
+    npart = sum(g.n_particles for g in grids)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    s0 = grids[0].stream
+
+    def timed(step_fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            with torch.cuda.stream(s0):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(s0)
+            step_fn()
+            with torch.cuda.stream(s0):
+                ev[i][1].record(s0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        return float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3, wall
+
+    def unbatched():
+        for g in grids:
+            g.step(1)
+        # the end event waits for every box
+        for g in grids[1:]:
+            e = torch.cuda.Event()
+            e.record(g.stream)
+            s0.wait_event(e)
+
+    batch = Batch(grids)
+    batch.step(args.warmup)
+    t_default, wall_default = timed(lambda: batch.step(1), args.steps)
+    tiles = batch.autotune(reps=3)
+    batch.step(args.warmup)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    time.sleep(0.3)
+    t_batch, wall_batch = timed(lambda: batch.step(1), args.steps)
+    clocks = sampler.stop()
+    for g in grids:
+        g.step(args.warmup)
+    t_unb, wall_unb = timed(unbatched, args.steps)
+    by_edge = {}
+    for g, t in zip(grids, tiles):
+        by_edge.setdefault(str(g.shape[2]), [list(t)])
+    line = {
+        "metric": ENSEMBLE_METRIC, "value": cells * args.steps / t_batch, "unit": "cell-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble: 256 FP32 boxes, edges uniform in {16,24,32,48}, 1-200 particles each "
+                               "(min sep 2h), kT=1e-3, Philox seed = box index, one CUDA graph per step",
+                   "boxes": len(grids), "cells": cells, "particles": npart,
+                   "l2": "flushed between timed steps (512 MB write, outside the step events)"},
+        "particle_steps_per_s": npart * args.steps / t_batch,
+        "tiles_by_edge": {k: v[0] for k, v in sorted(by_edge.items(), key=lambda kv: int(kv[0]))},
+        "default_tiling": {"value": cells * args.steps / t_default, "ms_per_step": 1e3 * t_default / args.steps},
+        "unbatched": {"value": cells * args.steps / t_unb, "ms_per_step": 1e3 * t_unb / args.steps,
+                      "wall_ms_per_step": 1e3 * wall_unb / args.steps},
+        "wall_ms_per_step": 1e3 * wall_batch / args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for g in grids:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +261,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="box", choices=["box", "ensemble"],
+                    help="box: the 128^3 single box (default); ensemble: the batched 256-box ensemble")
+    ap.add_argument("--boxes", type=int, default=256)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -195,6 +278,10 @@ def main():
     import torch.distributed as dist
 
     torch.cuda.set_device(local)
+    if args.workload == "ensemble":
+        if rank == 0:
+            run_ensemble(args)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1307_0702_gb300 import workloads as W

@@ -167,10 +167,11 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes);
 
 ic_status ic_device_views(ic_ctx *ctx, ic_views *out);
 
-/* Batched ensemble: many independent boxes (contexts on the current device,
- * each with its own stream, e.g. different sizes, seeds or boxes ids) advanced
- * together.  ic_batch_step captures the whole ensemble step -- every box's
- * kernels as parallel branches -- into one CUDA graph per buffer parity and
+/* Batched ensemble: many independent boxes (distinct contexts on the current
+ * device, e.g. different sizes, seeds or box ids) advanced together.
+ * ic_batch_step captures the whole ensemble step -- every box's kernels as a
+ * branch on the box's stream; boxes that share a stream run one after the
+ * other in it -- into one CUDA graph per buffer parity and
  * launches it once per step; each box evolves exactly as under its own
  * ic_step (the observables of the method are ensemble averages, Sec. 6).
  * The batch does not own the contexts; modifying a context (adding
@@ -181,6 +182,26 @@ typedef struct ic_batch ic_batch;
 ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out);
 ic_status ic_batch_step(ic_batch *batch, int nsteps, const double *w);
 void ic_batch_destroy(ic_batch *batch);
+
+/* Stage-kernel tiling.  The paper has no counterpart: this is a performance
+ * setting.  The RK3 stage kernel marches CTAs of tile_x x tile_y cells along
+ * z in chunks of zchunk planes; tile_x is 32 or 16 (tile_y is fixed per
+ * precision: 8 in FP32, 4 in FP64).  Every field, particle and force is bit
+ * for bit the same under every tiling; only the driven-mode amplitude A(t)
+ * and <A^2>_w change, by the rounding of their reduction order.
+ * ic_set_tile: IC_ERR_ARG for tile_x not 16 or 32, or zchunk < 8 (unless it is
+ * at least nz).  ic_get_tile: the current tiling (each pointer may be NULL).
+ * ic_autotune synchronises the stream, times the three stage kernels of every
+ * candidate (tile_x 32 and 16; zchunk 32, 16 and 8, clipped to nz), reps
+ * repetitions each, on the context's scratch buffers (U^n is left untouched:
+ * the state is unchanged) and keeps the fastest; choice[3] (or NULL) receives
+ * tile_x, tile_y, zchunk.  ic_batch_autotune tunes one context of each
+ * distinct grid shape and precision of the batch and gives the choice to the
+ * others. */
+ic_status ic_set_tile(ic_ctx *ctx, int tile_x, int zchunk);
+ic_status ic_get_tile(const ic_ctx *ctx, int *tile_x, int *tile_y, int *zchunk);
+ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice);
+ic_status ic_batch_autotune(ic_batch *batch, int reps);
 
 /* Kernel timing for measurement.  While enabled, ic_step launches without
  * CUDA graphs and brackets every kernel with CUDA events on the context's

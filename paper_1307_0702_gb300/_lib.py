@@ -53,6 +53,10 @@ SIGNATURES = {
     "ic_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
     "ic_batch_step": (c_int, [c_void_p, c_int, PD]),
     "ic_batch_destroy": (None, [c_void_p]),
+    "ic_set_tile": (c_int, [c_void_p, c_int, c_int]),
+    "ic_get_tile": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ic_autotune": (c_int, [c_void_p, c_int, POINTER(c_int)]),
+    "ic_batch_autotune": (c_int, [c_void_p, c_int]),
     "ic_profile": (c_int, [c_void_p, c_int]),
     "ic_profile_read": (c_int, [c_void_p, PD, POINTER(c_int64), c_int]),
     "ic_fluid_step_noalloc": (c_int, [POINTER(GridParams), POINTER(c_void_p), POINTER(c_void_p), c_int64]),

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <vector>
 
 #include "ic_internal.hpp"
@@ -709,7 +710,7 @@ ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out) {
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return IC_ERR_ARG;
     for (int j = 0; j < i; ++j)
-      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return IC_ERR_ARG;   // distinct streams
+      if (ctxs[j] == ctxs[i]) return IC_ERR_ARG;   // a box appears once
   }
   ic_batch *b = new ic_batch();
   b->ctxs.assign(ctxs, ctxs + n);
@@ -775,6 +776,102 @@ ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
   for (ic_ctx *c : b->ctxs) {
     if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) return IC_ERR_CUDA;
     c->host_step += nsteps;
+  }
+  return IC_OK;
+}
+
+ic_status ic_set_tile(ic_ctx *ctx, int tile_x, int zchunk) {
+  if (!ctx || (tile_x != 16 && tile_x != 32)) return IC_ERR_ARG;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!ic::set_stage_tile(ctx, tile_x == 16 ? 1 : 0, zchunk)) return fail(ctx, IC_ERR_ARG, "zchunk below 8");
+  invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+ic_status ic_get_tile(const ic_ctx *ctx, int *tile_x, int *tile_y, int *zchunk) {
+  if (!ctx) return IC_ERR_ARG;
+  int t[3];
+  ic::stage_tile(ctx, &t[0], &t[1], &t[2]);
+  if (tile_x) *tile_x = t[0];
+  if (tile_y) *tile_y = t[1];
+  if (zchunk) *zchunk = t[2];
+  return IC_OK;
+}
+
+ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
+  if (!ctx || reps <= 0) return IC_ERR_ARG;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // the stage kernels of one step, U^n (buffer cur) only read: stage 1 writes
+  // the other state buffer, stage 2 the half-step buffer, stage 3 the other
+  // state buffer again (all three, the noise and the partials are scratch
+  // until the next step rewrites them)
+  void *const *U0 = ctx->U[ctx->cur];
+  void *const *U1 = ctx->U[1 - ctx->cur];
+  void *const *U2 = ctx->U[2];
+  auto stages = [&]() {
+    cudaError_t e = ic::launch_stage(ctx, 0, U0, U0, U1);
+    if (e == cudaSuccess) e = ic::launch_stage(ctx, 1, U1, U0, U2);
+    if (e == cudaSuccess) e = ic::launch_stage(ctx, 2, U2, U0, U1);
+    return e;
+  };
+  cudaEvent_t e0, e1;
+  IC_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, IC_ERR_CUDA, "cudaEventCreate");
+  }
+  int best_v = ctx->tile_variant, best_z = ctx->zchunk;
+  float best_ms = -1.0f;
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+    int last = -1;
+    for (int z : {32, 16, 8}) {
+      const int zc = std::min(z, ctx->p.nz);
+      if (zc == last || !ic::set_stage_tile(ctx, v, zc)) continue;
+      last = zc;
+      err = stages();   // warm-up
+      if (err == cudaSuccess) err = cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < reps && err == cudaSuccess; ++r) err = stages();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, ctx->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) break;
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best_v = v;
+        best_z = zc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ic::set_stage_tile(ctx, best_v, best_z);
+  invalidate_graphs(ctx);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "autotune");
+  if (choice) ic::stage_tile(ctx, &choice[0], &choice[1], &choice[2]);
+  return IC_OK;
+}
+
+ic_status ic_batch_autotune(ic_batch *b, int reps) {
+  if (!b || reps <= 0) return IC_ERR_ARG;
+  std::vector<std::array<int, 6>> keys;
+  std::vector<ic_ctx *> tuned;
+  for (ic_ctx *c : b->ctxs) {
+    const std::array<int, 6> key{c->p.nx, c->p.ny, c->p.nz, c->p.precision, c->p.kT > 0.0 ? 1 : 0,
+                                 c->ps.n > 0 ? 1 : 0};
+    size_t j = 0;
+    while (j < keys.size() && keys[j] != key) ++j;
+    if (j == keys.size()) {
+      const ic_status st = ic_autotune(c, reps, nullptr);
+      if (st) return st;
+      keys.push_back(key);
+      tuned.push_back(c);
+    } else {
+      IC_CUDA(c, cudaStreamSynchronize(c->stream));
+      ic::set_stage_tile(c, tuned[j]->tile_variant, tuned[j]->zchunk);
+      invalidate_graphs(c);
+    }
   }
   return IC_OK;
 }

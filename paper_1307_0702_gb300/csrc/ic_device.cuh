@@ -186,6 +186,12 @@ __device__ __forceinline__ int ring_delta(int b, int a, int n) {
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
+// a * b + c with one rounding, never split by the compiler: values that more
+// than one CTA computes for the same cell (halo planes) must round the same
+// way in every inlined copy of the code that produces them
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename real>
 __device__ __forceinline__ real warp_sum(real v) {
 #pragma unroll

@@ -73,12 +73,15 @@ constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
 #define IC_FP32_MIN_CTAS 2
 #endif
 
-// CTAs per SM the register budget is sized for
-template <typename real>
-constexpr int min_ctas() { return sizeof(real) == 4 ? IC_FP32_MIN_CTAS : 1; }
+// CTAs per SM the register budget is sized for: in FP32 the budget of
+// IC_FP32_MIN_CTAS wide (34 x (TY + 2)-thread) CTAs, whatever the tile
+template <typename real, int EXY>
+constexpr int min_ctas() {
+  return sizeof(real) == 4 ? (IC_FP32_MIN_CTAS * 34 * (IC_FP32_TILE_Y + 2) + EXY - 1) / EXY : 1;
+}
 
 template <typename real, int TX, int TY, int STAGE, bool NOISE>
-__global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) * (TY + 2)>())
     k_rk3_stage(const StageArgs<real> a) {
   constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
   enum { GX = 0, GY, GZ, VX, VY, VZ };
@@ -155,20 +158,20 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real>())
     v.gy = r.gy;
     v.gz = r.gz;
     v.pp = r.pp;
-    v.vx = fdiv(v.gx, rho0 + half * (v.dr + r.drx));
-    v.vy = fdiv(v.gy, rho0 + half * (v.dr + r.dry));
-    v.vz = fdiv(v.gz, rho0 + half * (v.dr + r.drz));
+    v.vx = fdiv(v.gx, fma_rn(half, v.dr + r.drx, rho0));
+    v.vy = fdiv(v.gy, fma_rn(half, v.dr + r.dry, rho0));
+    v.vz = fdiv(v.gz, fma_rn(half, v.dr + r.drz, rho0));
     if (NOISE && STAGE == 0) {
       // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
       const uint32_t i = cell_of(kk);
       real wa[6], wb[6];
       stress_normals_ab(key, uint32_t(i), ustep, wa, wb);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) v.nz[j] = wa[j] + beta * wb[j];
+      for (int j = 0; j < 6; ++j) v.nz[j] = fma_rn(beta, wb[j], wa[j]);
       if (interior && kk >= z0 && kk < z1) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          a.noise_out[j][i] = wa[j] + real(1.7320508075688772) * wb[j];
+          a.noise_out[j][i] = fma_rn(real(1.7320508075688772), wb[j], wa[j]);
           a.noise_out[6 + j][i] = wa[j];
         }
       }
@@ -344,34 +347,46 @@ FluidConsts<real> fluid_consts(const ic_ctx *ctx) {
   return c;
 }
 
-template <typename real>
+// Tile shapes of the stage kernel: variant 0 is the wide tile tuned for large
+// boxes; variant 1 halves the x extent so that 16- and 48-cell boxes fill
+// their tiles (the autotuner picks between them and the z chunk).
+template <typename real, int V>
 struct TileShape;
 template <>
-struct TileShape<float> {
+struct TileShape<float, 0> {
   static constexpr int TX = 32, TY = IC_FP32_TILE_Y;
 };
 template <>
-struct TileShape<double> {
+struct TileShape<float, 1> {
+  static constexpr int TX = 16, TY = IC_FP32_TILE_Y;
+};
+template <>
+struct TileShape<double, 0> {
   static constexpr int TX = 32, TY = 4;
+};
+template <>
+struct TileShape<double, 1> {
+  static constexpr int TX = 16, TY = 4;
 };
 
 // planes per CTA along z (32 balances the 2.5D prologue against the tail wave at 128^3)
 #ifndef IC_ZCHUNK
 #define IC_ZCHUNK 32
 #endif
-int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, IC_ZCHUNK); }
+int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, ctx->zchunk > 0 ? ctx->zchunk : IC_ZCHUNK); }
 
 template <typename real>
 dim3 stage_grid(const ic_ctx *ctx) {
-  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  const int TX = ctx->tile_variant == 1 ? TileShape<real, 1>::TX : TileShape<real, 0>::TX;
+  const int TY = ctx->tile_variant == 1 ? TileShape<real, 1>::TY : TileShape<real, 0>::TY;
   const int zc = zchunk_for(ctx);
   return dim3((ctx->p.nx + TX - 1) / TX, (ctx->p.ny + TY - 1) / TY, (ctx->p.nz + zc - 1) / zc);
 }
 
-template <typename real, int STAGE, bool NOISE>
+template <typename real, int V, int STAGE, bool NOISE>
 cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const in_n[4],
                            void *const out[4]) {
-  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  constexpr int TX = TileShape<real, V>::TX, TY = TileShape<real, V>::TY;
   constexpr int EXY = (TX + 2) * (TY + 2);
   StageArgs<real> a;
   for (int j = 0; j < 4; ++j) {
@@ -394,18 +409,25 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_stage_r(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+template <typename real, int V>
+cudaError_t launch_stage_v(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
                            void *const out[4]) {
   const bool noise = ctx->p.kT > 0.0;
   switch (stage * 2 + (noise ? 1 : 0)) {
-    case 0: return launch_stage_t<real, 0, false>(ctx, in_s, in_n, out);
-    case 1: return launch_stage_t<real, 0, true>(ctx, in_s, in_n, out);
-    case 2: return launch_stage_t<real, 1, false>(ctx, in_s, in_n, out);
-    case 3: return launch_stage_t<real, 1, true>(ctx, in_s, in_n, out);
-    case 4: return launch_stage_t<real, 2, false>(ctx, in_s, in_n, out);
-    default: return launch_stage_t<real, 2, true>(ctx, in_s, in_n, out);
+    case 0: return launch_stage_t<real, V, 0, false>(ctx, in_s, in_n, out);
+    case 1: return launch_stage_t<real, V, 0, true>(ctx, in_s, in_n, out);
+    case 2: return launch_stage_t<real, V, 1, false>(ctx, in_s, in_n, out);
+    case 3: return launch_stage_t<real, V, 1, true>(ctx, in_s, in_n, out);
+    case 4: return launch_stage_t<real, V, 2, false>(ctx, in_s, in_n, out);
+    default: return launch_stage_t<real, V, 2, true>(ctx, in_s, in_n, out);
   }
+}
+
+template <typename real>
+cudaError_t launch_stage_r(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+                           void *const out[4]) {
+  if (ctx->tile_variant == 1) return launch_stage_v<real, 1>(ctx, stage, in_s, in_n, out);
+  return launch_stage_v<real, 0>(ctx, stage, in_s, in_n, out);
 }
 
 // ------------------------------------------------------------ thermal state
@@ -555,8 +577,24 @@ void drive_amplitudes(const ic_ctx *ctx, int64_t step, double out[3]) {
 }
 
 size_t fluid_num_partials(const ic_ctx *ctx) {
-  const dim3 g = ctx->p.precision == IC_FP32 ? stage_grid<float>(ctx) : stage_grid<double>(ctx);
-  return std::max<size_t>(size_t(g.x) * g.y * g.z, size_t(kRedBlocks) * 4);
+  // the most CTAs any tile variant and z chunk the tuner may choose can launch
+  const int ty = std::min<int>(TileShape<float, 1>::TY, TileShape<double, 1>::TY);
+  const size_t n = size_t((ctx->p.nx + 15) / 16) * ((ctx->p.ny + ty - 1) / ty) * ((ctx->p.nz + kMinZChunk - 1) / kMinZChunk);
+  return std::max<size_t>(n, size_t(kRedBlocks) * 4);
+}
+
+bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk) {
+  if (variant < 0 || variant > 1 || (zchunk < kMinZChunk && zchunk < ctx->p.nz)) return false;
+  ctx->tile_variant = variant;
+  ctx->zchunk = std::min(zchunk, ctx->p.nz);
+  return true;
+}
+
+void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk) {
+  const bool f = ctx->p.precision == IC_FP32, v1 = ctx->tile_variant == 1;
+  *tx = v1 ? 16 : 32;
+  *ty = f ? TileShape<float, 0>::TY : TileShape<double, 0>::TY;
+  *zchunk = zchunk_for(ctx);
 }
 
 cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
@@ -570,7 +608,7 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
                                const void *const in_s[4], const void *const in_n[4], void *const out[4],
                                void *const noise[12], const int64_t *step, double *partials,
                                cudaStream_t stream) {
-  constexpr int TX = TileShape<real>::TX, TY = TileShape<real>::TY;
+  constexpr int TX = TileShape<real, 0>::TX, TY = TileShape<real, 0>::TY;
   constexpr int EXY = (TX + 2) * (TY + 2);
   StageArgs<real> a;
   for (int j = 0; j < 4; ++j) {
@@ -610,10 +648,10 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
 size_t stage_ctas_raw(const ic_grid_params &p) {
   const int zc = std::min<int>(p.nz, IC_ZCHUNK);
   if (p.precision == IC_FP32) {
-    constexpr int TX = TileShape<float>::TX, TY = TileShape<float>::TY;
+    constexpr int TX = TileShape<float, 0>::TX, TY = TileShape<float, 0>::TY;
     return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
   }
-  constexpr int TX = TileShape<double>::TX, TY = TileShape<double>::TY;
+  constexpr int TX = TileShape<double, 0>::TX, TY = TileShape<double, 0>::TY;
   return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
 }
 

@@ -85,6 +85,8 @@ struct ic_ctx {
   cudaEvent_t staging_done = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
   uint64_t generation = 0;                          // bumped whenever the captured step changes
+  int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)
+  int zchunk = 0;          // planes per stage-kernel CTA along z (0 = default)
   std::string err;
   double omega = 0, force_amp = 0, kwave = 0;
   // kernel timing (ic_profile): event pairs per kernel class
@@ -119,6 +121,10 @@ cudaError_t launch_stage_raw(const ic_grid_params &p, const void *consts, int st
                              const void *const in_n[4], void *const out[4], void *const noise[12],
                              const int64_t *step, double *partials, cudaStream_t stream);
 size_t stage_ctas_raw(const ic_grid_params &p);
+// stage-kernel tiling: variant 0 (32-wide) or 1 (16-wide) and the z chunk
+constexpr int kMinZChunk = 8;
+bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk);
+void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk);
 
 // particles (ic_particles.cu)
 enum ParticlePhase { kHalfStep = 0, kPressure = 1, kForce = 2, kImpulse = 3, kSpread = 4, kFinal = 5 };

@@ -179,6 +179,22 @@ class Grid:
         self._check(self._lib.ic_restore(self._ctx, buf, len(blob)))
         self.n_particles = int(np.frombuffer(blob[28:32], dtype=np.int32)[0])
 
+    def set_tile(self, tile_x, zchunk):
+        """Stage-kernel tiling (tile_x 32 or 16, zchunk >= 8 planes); results are unchanged."""
+        self._check(self._lib.ic_set_tile(self._ctx, int(tile_x), int(zchunk)))
+
+    def tile(self):
+        """(tile_x, tile_y, zchunk) of the stage kernel."""
+        t = [ctypes.c_int() for _ in range(3)]
+        self._check(self._lib.ic_get_tile(self._ctx, *[ctypes.byref(x) for x in t]))
+        return tuple(x.value for x in t)
+
+    def autotune(self, reps=5):
+        """Time every stage-kernel tiling on scratch buffers, keep the fastest; returns it."""
+        out = (ctypes.c_int * 3)()
+        self._check(self._lib.ic_autotune(self._ctx, int(reps), out))
+        return tuple(out)
+
     def profile(self, enable=True):
         """Kernel timing on/off (graphs are off while it is on)."""
         self._check(self._lib.ic_profile(self._ctx, 1 if enable else 0))
@@ -224,7 +240,7 @@ class Batch:
         self._b = ctypes.c_void_p()
         st = self._lib.ic_batch_create(arr, len(self.grids), ctypes.byref(self._b))
         if st != 0:
-            raise ICError(st, "ic_batch_create failed (grids must have distinct streams)")
+            raise ICError(st, "ic_batch_create failed (each grid may appear once)")
 
     def step(self, nsteps=1, weights=None):
         w = None if weights is None else _f64(weights)
@@ -232,6 +248,13 @@ class Batch:
         if st != 0:
             msg = self._lib.ic_last_error(self.grids[0]._ctx)
             raise ICError(st, msg.decode() if msg else "ic_batch_step failed")
+
+    def autotune(self, reps=5):
+        """Tune the stage tiling once per distinct box shape; returns each box's tiling."""
+        st = self._lib.ic_batch_autotune(self._b, int(reps))
+        if st != 0:
+            raise ICError(st, "ic_batch_autotune failed")
+        return [g.tile() for g in self.grids]
 
     def close(self):
         if getattr(self, "_b", None) and self._b.value:

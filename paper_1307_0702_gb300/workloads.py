@@ -169,6 +169,23 @@ def large_box_config(n=128, n_particles=10000):
                                 precision="fp32", place_seed=3)
 
 
+def ensemble_config(n_boxes=256, sizes=(16, 24, 32, 48), max_particles=200, seed=0):
+    """Heterogeneous ensemble: box edges uniform over ``sizes``, 1..max_particles
+    particles per box (uniform count, min separation 2h), contrasts of the
+    single-particle case (m_p = 1.5 rho0 V, kappa_p = 0.5 kappa_f), kT = 1e-3,
+    FP32, Philox seed = box index.  Returns [(grid params, particles)]."""
+    rng = np.random.default_rng(seed)
+    edges = rng.choice(np.asarray(sizes), n_boxes)
+    counts = rng.integers(1, max_particles + 1, n_boxes)
+    out = []
+    for b in range(n_boxes):
+        gp, parts = many_particle_config(int(edges[b]), int(counts[b]), kT=1e-3, wave_amp=1e-3, seed=b,
+                                         min_sep=2.0, fixed_contrast=(1.5, 0.5), precision="fp32",
+                                         place_seed=10000 + b)
+        out.append((gp, parts))
+    return out
+
+
 def blackman_harris(nsteps, skip=0):
     """Averaging weights: zero for the first ``skip`` steps, then a 4-term
     Blackman-Harris window normalised to sum 1."""

@@ -10,7 +10,7 @@ from paper_1307_0702_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def make_boxes(prec):
+def make_boxes(prec, stream=None):
     from paper_1307_0702_gb300 import Grid
 
     specs = [(16, 3, 0), (24, 7, 1), (16, 0, 2), (20, 12, 3)]
@@ -20,7 +20,7 @@ def make_boxes(prec):
                                            k_spring=0.4 if box % 2 else 0.0)
         gp["box"] = box
         rho, g = W.standing_wave_fields(gp)
-        grid = Grid(gp)
+        grid = Grid(gp, stream=stream)
         grid.set_state(rho, g)
         grid.init_thermal(100 + box)
         if npart:
@@ -60,4 +60,84 @@ def test_batch_equals_individual_steps(prec):
         for u, v in zip(x, y):
             assert np.array_equal(u, v)
     for g in a_grids + b_grids:
+        g.close()
+
+
+def test_batch_boxes_sharing_one_stream():
+    import torch
+
+    from paper_1307_0702_gb300 import Batch
+
+    a_grids, _ = make_boxes("fp32", stream=torch.cuda.Stream())
+    with Batch(a_grids) as batch:
+        batch.step(4, np.ones(4))
+    b_grids, _ = make_boxes("fp32")
+    for g in b_grids:
+        g.step(4, np.ones(4))
+    for ga, gb in zip(a_grids, b_grids):
+        for u, v in zip(snapshot(ga), snapshot(gb)):
+            assert np.array_equal(u, v)
+    for g in a_grids + b_grids:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tiling_leaves_results_unchanged(prec):
+    """Every stage-kernel tiling gives the same fields, particles and forces
+    bit for bit (only the reduction order of A(t) changes)."""
+    from paper_1307_0702_gb300 import Grid
+
+    runs = []
+    for tile in [(32, 32), (16, 8), (32, 8), (16, 16)]:
+        gp, parts = W.many_particle_config((40, 20, 18), 9, kT=1e-3, wave_amp=2e-3, seed=5, precision=prec,
+                                           k_spring=0.3)
+        rho, g = W.standing_wave_fields(gp)
+        with Grid(gp) as grid:
+            grid.set_tile(*tile)
+            assert grid.tile()[0] == tile[0] and grid.tile()[2] == min(tile[1], 18)
+            grid.set_state(rho, g)
+            grid.init_thermal(4)
+            grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])
+            grid.step(6, np.ones(6))
+            runs.append(snapshot(grid))
+    for other in runs[1:]:
+        for u, v in zip(runs[0][:-1], other[:-1]):
+            assert np.array_equal(u, v)
+        assert np.allclose(runs[0][-1], other[-1], rtol=1e-5 if prec == "fp32" else 1e-12, atol=0)
+
+
+def test_autotune_keeps_state_and_results():
+    from paper_1307_0702_gb300 import Batch, Grid
+
+    def fresh():
+        gp, parts = W.many_particle_config(24, 5, kT=1e-3, wave_amp=2e-3, seed=8, precision="fp32")
+        rho, g = W.standing_wave_fields(gp)
+        grid = Grid(gp)
+        grid.set_state(rho, g)
+        grid.init_thermal(1)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"])
+        return grid
+
+    a, b = fresh(), fresh()
+    a.step(2, np.ones(2))
+    b.step(2, np.ones(2))
+    before = snapshot(a)
+    choice = a.autotune(reps=2)
+    assert choice[0] in (16, 32) and choice[2] in (8, 16, 24)
+    for u, v in zip(before, snapshot(a)):
+        assert np.array_equal(u, v)
+    a.step(3, np.ones(3))
+    b.step(3, np.ones(3))
+    for u, v in zip(snapshot(a)[:-1], snapshot(b)[:-1]):
+        assert np.array_equal(u, v)
+    c = fresh()
+    c.step(5, np.ones(5))
+    with Batch([a, c]) as batch:
+        tiles = batch.autotune(reps=1)
+        assert tiles[0] == tiles[1]
+        batch.step(2, np.ones(2))
+    b.step(2, np.ones(2))
+    for u, v in zip(snapshot(a)[:-1], snapshot(b)[:-1]):
+        assert np.array_equal(u, v)
+    for g in (a, b, c):
         g.close()
