@@ -19,6 +19,9 @@ fluid   : conservative staggered flux divergence and the SSP-RK3 substep
           (Sec. 4.2 Eqs. (eq:consvDens), (eq:consvMom), (totp); App. A.2).
 ic      : the full IC time step, substeps 1-7 of App. A.2, with the particle
           pressure of Eqs. (eq:pressure), (omega).
+slabs   : the same step with the box split into z-slabs over ranks (halo
+          exchange, owner-computed particle gathers, replicated spreads),
+          pinned bit for bit to ``ic`` over gloo ranks.
 theory  : closed forms used as pins (Eqs. (eq:acousticForce2), (f1), (f2),
           (part_svel), (ke), (eq:densityVariance); discrete dispersion).
 

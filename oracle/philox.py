@@ -108,7 +108,12 @@ def stress_normals(seed, box, step, ncells):
 
     Rows 0..5 are W_A (xx, yy, zz, xy, xz, yz), rows 6..11 are W_B.
     """
-    w = words(seed, box, np.arange(ncells), step, PURPOSE_STRESS, 6)
+    return stress_normals_at(seed, box, step, np.arange(ncells))
+
+
+def stress_normals_at(seed, box, step, cells):
+    """The same 12 normals for the given linear cell indices only: (12, len(cells))."""
+    w = words(seed, box, cells, step, PURPOSE_STRESS, 6)
     u = uniform52(w[:, 0:12].T, w[:, 12:24].T)
     return box_muller(u)
 
