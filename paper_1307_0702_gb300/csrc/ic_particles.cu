@@ -1,6 +1,7 @@
 // Particle kernels of libic: the particle substeps of App. A.2 coupled to the
-// grid through the 3-point kernel (App. A.1).  One warp per particle; lanes
-// 0..26 own the 27 points of a location set.
+// grid through the 3-point kernel (App. A.1).  One group of 16 lanes per
+// particle (two per warp); each lane holds two of the 27 points of a location
+// set.
 //
 // Per step (the fluid stages run in ic_fluid.cu between these launches):
 //   kHalfStep   substeps 1-2: J^n v^n at q^n -> q^{n+1/2}; F^{n+1/2};
@@ -35,7 +36,6 @@
 namespace ic {
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
 constexpr int kFixBits = 40;
 
 template <typename real>
@@ -155,32 +155,75 @@ struct Grid4 {
   real *f[4];   // delta rho, g_x, g_y, g_z
 };
 
+// Lanes of the group that serves one particle: kGroup consecutive lanes of a
+// warp (two particles per warp), each lane holding up to kPointsPerLane of the
+// 27 points of a location set.  With 1e4 particles a group of 16 keeps every
+// particle of a launch resident at once on 152 SMs (a warp per particle would
+// need more warps than the SMs hold and run the latency-bound work in waves).
+constexpr int kGroup = 16;
+constexpr int kPointsPerLane = (27 + kGroup - 1) / kGroup;
+constexpr int kBlockThreads = 128;
+constexpr int kGroupsPerBlock = kBlockThreads / kGroup;
+// resident blocks per SM the register budget is sized for: in FP32 9 x 8 = 72
+// particles per SM, 10944 on 152 SMs; FP64 keeps more registers per lane
+template <typename real>
+constexpr int min_blocks() { return sizeof(real) == 4 ? 9 : 5; }
+
+struct Lanes {
+  int sub;         // lane within the group
+  unsigned mask;   // the group's lanes in the warp
+};
+
+__device__ __forceinline__ Lanes group_lanes() {
+  const int lane = threadIdx.x & 31;
+  return {lane & (kGroup - 1), kGroup == 32 ? 0xffffffffu : (((1u << kGroup) - 1u) << (lane & ~(kGroup - 1)))};
+}
+
+__device__ __forceinline__ int group_particle() { return int((blockIdx.x * kBlockThreads + threadIdx.x) / kGroup); }
+
+template <typename T>
+__device__ __forceinline__ T gshfl(const Lanes &L, T v, int src) { return __shfl_sync(L.mask, v, src, kGroup); }
+
+template <typename real>
+__device__ __forceinline__ real group_sum(const Lanes &L, real v) {
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(L.mask, v, o, kGroup);
+  return v;
+}
+
+// ballot of the group's lanes, bit s = lane s of the group
+__device__ __forceinline__ unsigned group_ballot(const Lanes &L, bool pred) {
+  const int shift = int(threadIdx.x & 31) & ~(kGroup - 1);
+  return (__ballot_sync(L.mask, pred) & L.mask) >> shift;
+}
+
 template <typename real>
 __device__ __forceinline__ int n_of(const PConsts<real> &pc, int a) {
   return a == 0 ? pc.n[0] : (a == 1 ? pc.n[1] : pc.n[2]);
 }
 
-// Stencil of a particle (lane a < 3 holds the position component q_a): centre
-// base and weights, own-axis face base and weights, broadcast to the warp.
+// Stencil of a particle (lane a < 3 of the group holds the position component
+// q_a): centre base and weights, own-axis face base and weights, broadcast to
+// the group.
 template <typename real>
-__device__ void stencil_warp(typename Pos<real>::T qa, int lane, const PConsts<real> &pc, int base[6],
-                             real w[18]) {
+__device__ void stencil_group(typename Pos<real>::T qa, const Lanes &L, const PConsts<real> &pc, int base[6],
+                              real w[18]) {
   int bc = 0, bf = 0;
   real wc[3] = {real(0), real(0), real(0)}, wf[3] = {real(0), real(0), real(0)};
-  if (lane < 3) {
+  if (L.sub < 3) {
     real rc, rf;
-    Pos<real>::axis(qa, pc, lane, bc, rc, bf, rf);
+    Pos<real>::axis(qa, pc, L.sub, bc, rc, bf, rf);
     peskin3(rc, wc);
     peskin3(rf, wf);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    base[a] = __shfl_sync(0xffffffffu, bc, a);
-    base[3 + a] = __shfl_sync(0xffffffffu, bf, a);
+    base[a] = gshfl(L, bc, a);
+    base[3 + a] = gshfl(L, bf, a);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      w[3 * a + j] = __shfl_sync(0xffffffffu, wc[j], a);
-      w[9 + 3 * a + j] = __shfl_sync(0xffffffffu, wf[j], a);
+      w[3 * a + j] = gshfl(L, wc[j], a);
+      w[9 + 3 * a + j] = gshfl(L, wf[j], a);
     }
   }
 }
@@ -202,42 +245,46 @@ __device__ __forceinline__ real sel3(const real *w3, int d) {   // w3[d + 1], d 
   return d < 0 ? w3[0] : (d == 0 ? w3[1] : w3[2]);
 }
 
-// Warp gather at one stencil: J delta rho (out[0]) and J v^a (out[1+a]).
-// Lane l < 27 owns the point (l % 3, (l / 3) % 3, l / 9) - 1 of each location set.
+// Group gather at one stencil: J delta rho (out[0]) and J v^a (out[1+a]).
+// Point t (0..26) is (t % 3, (t / 3) % 3, t / 9) - 1 of each location set;
+// lane s of the group takes the points s, s + kGroup, ...
 template <typename real>
 __device__ void gather(const Grid4<real> &G, const int base[6], const real w[18], const PConsts<real> &pc,
-                       int lane, bool want_rho, bool want_v, real out[4]) {
+                       const Lanes &L, bool want_rho, bool want_v, real out[4]) {
   real acc[4] = {real(0), real(0), real(0), real(0)};
-  if (lane < 27) {
-    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+#pragma unroll
+  for (int k = 0; k < kPointsPerLane; ++k) {
+    const int t = L.sub + kGroup * k;
+    if (t >= 27) break;
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
     const int cx = step_coord(base[0], dx, pc.n[0]), cy = step_coord(base[1], dy, pc.n[1]),
               cz = step_coord(base[2], dz, pc.n[2]);
     const real wcx = sel3(w + 0, dx), wcy = sel3(w + 3, dy), wcz = sel3(w + 6, dz);
-    if (want_rho) acc[0] = wcx * wcy * wcz * G.f[0][cell_index(cx, cy, cz, pc)];
+    if (want_rho) acc[0] += wcx * wcy * wcz * G.f[0][cell_index(cx, cy, cz, pc)];
     if (want_v) {
       const real rho0 = pc.rho0, half = real(0.5);
       {  // x faces
         const int fx = step_coord(base[3], dx, pc.n[0]);
         const int fxp = (fx + 1 == pc.n[0]) ? 0 : fx + 1;
         const size_t i = cell_index(fx, cy, cz, pc), iu = cell_index(fxp, cy, cz, pc);
-        acc[1] = sel3(w + 9, dx) * wcy * wcz * fdiv(G.f[1][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
+        acc[1] += sel3(w + 9, dx) * wcy * wcz * fdiv(G.f[1][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
       }
       {  // y faces
         const int fy = step_coord(base[4], dy, pc.n[1]);
         const int fyp = (fy + 1 == pc.n[1]) ? 0 : fy + 1;
         const size_t i = cell_index(cx, fy, cz, pc), iu = cell_index(cx, fyp, cz, pc);
-        acc[2] = wcx * sel3(w + 12, dy) * wcz * fdiv(G.f[2][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
+        acc[2] += wcx * sel3(w + 12, dy) * wcz * fdiv(G.f[2][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
       }
       {  // z faces
         const int fz = step_coord(base[5], dz, pc.n[2]);
         const int fzp = (fz + 1 == pc.n[2]) ? 0 : fz + 1;
         const size_t i = cell_index(cx, cy, fz, pc), iu = cell_index(cx, cy, fzp, pc);
-        acc[3] = wcx * wcy * sel3(w + 15, dz) * fdiv(G.f[3][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
+        acc[3] += wcx * wcy * sel3(w + 15, dz) * fdiv(G.f[3][i], rho0 + half * (G.f[0][i] + G.f[0][iu]));
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) out[j] = warp_sum(acc[j]);
+  for (int j = 0; j < 4; ++j) out[j] = group_sum(L, acc[j]);
 }
 
 template <typename real>
@@ -256,6 +303,44 @@ __device__ __forceinline__ int ring_d(int b, int a, int n) {
   return d;
 }
 
+// Visits p and the neighbours of p whose centre bases lie within `reach`
+// cells of p's on every axis, in ascending particle index.  The neighbour
+// list is screened a group-width at a time (one parallel load of indices and
+// bases) so that far neighbours cost no dependent round trip.
+template <typename real, typename Visit>
+__device__ __forceinline__ void for_near_members(const PV<real> &P, int p, const int pb[3], int reach,
+                                                 const PConsts<real> &pc, const Lanes &L, Visit visit) {
+  const int nn = P.nnbr[p];
+  const int *nb = P.nbr + size_t(p) * kMaxNeighbours;
+  bool self_done = false;
+  for (int j0 = 0; j0 < nn; j0 += kGroup) {
+    const int j = j0 + L.sub;
+    int m_l = 0;
+    bool near = false;
+    if (j < nn) {
+      m_l = nb[j];
+      near = true;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int d = ring_d(P.base[6 * m_l + b], pb[b], pc.n[b]);
+        near = near && d <= reach && d >= -reach;
+      }
+    }
+    unsigned bits = group_ballot(L, near);
+    while (bits) {
+      const int k = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int m = gshfl(L, m_l, k);
+      if (!self_done && m > p) {
+        visit(p);
+        self_done = true;
+      }
+      visit(m);
+    }
+  }
+  if (!self_done) visit(p);
+}
+
 template <typename real>
 __device__ __forceinline__ real w1(const real *w3, int d) {
   return (unsigned(d + 1) < 3u) ? w3[d + 1] : real(0);
@@ -266,7 +351,7 @@ __device__ __forceinline__ real pick3(const real v[4], int a) {
   return a == 0 ? v[1] : (a == 1 ? v[2] : v[3]);
 }
 
-// Per-warp staging of one member particle for the face updates.
+// Per-group staging of one member particle for the face updates.
 template <typename real>
 struct Member {
   int base[6];
@@ -280,146 +365,131 @@ struct Member {
 // hold it, which adds  scale * sum_m W_a(m, f) vec_m[a] / h^3  over the
 // particles m whose stencils reach the face, in ascending particle index.
 // vec is the tether force (stage source S F) or the impulse (-S dg).
+constexpr int kFacesPerLane = (81 + kGroup - 1) / kGroup;
+
 template <typename real>
-__device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int p, int lane, const real *vec,
-                                   real scale, const PConsts<real> &pc, Member<real> *sm) {
-  const int nn = P.nnbr[p];
-  const int *nb = P.nbr + size_t(p) * kMaxNeighbours;
+__device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int p, const Lanes &L,
+                                   const real *vec, real scale, const PConsts<real> &pc, Member<real> *sm) {
   int pb[6];
 #pragma unroll
   for (int b = 0; b < 6; ++b) pb[b] = P.base[6 * p + b];
 
-  // this lane's faces: t = lane + 32 j < 81; axis a = t / 27, point (t % 27)
-  int fa[3], fA[3], fB1[3], fB2[3];
-  bool owner[3];
-  real total[3];
+  // this lane's faces: t = sub + kGroup j < 81; axis a = t / 27, point (t % 27)
+  auto axis_of = [&](int j) { const int t = L.sub + kGroup * j; return t < 81 ? t / 27 : 0; };
+  int fA[kFacesPerLane], fB1[kFacesPerLane], fB2[kFacesPerLane];
+  unsigned owner = 0;   // bit j: this lane still owns face j
+  real total[kFacesPerLane];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int t = lane + 32 * j;
-    const int a = (t < 81) ? t / 27 : 0, r = t % 27;
+  for (int j = 0; j < kFacesPerLane; ++j) {
+    const int t = L.sub + kGroup * j;
+    const int a = axis_of(j), r = t % 27;
     const int b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
     const int pa = a == 0 ? pb[3] : (a == 1 ? pb[4] : pb[5]);     // face base along a
     const int p1 = b1 == 0 ? pb[0] : (b1 == 1 ? pb[1] : pb[2]);
     const int p2 = b2 == 0 ? pb[0] : (b2 == 1 ? pb[1] : pb[2]);
-    fa[j] = a;
     fA[j] = step_coord(pa, r % 3 - 1, n_of(pc, a));
     fB1[j] = step_coord(p1, (r / 3) % 3 - 1, n_of(pc, b1));
     fB2[j] = step_coord(p2, r / 9 - 1, n_of(pc, b2));
-    owner[j] = t < 81;
+    if (t < 81) owner |= 1u << j;
     total[j] = real(0);
   }
 
-  int j_nb = 0;
-  bool self_done = false;
-  while (true) {
-    int m;
-    if (!self_done && (j_nb >= nn || nb[j_nb] > p)) {
-      m = p;
-      self_done = true;
-    } else if (j_nb < nn) {
-      m = nb[j_nb++];
-    } else {
-      break;
-    }
-    // face stencils of two particles can share a face only if their centre
-    // bases are within 3 cells on every axis
-    bool far = false;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int d = ring_d(P.base[6 * m + b], pb[b], pc.n[b]);
-      far = far || d > 3 || d < -3;
-    }
-    if (far) continue;
-    __syncwarp();
-    if (lane < 6) sm->base[lane] = P.base[6 * m + lane];
-    if (lane < 18) sm->w[lane] = P.w[18 * m + lane];
-    if (lane < 3) sm->vec[lane] = vec[3 * m + lane];
-    __syncwarp();
+  // face stencils of two particles can share a face only if their centre
+  // bases are within 3 cells on every axis
+  for_near_members(P, p, pb, 3, pc, L, [&](int m) {
+    __syncwarp(L.mask);
+    if (L.sub < 6) sm->base[L.sub] = P.base[6 * m + L.sub];
+    for (int i = L.sub; i < 18; i += kGroup) sm->w[i] = P.w[18 * m + i];
+    if (L.sub < 3) sm->vec[L.sub] = vec[3 * m + L.sub];
+    __syncwarp(L.mask);
     const bool lower = m < p;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int a = fa[j], b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
+    for (int j = 0; j < kFacesPerLane; ++j) {
+      const int a = axis_of(j), b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
       const int df = ring_d(fA[j], sm->base[3 + a], n_of(pc, a));
       const int d1 = ring_d(fB1[j], sm->base[b1], n_of(pc, b1));
       const int d2 = ring_d(fB2[j], sm->base[b2], n_of(pc, b2));
       const bool inside = df >= -1 && df <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1;
-      if (lower && inside) owner[j] = false;
+      if (lower && inside) owner &= ~(1u << j);
       const real wt = w1(sm->w + 9 + 3 * a, df) * w1(sm->w + 3 * b1, d1) * w1(sm->w + 3 * b2, d2);
       total[j] += wt * sm->vec[a] * pc.inv_h3;
     }
-  }
+  });
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    if (owner[j]) {
-      const int a = fa[j];
+  for (int j = 0; j < kFacesPerLane; ++j) {
+    if (owner & (1u << j)) {
+      const int a = axis_of(j);
       const int x = a == 0 ? fA[j] : (a == 1 ? fB2[j] : fB1[j]);
       const int y = a == 1 ? fA[j] : (a == 2 ? fB2[j] : fB1[j]);
       const int z = a == 2 ? fA[j] : (a == 0 ? fB2[j] : fB1[j]);
-      G.f[1 + a][cell_index(x, y, z, pc)] += scale * total[j];
+      real *ga = a == 0 ? G.f[1] : (a == 1 ? G.f[2] : G.f[3]);
+      ga[cell_index(x, y, z, pc)] += scale * total[j];
     }
   }
 }
 
 // ------------------------------------------------------------------ kernels
 template <typename real>
-__global__ void k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc, int *rebuild, int *status) {
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc,
+                                                             int *rebuild, int *status) {
   using PosT = Pos<real>;
   using T = typename PosT::T;
-  const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+  const int p = group_particle();
+  const Lanes L = group_lanes();
   if (p >= P.n) return;
 
   if (*rebuild) {
     // neighbour list from q^n, in ascending index order
     const T q0 = P.q[3 * p], q1 = P.q[3 * p + 1], q2 = P.q[3 * p + 2];
+    const int shift = (threadIdx.x & 31) & ~(kGroup - 1);
     int count = 0;
-    for (int j0 = 0; j0 < P.n; j0 += 32) {
-      const int j = j0 + lane;
+    for (int j0 = 0; j0 < P.n; j0 += kGroup) {
+      const int j = j0 + L.sub;
       bool hit = false;
       if (j < P.n && j != p) {
         hit = fabs(PosT::diff(P.q[3 * j], q0, pc, 0)) < pc.cutoff &&
               fabs(PosT::diff(P.q[3 * j + 1], q1, pc, 1)) < pc.cutoff &&
               fabs(PosT::diff(P.q[3 * j + 2], q2, pc, 2)) < pc.cutoff;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      const unsigned m = (__ballot_sync(L.mask, hit) & L.mask) >> shift;
       if (hit) {
-        const int slot = count + __popc(m & ((1u << lane) - 1u));
+        const int slot = count + __popc(m & ((1u << L.sub) - 1u));
         if (slot < kMaxNeighbours) P.nbr[size_t(p) * kMaxNeighbours + slot] = j;
       }
       count += __popc(m);
     }
-    if (lane == 0) {
+    if (L.sub == 0) {
       if (count > kMaxNeighbours) atomicOr(status, kStatusNbrOverflow);
       P.nnbr[p] = min(count, kMaxNeighbours);
     }
-    if (lane < 3) P.q_build[3 * p + lane] = P.q[3 * p + lane];
+    if (L.sub < 3) P.q_build[3 * p + L.sub] = P.q[3 * p + L.sub];
   }
 
   // substep 1: q^{n+1/2} = q^n + dt/2 J^n v^n (lane a < 3 owns axis a)
-  const T q_l = lane < 3 ? P.q[3 * p + lane] : T(0);
+  const T q_l = L.sub < 3 ? P.q[3 * p + L.sub] : T(0);
   int base[6];
   real w[18];
-  stencil_warp<real>(q_l, lane, pc, base, w);
+  stencil_group<real>(q_l, L, pc, base, w);
   real g4[4];
-  gather(G, base, w, pc, lane, false, true, g4);
+  gather(G, base, w, pc, L, false, true, g4);
   T qh_l = T(0);
   real F_l = real(0);
-  if (lane < 3) {
-    qh_l = PosT::advance(q_l, real(0.5) * pc.dt * pick3(g4, lane), pc, lane);
+  if (L.sub < 3) {
+    qh_l = PosT::advance(q_l, real(0.5) * pc.dt * pick3(g4, L.sub), pc, L.sub);
     // substep 2: tether force at q^{n+1/2}
-    F_l = -P.k_s[p] * real(PosT::diff(qh_l, P.q_eq[3 * p + lane], pc, lane));
+    F_l = -P.k_s[p] * real(PosT::diff(qh_l, P.q_eq[3 * p + L.sub], pc, L.sub));
   }
 
   // stencil at q^{n+1/2}; J^{n+1/2} v^n
-  stencil_warp<real>(qh_l, lane, pc, base, w);
-  gather(G, base, w, pc, lane, false, true, g4);
-  if (lane < 3) {
-    P.q_half[3 * p + lane] = qh_l;
-    P.force[3 * p + lane] = F_l;
-    P.jv_n[3 * p + lane] = pick3(g4, lane);
-    if (fabs(PosT::diff(qh_l, P.q_build[3 * p + lane], pc, lane)) > pc.skin_limit) atomicOr(status, kStatusSkin);
+  stencil_group<real>(qh_l, L, pc, base, w);
+  gather(G, base, w, pc, L, false, true, g4);
+  if (L.sub < 3) {
+    P.q_half[3 * p + L.sub] = qh_l;
+    P.force[3 * p + L.sub] = F_l;
+    P.jv_n[3 * p + L.sub] = pick3(g4, L.sub);
+    if (fabs(PosT::diff(qh_l, P.q_build[3 * p + L.sub], pc, L.sub)) > pc.skin_limit) atomicOr(status, kStatusSkin);
   }
-  if (lane == 0) {
+  if (L.sub == 0) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) P.base[6 * p + j] = base[j];
 #pragma unroll
@@ -433,138 +503,137 @@ __global__ void k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc, int *re
 // particle's centre stencil holds them).  The Omega of the particles whose
 // stencils reach p's cells are regathered here, so one launch suffices.
 template <typename real>
-__global__ void k_pressure(PV<real> P, Grid4<real> G, PConsts<real> pc, real *pp, int *rebuild) {
-  const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_pressure(PV<real> P, Grid4<real> G, PConsts<real> pc, real *pp,
+                                                            int *rebuild) {
+  const int p = group_particle();
+  const Lanes L = group_lanes();
   // the neighbour lists were rebuilt (if flagged) by the half step: clear the flag
   if (rebuild && blockIdx.x == 0 && threadIdx.x == 0) *rebuild = 0;
   if (p >= P.n) return;
-  const int nn = P.nnbr[p];
-  const int *nb = P.nbr + size_t(p) * kMaxNeighbours;
   int pb[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) pb[b] = P.base[6 * p + b];
-  // this lane's cell of p's centre stencil
-  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-  const int cx = step_coord(pb[0], dx, pc.n[0]), cy = step_coord(pb[1], dy, pc.n[1]),
-            cz = step_coord(pb[2], dz, pc.n[2]);
-  bool owner = lane < 27;
-  real total = real(0);
-  int j_nb = 0;
-  bool self_done = false;
-  while (true) {
-    int m;
-    if (!self_done && (j_nb >= nn || nb[j_nb] > p)) {
-      m = p;
-      self_done = true;
-    } else if (j_nb < nn) {
-      m = nb[j_nb++];
-    } else {
-      break;
-    }
+  // this lane's cells of p's centre stencil: t = sub + kGroup k < 27
+  int cx[kPointsPerLane], cy[kPointsPerLane], cz[kPointsPerLane];
+  bool owner[kPointsPerLane];
+  real total[kPointsPerLane];
+#pragma unroll
+  for (int k = 0; k < kPointsPerLane; ++k) {
+    const int t = L.sub + kGroup * k;
+    cx[k] = step_coord(pb[0], t % 3 - 1, pc.n[0]);
+    cy[k] = step_coord(pb[1], (t / 3) % 3 - 1, pc.n[1]);
+    cz[k] = step_coord(pb[2], (t / 9) % 3 - 1, pc.n[2]);
+    owner[k] = t < 27;
+    total[k] = real(0);
+  }
+  // centre stencils of two particles share a cell only within 2 cells on every axis
+  for_near_members(P, p, pb, 2, pc, L, [&](int m) {
     int mb[6];
     real mw[18];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) mb[b] = P.base[6 * m + b];
-    bool far = false;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int d = ring_d(mb[b], pb[b], pc.n[b]);
-      far = far || d > 2 || d < -2;
-    }
-    if (far) continue;
     load_stencil(P, m, mb, mw);
     real g4[4];
-    gather(G, mb, mw, pc, lane, true, false, g4);
+    gather(G, mb, mw, pc, L, true, false, g4);
     const real omega = P.eps[m] * pc.vol * g4[0];
-    const int ex = ring_d(cx, mb[0], pc.n[0]), ey = ring_d(cy, mb[1], pc.n[1]), ez = ring_d(cz, mb[2], pc.n[2]);
-    const bool inside = ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1;
-    if (m < p && inside) owner = false;
-    if (inside) total += sel3(mw + 0, ex) * sel3(mw + 3, ey) * sel3(mw + 6, ez) * omega;
-  }
-  if (owner) pp[cell_index(cx, cy, cz, pc)] = total * pc.inv_h3;
+#pragma unroll
+    for (int k = 0; k < kPointsPerLane; ++k) {
+      const int ex = ring_d(cx[k], mb[0], pc.n[0]), ey = ring_d(cy[k], mb[1], pc.n[1]),
+                ez = ring_d(cz[k], mb[2], pc.n[2]);
+      const bool inside = ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1;
+      if (m < p && inside) owner[k] = false;
+      if (inside) total[k] += sel3(mw + 0, ex) * sel3(mw + 3, ey) * sel3(mw + 6, ez) * omega;
+    }
+  });
+#pragma unroll
+  for (int k = 0; k < kPointsPerLane; ++k)
+    if (owner[k]) pp[cell_index(cx[k], cy[k], cz[k], pc)] = total[k] * pc.inv_h3;
 }
 
 // Spring-force source of RK stage s (b_s dt S F) or the impulse (-S dg).
 template <typename real, int KIND>
-__global__ void k_face_update(PV<real> P, Grid4<real> G, PConsts<real> pc, real scale) {
-  __shared__ Member<real> sm[kWarpsPerBlock];
-  const int warp = threadIdx.x / 32;
-  const int p = blockIdx.x * kWarpsPerBlock + warp;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_face_update(PV<real> P, Grid4<real> G, PConsts<real> pc,
+                                                               real scale) {
+  __shared__ Member<real> sm[kGroupsPerBlock];
+  const int p = group_particle();
+  const Lanes L = group_lanes();
   if (p >= P.n) return;
-  update_owned_faces<real>(P, G, p, lane, KIND == 0 ? P.force : P.dg, scale, pc, &sm[warp]);
+  update_owned_faces<real>(P, G, p, L, KIND == 0 ? P.force : P.dg, scale, pc, &sm[threadIdx.x / kGroup]);
 }
 
 template <typename real>
-__global__ void k_impulse(PV<real> P, Grid4<real> G, PConsts<real> pc) {
-  const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_impulse(PV<real> P, Grid4<real> G, PConsts<real> pc) {
+  const int p = group_particle();
+  const Lanes L = group_lanes();
   if (p >= P.n) return;
   int base[6];
   real w[18];
   load_stencil(P, p, base, w);
   real g4[4];
-  gather(G, base, w, pc, lane, true, true, g4);
-  if (lane < 3) {
+  gather(G, base, w, pc, L, true, true, g4);
+  if (L.sub < 3) {
     const real mf = pc.vol * (pc.rho0 + g4[0]);   // m_f = V J rho^{n+1}
     const real me = P.m_e[p];
-    const real u = P.u[3 * p + lane];
-    const real rel = pick3(g4, lane) - u;
+    const real u = P.u[3 * p + L.sub];
+    const real rel = pick3(g4, L.sub) - u;
     const real dg = me * mf / (me + mf) * rel;
-    P.dg[3 * p + lane] = dg;
-    P.u[3 * p + lane] = u + mf / (me + mf) * rel;
-    P.lam[3 * p + lane] = dg / pc.dt - P.force[3 * p + lane];
-    if (lane == 0) P.jrho[p] = pc.rho0 + g4[0];
+    P.dg[3 * p + L.sub] = dg;
+    P.u[3 * p + L.sub] = u + mf / (me + mf) * rel;
+    P.lam[3 * p + L.sub] = dg / pc.dt - P.force[3 * p + L.sub];
+    if (L.sub == 0) P.jrho[p] = pc.rho0 + g4[0];
   }
 }
 
 template <typename real>
-__global__ void k_final(PV<real> P, Grid4<real> G, PConsts<real> pc, const int64_t *step, const double *weights,
-                        int *rebuild, real *pp) {
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<real> P, Grid4<real> G, PConsts<real> pc,
+                                                         const int64_t *step, const double *weights, int *rebuild,
+                                                         real *pp) {
   using PosT = Pos<real>;
-  const int p = blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+  const int p = group_particle();
+  const Lanes L = group_lanes();
   if (p >= P.n) return;
   int base[6];
   real w[18];
   load_stencil(P, p, base, w);
   real g4[4];
-  gather(G, base, w, pc, lane, false, true, g4);
+  gather(G, base, w, pc, L, false, true, g4);
   // the particle pressure of this step is consumed: clear p's 27 cells
-  if (lane < 27)
-    pp[cell_index(step_coord(base[0], lane % 3 - 1, pc.n[0]), step_coord(base[1], (lane / 3) % 3 - 1, pc.n[1]),
-                  step_coord(base[2], lane / 9 - 1, pc.n[2]), pc)] = real(0);
-  bool move = false;
-  if (lane < 3) {
-    const typename PosT::T qn = PosT::advance(
-        P.q[3 * p + lane], real(0.5) * pc.dt * (pick3(g4, lane) + P.jv_n[3 * p + lane]), pc, lane);
-    P.q[3 * p + lane] = qn;
-    move = fabs(PosT::diff(qn, P.q_build[3 * p + lane], pc, lane)) > pc.rebuild_at;
+#pragma unroll
+  for (int k = 0; k < kPointsPerLane; ++k) {
+    const int t = L.sub + kGroup * k;
+    if (t < 27)
+      pp[cell_index(step_coord(base[0], t % 3 - 1, pc.n[0]), step_coord(base[1], (t / 3) % 3 - 1, pc.n[1]),
+                    step_coord(base[2], t / 9 - 1, pc.n[2]), pc)] = real(0);
   }
-  if (__any_sync(0xffffffffu, move) && lane == 0) *rebuild = 1;
+  bool move = false;
+  if (L.sub < 3) {
+    const typename PosT::T qn = PosT::advance(
+        P.q[3 * p + L.sub], real(0.5) * pc.dt * (pick3(g4, L.sub) + P.jv_n[3 * p + L.sub]), pc, L.sub);
+    P.q[3 * p + L.sub] = qn;
+    move = fabs(PosT::diff(qn, P.q_build[3 * p + L.sub], pc, L.sub)) > pc.rebuild_at;
+  }
+  if (__any_sync(L.mask, move) && L.sub == 0) *rebuild = 1;
   // weighted sums in FP64, one value per lane: lanes 0-2 the tether force, 3-5 lambda
-  if (lane < 6) {
+  if (L.sub < 6) {
     const int64_t jw = step[0] - step[1];
     const double wt = (jw >= 0 && jw < step[2]) ? weights[jw] : 0.0;
-    const real v = lane < 3 ? P.force[3 * p + lane] : P.lam[3 * p + lane - 3];
-    P.acc[6 * p + lane] += wt * double(v);
+    const real v = L.sub < 3 ? P.force[3 * p + L.sub] : P.lam[3 * p + L.sub - 3];
+    P.acc[6 * p + L.sub] += wt * double(v);
   }
 }
 
 template <typename real>
-__global__ void k_init_velocity(PV<real> P, Grid4<real> G, PConsts<real> pc, int first, int n) {
+__global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_init_velocity(PV<real> P, Grid4<real> G, PConsts<real> pc,
+                                                                 int first, int n) {
   using T = typename Pos<real>::T;
-  const int p = first + blockIdx.x * kWarpsPerBlock + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+  const int p = first + group_particle();
+  const Lanes L = group_lanes();
   if (p >= first + n) return;
-  const T q_l = lane < 3 ? P.q[3 * p + lane] : T(0);
+  const T q_l = L.sub < 3 ? P.q[3 * p + L.sub] : T(0);
   int base[6];
   real w[18];
-  stencil_warp<real>(q_l, lane, pc, base, w);
+  stencil_group<real>(q_l, L, pc, base, w);
   real g4[4];
-  gather(G, base, w, pc, lane, false, true, g4);
-  if (lane < 3) P.u[3 * p + lane] = pick3(g4, lane);
+  gather(G, base, w, pc, L, false, true, g4);
+  if (L.sub < 3) P.u[3 * p + L.sub] = pick3(g4, L.sub);
 }
 
 template <typename real>
@@ -619,7 +688,7 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
   const PV<real> P = view<real>(ctx->ps);
   if (P.n == 0) return cudaSuccess;
   const PConsts<real> pc = particle_consts<real>(ctx);
-  const dim3 grid((P.n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
+  const dim3 grid((P.n + kGroupsPerBlock - 1) / kGroupsPerBlock), block(kBlockThreads);
   static const double kCoef[3] = {1.0, 0.25, 2.0 / 3.0};
   real *pp = static_cast<real *>(ctx->pp);
   switch (phase) {
@@ -657,7 +726,7 @@ cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *
 }
 
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]) {
-  const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
+  const dim3 grid((n + kGroupsPerBlock - 1) / kGroupsPerBlock), block(kBlockThreads);
   if (ctx->p.precision == IC_FP32)
     k_init_velocity<float><<<grid, block, 0, ctx->stream>>>(view<float>(ctx->ps), grid4<float>(state),
                                                             particle_consts<float>(ctx), first, n);
