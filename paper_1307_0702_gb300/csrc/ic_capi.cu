@@ -305,6 +305,13 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   ic_ctx *ctx = new ic_ctx();
   ctx->p = p;
   ctx->cells = int64_t(p.nx) * p.ny * p.nz;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        ctx->sm_count <= 0)
+      ctx->sm_count = 1;
+  }
   ctx->real_size = p.precision == IC_FP32 ? 4 : 8;
   auto bail = [&](ic_status st) {
     ic_destroy(ctx);

@@ -17,13 +17,19 @@
 //   Stage s: U_{s+1} = a_s U^n + b_s (U_s + dt dU/dt(U_s, t_s)), (a, b) =
 //   (0, 1), (3/4, 1/4), (1/3, 2/3); t_s = t^n, t^{n+1}, t^{n+1/2}.
 //
-// Kernel layout.  A CTA owns a TX x TY column of cells and marches up a chunk
-// of z planes ("2.5D" blocking).  Its (TX+2) x (TY+2) threads also cover a
-// one-cell ring so that each thread computes the fluxes of one cell; the
-// in-plane neighbours come from shared memory and the z neighbours from
-// registers carried between planes.  Per plane: one load of the next plane,
-// one flux evaluation with the Philox noise regenerated in registers, and one
-// fused combination with U^n.  State stores delta rho = rho - rho0.
+// Kernel layout.  The grid is cut into TX x TY columns of cells; a CTA marches
+// up runs of z planes of a column ("2.5D" blocking).  Its (TX+2) x (TY+2)
+// threads also cover a one-cell ring so that each thread computes the fluxes
+// of one cell; the in-plane neighbours come from shared memory and the z
+// neighbours from registers carried between planes.  Per plane: one load of
+// the next plane, one flux evaluation, and one fused combination with U^n.
+// State stores delta rho = rho - rho0.
+//
+// Schedule.  The (column, plane) pairs are numbered column by column and split
+// into gridDim.x equal contiguous ranges, one per CTA; a range that crosses a
+// column boundary is marched as two runs.  With the grid sized to the CTAs the
+// SMs hold at once, every CTA gets the same number of planes, so no partial
+// last wave is left (a grid of fixed z chunks leaves one at most sizes).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,7 +52,7 @@ struct StageArgs {
   FluidConsts<real> c;
   const int64_t *step;
   double *partials;                // stage 3: per-CTA sum of delta rho cos(k x)
-  int zchunk;
+  int ncols_x, ncols_y;            // tile columns along x and y
 };
 
 template <typename real>
@@ -93,16 +99,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   const int NX = c.nx, NY = c.ny, NZ = c.nz;
   const int t = threadIdx.x;
   const int ex = t % EX, ey = t / EX;
-  const int gx_raw = int(blockIdx.x) * TX + ex - 1;
-  const int gy_raw = int(blockIdx.y) * TY + ey - 1;
-  const int x = wrap(gx_raw, NX), y = wrap(gy_raw, NY);
-  const int xp = (x + 1 == NX) ? 0 : x + 1;
-  const int yp = (y + 1 == NY) ? 0 : y + 1;
-  const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx_raw < NX && gy_raw < NY;
   const int eXm = ey * EX + max(ex - 1, 0), eXp = ey * EX + min(ex + 1, EX - 1);
   const int eYm = max(ey - 1, 0) * EX + ex, eYp = min(ey + 1, EY - 1) * EX + ex;
-  const int z0 = int(blockIdx.z) * a.zchunk;
-  const int z1 = min(z0 + a.zchunk, NZ);
   const auto zwrap = [NZ](int kk) { return kk < 0 ? kk + NZ : (kk >= NZ ? kk - NZ : kk); };
 
   const int64_t step = *a.step;
@@ -114,7 +112,26 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   const real beta = STAGE == 0 ? real(-1.7320508075688772) : (STAGE == 1 ? real(1.7320508075688772) : real(0));
   const RngKey key{c.k0, c.k1, c.box};
   const uint32_t ustep = uint32_t(step);
-  const size_t plane = size_t(NX) * NY;
+  const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
+  const real dt = c.dt;
+  const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
+  real mode_acc = real(0);
+
+  // this CTA's share of the (column, plane) pairs
+  const int units = a.ncols_x * a.ncols_y * NZ;
+  const int u_end = int((long long)units * (blockIdx.x + 1) / gridDim.x);
+  for (int u = int((long long)units * blockIdx.x / gridDim.x); u < u_end;) {
+  const int col = u / NZ;
+  const int z0 = u - col * NZ;
+  const int z1 = min(NZ, z0 + (u_end - u));
+  u += z1 - z0;
+  const int gx_raw = (col % a.ncols_x) * TX + ex - 1;
+  const int gy_raw = (col / a.ncols_x) * TY + ey - 1;
+  const int x = wrap(gx_raw, NX), y = wrap(gy_raw, NY);
+  const int xp = (x + 1 == NX) ? 0 : x + 1;
+  const int yp = (y + 1 == NY) ? 0 : y + 1;
+  const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx_raw < NX && gy_raw < NY;
+  __syncthreads();   // the previous run's last reads of shared memory are done
 
   // cos(k x) along the wave axis (mode amplitude and MODE drive), and the
   // drive profile: cos(k x) (MODE) or the indicator of the driven plane (PLANE)
@@ -130,7 +147,6 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   };
 
   // 32-bit cell offsets: in-plane offsets fixed per thread, plus k * plane
-  const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
   const uint32_t o_c = uint32_t(x) + uint32_t(NX) * uint32_t(y);
   const uint32_t o_xp = uint32_t(xp) + uint32_t(NX) * uint32_t(y);
   const uint32_t o_yp = uint32_t(x) + uint32_t(NX) * uint32_t(yp);
@@ -199,9 +215,6 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   store_plane((z0 - 1) & 1, P);
   PlaneRaw<real> R = fetch(z0);
   real vz_m = real(0), gz_m = real(0), txz_m = real(0), tyz_m = real(0), tzz_k = real(0);
-  real mode_acc = real(0);
-  const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
-  const real dt = c.dt;
 
   for (int k = z0 - 1; k < z1; ++k) {
     // prefetch plane k + 2 (the last plane any flux of this chunk needs is z1)
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     P = Q;
     R = Rn;
   }
-  (void)plane;
+  }   // runs
 
   if (STAGE == 2) {
     // per-CTA partial of sum (rho - rho0) cos(k x), fixed reduction order
@@ -305,8 +318,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
       double s = 0.0;
       const int nw = (EXY + 31) / 32;
       for (int j = 0; j < nw; ++j) s += double(s_red[j]);
-      const size_t b = blockIdx.x + size_t(gridDim.x) * (blockIdx.y + size_t(gridDim.y) * blockIdx.z);
-      a.partials[b] = s;
+      a.partials[blockIdx.x] = s;
     }
   }
 }
@@ -369,18 +381,36 @@ struct TileShape<double, 1> {
   static constexpr int TX = 16, TY = 4;
 };
 
-// planes per CTA along z (32 balances the 2.5D prologue against the tail wave at 128^3)
+// Fewest z planes a CTA marches: the grid is the CTAs the SMs hold at once
+// (the register budget of the launch bounds) unless the box has fewer than
+// IC_ZCHUNK planes per such CTA, so that a small box does not pay the 2.5D
+// prologue (one extra plane per run) on runs of a few planes.
 #ifndef IC_ZCHUNK
 #define IC_ZCHUNK 32
 #endif
 int zchunk_for(const ic_ctx *ctx) { return std::min<int>(ctx->p.nz, ctx->zchunk > 0 ? ctx->zchunk : IC_ZCHUNK); }
 
+struct StageLayout {
+  int ncols_x, ncols_y, ctas;
+};
+
+template <typename real, int V>
+StageLayout stage_layout_v(const ic_grid_params &p, int zchunk, int sm_count) {
+  constexpr int TX = TileShape<real, V>::TX, TY = TileShape<real, V>::TY;
+  constexpr int EXY = (TX + 2) * (TY + 2);
+  StageLayout l;
+  l.ncols_x = (p.nx + TX - 1) / TX;
+  l.ncols_y = (p.ny + TY - 1) / TY;
+  const long long units = (long long)l.ncols_x * l.ncols_y * p.nz;
+  const long long resident = (long long)min_ctas<real, EXY>() * sm_count;
+  l.ctas = int(std::max<long long>(1, std::min<long long>(resident, (units + zchunk - 1) / zchunk)));
+  return l;
+}
+
 template <typename real>
-dim3 stage_grid(const ic_ctx *ctx) {
-  const int TX = ctx->tile_variant == 1 ? TileShape<real, 1>::TX : TileShape<real, 0>::TX;
-  const int TY = ctx->tile_variant == 1 ? TileShape<real, 1>::TY : TileShape<real, 0>::TY;
-  const int zc = zchunk_for(ctx);
-  return dim3((ctx->p.nx + TX - 1) / TX, (ctx->p.ny + TY - 1) / TY, (ctx->p.nz + zc - 1) / zc);
+StageLayout stage_layout(const ic_ctx *ctx) {
+  return ctx->tile_variant == 1 ? stage_layout_v<real, 1>(ctx->p, zchunk_for(ctx), ctx->sm_count)
+                                : stage_layout_v<real, 0>(ctx->p, zchunk_for(ctx), ctx->sm_count);
 }
 
 template <typename real, int V, int STAGE, bool NOISE>
@@ -401,11 +431,13 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   a.c = fluid_consts<real>(ctx);
   a.step = ctx->d.step;
   a.partials = ctx->d.partials;
-  a.zchunk = zchunk_for(ctx);
+  const StageLayout l = stage_layout_v<real, V>(ctx->p, zchunk_for(ctx), ctx->sm_count);
+  a.ncols_x = l.ncols_x;
+  a.ncols_y = l.ncols_y;
   const size_t smem = 18 * EXY * sizeof(real);
   auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  kern<<<stage_grid<real>(ctx), EXY, smem, ctx->stream>>>(a);
+  kern<<<l.ctas, EXY, smem, ctx->stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -623,8 +655,10 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
   a.c = c;
   a.step = step;
   a.partials = partials;
-  a.zchunk = std::min<int>(p.nz, IC_ZCHUNK);
-  const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + a.zchunk - 1) / a.zchunk);
+  const StageLayout l = stage_layout_v<real, 0>(p, std::min<int>(p.nz, IC_ZCHUNK), 1 << 20);
+  a.ncols_x = l.ncols_x;
+  a.ncols_y = l.ncols_y;
+  const dim3 grid(l.ctas);
   const size_t smem = 18 * EXY * sizeof(real);
   const bool noise_on = p.kT > 0.0;
   switch (stage * 2 + (noise_on ? 1 : 0)) {
@@ -647,12 +681,8 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
 
 size_t stage_ctas_raw(const ic_grid_params &p) {
   const int zc = std::min<int>(p.nz, IC_ZCHUNK);
-  if (p.precision == IC_FP32) {
-    constexpr int TX = TileShape<float, 0>::TX, TY = TileShape<float, 0>::TY;
-    return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
-  }
-  constexpr int TX = TileShape<double, 0>::TX, TY = TileShape<double, 0>::TY;
-  return size_t((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY) * ((p.nz + zc - 1) / zc);
+  return size_t(p.precision == IC_FP32 ? stage_layout_v<float, 0>(p, zc, 1 << 20).ctas
+                                       : stage_layout_v<double, 0>(p, zc, 1 << 20).ctas);
 }
 
 cudaError_t launch_stage_raw(const ic_grid_params &p, const void *consts, int stage, const void *const in_s[4],
@@ -701,8 +731,7 @@ cudaError_t launch_field_sums(ic_ctx *ctx, void *const U[4], double *dev_out4) {
 }
 
 cudaError_t launch_end_of_step(ic_ctx *ctx) {
-  const dim3 g = ctx->p.precision == IC_FP32 ? stage_grid<float>(ctx) : stage_grid<double>(ctx);
-  const int nb = int(g.x * g.y * g.z);
+  const int nb = ctx->p.precision == IC_FP32 ? stage_layout<float>(ctx).ctas : stage_layout<double>(ctx).ctas;
   const int has_mode = 1;
   const ic_grid_params &p = ctx->p;
   const double amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;

@@ -86,7 +86,8 @@ struct ic_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
   uint64_t generation = 0;                          // bumped whenever the captured step changes
   int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)
-  int zchunk = 0;          // planes per stage-kernel CTA along z (0 = default)
+  int zchunk = 0;          // fewest z planes a stage-kernel CTA marches (0 = default)
+  int sm_count = 1;        // SMs of the context's device
   std::string err;
   double omega = 0, force_amp = 0, kwave = 0;
   // kernel timing (ic_profile): event pairs per kernel class
