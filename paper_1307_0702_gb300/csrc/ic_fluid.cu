@@ -55,6 +55,16 @@ struct StageArgs {
   int ncols_x, ncols_y;            // tile columns along x and y
 };
 
+// Explicitly rounded scalar arithmetic: the flux formulas are written as the
+// same sequence of rounded operations as the FP32 pair kernel, so that a
+// plane's values do not depend on which kernel, tile or CTA computes them.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fadd_rn(a, -b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dadd_rn(a, -b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename real>
 struct PlaneVals {
   real gx, gy, gz, vx, vy, vz, dr, pp;
@@ -71,19 +81,20 @@ constexpr double kStageTime[3] = {0.0, 1.0, 0.5};
 constexpr double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
 constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
 
-// Tile shape and register budget of the FP32 stage kernel (tuned on GB300).
+// Tile height of the FP32 (pair) stage kernel and register budget of the
+// scalar one, tuned on GB300.
 #ifndef IC_FP32_TILE_Y
-#define IC_FP32_TILE_Y 8
+#define IC_FP32_TILE_Y 12
 #endif
 #ifndef IC_FP32_MIN_CTAS
 #define IC_FP32_MIN_CTAS 2
 #endif
 
-// CTAs per SM the register budget is sized for: in FP32 the budget of
-// IC_FP32_MIN_CTAS wide (34 x (TY + 2)-thread) CTAs, whatever the tile
+// CTAs per SM the register budget of the scalar kernel is sized for: in FP32
+// the budget of IC_FP32_MIN_CTAS CTAs of 340 threads, whatever the tile
 template <typename real, int EXY>
 constexpr int min_ctas() {
-  return sizeof(real) == 4 ? (IC_FP32_MIN_CTAS * 34 * (IC_FP32_TILE_Y + 2) + EXY - 1) / EXY : 1;
+  return sizeof(real) == 4 ? (IC_FP32_MIN_CTAS * 340 + EXY - 1) / EXY : 1;
 }
 
 template <typename real, int TX, int TY, int STAGE, bool NOISE>
@@ -242,33 +253,41 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     const real gz_yp = Pk[GZ * EXY + eYp], vz_yp = Pk[VZ * EXY + eYp];
     const real vx1_xm = Pq[VX * EXY + eXm], vy1_ym = Pq[VY * EXY + eYm];
 
-    const real div_k = ((P.vx - vx_xm) + (P.vy - vy_ym) + (P.vz - vz_m)) * inv_h;
-    const real div_k1 = ((Q.vx - vx1_xm) + (Q.vy - vy1_ym) + (Q.vz - P.vz)) * inv_h;
-    const real pk = c2 * P.dr + P.pp + drive * profile(k);
-    const real pk1 = c2 * Q.dr + Q.pp + drive * profile(k + 1);
+    const real div_k = mul_rn(add_rn(add_rn(sub_rn(P.vx, vx_xm), sub_rn(P.vy, vy_ym)), sub_rn(P.vz, vz_m)), inv_h);
+    const real div_k1 = mul_rn(add_rn(add_rn(sub_rn(Q.vx, vx1_xm), sub_rn(Q.vy, vy1_ym)), sub_rn(Q.vz, P.vz)), inv_h);
+    const real pk = add_rn(fma_rn(c2, P.dr, P.pp), mul_rn(drive, profile(k)));
+    const real pk1 = add_rn(fma_rn(c2, Q.dr, Q.pp), mul_rn(drive, profile(k + 1)));
 
-    const real tr_k = P.nz[0] + P.nz[1] + P.nz[2];
-    const real tr_k1 = Q.nz[0] + Q.nz[1] + Q.nz[2];
-    const real sxx = nd * P.nz[0] + nt * tr_k;
-    const real syy = nd * P.nz[1] + nt * tr_k;
-    const real szz1 = nd * Q.nz[2] + nt * tr_k1;
-    const real sxy = ne * P.nz[3], sxz = ne * P.nz[4], syz = ne * P.nz[5];
-
-    const real txx = quarter * (gx_xm + P.gx) * (vx_xm + P.vx) + pk -
-                     (two_eta * (P.vx - vx_xm) * inv_h + lam2 * div_k) - sxx;
-    const real tyy = quarter * (gy_ym + P.gy) * (vy_ym + P.vy) + pk -
-                     (two_eta * (P.vy - vy_ym) * inv_h + lam2 * div_k) - syy;
-    const real tzz1 = quarter * (P.gz + Q.gz) * (P.vz + Q.vz) + pk1 -
-                      (two_eta * (Q.vz - P.vz) * inv_h + lam2 * div_k1) - szz1;
-    const real visc_xy = eta * ((vx_yp - P.vx) + (vy_xp - P.vy)) * inv_h;
-    const real txy = quarter * (P.gx + gx_yp) * (P.vy + vy_xp) - visc_xy - sxy;
-    const real tyx = quarter * (P.gy + gy_xp) * (P.vx + vx_yp) - visc_xy - sxy;
-    const real visc_xz = eta * ((Q.vx - P.vx) + (vz_xp - P.vz)) * inv_h;
-    const real txz = quarter * (P.gx + Q.gx) * (P.vz + vz_xp) - visc_xz - sxz;
-    const real tzx = quarter * (P.gz + gz_xp) * (P.vx + Q.vx) - visc_xz - sxz;
-    const real visc_yz = eta * ((Q.vy - P.vy) + (vz_yp - P.vz)) * inv_h;
-    const real tyz = quarter * (P.gy + Q.gy) * (P.vz + vz_yp) - visc_yz - syz;
-    const real tzy = quarter * (P.gz + gz_yp) * (P.vy + Q.vy) - visc_yz - syz;
+    real txx = add_rn(mul_rn(mul_rn(quarter, add_rn(gx_xm, P.gx)), add_rn(vx_xm, P.vx)), pk);
+    txx = sub_rn(txx, fma_rn(mul_rn(two_eta, sub_rn(P.vx, vx_xm)), inv_h, mul_rn(lam2, div_k)));
+    real tyy = add_rn(mul_rn(mul_rn(quarter, add_rn(gy_ym, P.gy)), add_rn(vy_ym, P.vy)), pk);
+    tyy = sub_rn(tyy, fma_rn(mul_rn(two_eta, sub_rn(P.vy, vy_ym)), inv_h, mul_rn(lam2, div_k)));
+    real tzz1 = add_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, Q.gz)), add_rn(P.vz, Q.vz)), pk1);
+    tzz1 = sub_rn(tzz1, fma_rn(mul_rn(two_eta, sub_rn(Q.vz, P.vz)), inv_h, mul_rn(lam2, div_k1)));
+    const real visc_xy = mul_rn(mul_rn(eta, add_rn(sub_rn(vx_yp, P.vx), sub_rn(vy_xp, P.vy))), inv_h);
+    real txy = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gx, gx_yp)), add_rn(P.vy, vy_xp)), visc_xy);
+    real tyx = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gy, gy_xp)), add_rn(P.vx, vx_yp)), visc_xy);
+    const real visc_xz = mul_rn(mul_rn(eta, add_rn(sub_rn(Q.vx, P.vx), sub_rn(vz_xp, P.vz))), inv_h);
+    real txz = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gx, Q.gx)), add_rn(P.vz, vz_xp)), visc_xz);
+    real tzx = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, gz_xp)), add_rn(P.vx, Q.vx)), visc_xz);
+    const real visc_yz = mul_rn(mul_rn(eta, add_rn(sub_rn(Q.vy, P.vy), sub_rn(vz_yp, P.vz))), inv_h);
+    real tyz = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gy, Q.gy)), add_rn(P.vz, vz_yp)), visc_yz);
+    real tzy = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, gz_yp)), add_rn(P.vy, Q.vy)), visc_yz);
+    if (NOISE) {
+      // Sigma_aa = sqrt2 S N_aa + sqrt2 (B - S/3) tr N, Sigma_ab = S N_ab
+      const real ntr = mul_rn(nt, add_rn(add_rn(P.nz[0], P.nz[1]), P.nz[2]));
+      const real ntr1 = mul_rn(nt, add_rn(add_rn(Q.nz[0], Q.nz[1]), Q.nz[2]));
+      txx = sub_rn(txx, fma_rn(nd, P.nz[0], ntr));
+      tyy = sub_rn(tyy, fma_rn(nd, P.nz[1], ntr));
+      tzz1 = sub_rn(tzz1, fma_rn(nd, Q.nz[2], ntr1));
+      const real sxy = mul_rn(ne, P.nz[3]), sxz = mul_rn(ne, P.nz[4]), syz = mul_rn(ne, P.nz[5]);
+      txy = sub_rn(txy, sxy);
+      tyx = sub_rn(tyx, sxy);
+      txz = sub_rn(txz, sxz);
+      tzx = sub_rn(tzx, sxz);
+      tyz = sub_rn(tyz, syz);
+      tzy = sub_rn(tzy, syz);
+    }
 
     T[TXX * EXY + t] = txx;
     T[TYY * EXY + t] = tyy;
@@ -279,17 +298,26 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     __syncthreads();
 
     if (out_here) {
-      const real r_rho = -((P.gx - gx_xm) + (P.gy - gy_ym) + (P.gz - gz_m)) * inv_h;
-      const real r_gx = -((T[TXX * EXY + eXp] - txx) + (txy - T[TXY * EXY + eYm]) + (txz - txz_m)) * inv_h;
-      const real r_gy = -((T[TYY * EXY + eYp] - tyy) + (tyx - T[TYX * EXY + eXm]) + (tyz - tyz_m)) * inv_h;
-      const real r_gz = -((tzz1 - tzz_k) + (tzx - T[TZX * EXY + eXm]) + (tzy - T[TZY * EXY + eYm])) * inv_h;
+      const real neg_inv_h = -inv_h;
+      const real r_rho =
+          mul_rn(add_rn(add_rn(sub_rn(P.gx, gx_xm), sub_rn(P.gy, gy_ym)), sub_rn(P.gz, gz_m)), neg_inv_h);
+      const real r_gx = mul_rn(add_rn(add_rn(sub_rn(T[TXX * EXY + eXp], txx), sub_rn(txy, T[TXY * EXY + eYm])),
+                                      sub_rn(txz, txz_m)),
+                               neg_inv_h);
+      const real r_gy = mul_rn(add_rn(add_rn(sub_rn(T[TYY * EXY + eYp], tyy), sub_rn(tyx, T[TYX * EXY + eXm])),
+                                      sub_rn(tyz, tyz_m)),
+                               neg_inv_h);
+      const real r_gz = mul_rn(add_rn(add_rn(sub_rn(tzz1, tzz_k), sub_rn(tzx, T[TZX * EXY + eXm])),
+                                      sub_rn(tzy, T[TZY * EXY + eYm])),
+                               neg_inv_h);
       const uint32_t i = i_out;
-      real o0 = P.dr + dt * r_rho, o1 = P.gx + dt * r_gx, o2 = P.gy + dt * r_gy, o3 = P.gz + dt * r_gz;
+      real o0 = fma_rn(dt, r_rho, P.dr), o1 = fma_rn(dt, r_gx, P.gx), o2 = fma_rn(dt, r_gy, P.gy),
+           o3 = fma_rn(dt, r_gz, P.gz);
       if (STAGE != 0) {
-        o0 = ca * un[0] + cb * o0;
-        o1 = ca * un[1] + cb * o1;
-        o2 = ca * un[2] + cb * o2;
-        o3 = ca * un[3] + cb * o3;
+        o0 = fma_rn(ca, un[0], mul_rn(cb, o0));
+        o1 = fma_rn(ca, un[1], mul_rn(cb, o1));
+        o2 = fma_rn(ca, un[2], mul_rn(cb, o2));
+        o3 = fma_rn(ca, un[3], mul_rn(cb, o3));
       }
       a.o[0][i] = o0;
       a.o[1][i] = o1;
@@ -311,6 +339,351 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     // per-CTA partial of sum (rho - rho0) cos(k x), fixed reduction order
     const real v = warp_sum(mode_acc);
     __shared__ real s_red[32];
+    const int lane = t & 31, wid = t >> 5;
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      const int nw = (EXY + 31) / 32;
+      for (int j = 0; j < nw; ++j) s += double(s_red[j]);
+      a.partials[blockIdx.x] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------- FP32 pair kernel
+// The FP32 form of the stage kernel for the wide tile: each thread marches two
+// z planes at a time and holds every per-cell quantity as a pair {plane k,
+// plane k+1}, so that shared memory moves 8-byte pairs and the barriers, the
+// address arithmetic and the loop overhead are paid once per two planes; the
+// next pair's loads are staged into shared memory with asynchronous copies
+// while the current pair's fluxes are computed.  Quantities one plane up or
+// down ("U" and "D" below) are pairs shifted by one element, assembled from
+// the neighbouring pair or from values carried between iterations.  Each
+// plane's values are the same sequence of rounded operations as in the scalar
+// kernel, whichever element of a pair, CTA, run or kernel computes them, so
+// every tiling gives the same bits.
+
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+// Pair arithmetic element by element with the scalar rounded intrinsics.
+// (The packed FP32x2 intrinsics were measured no faster here, and the
+// compiler fuses a packed multiply and add into one packed FMA even in their
+// round-to-nearest forms, so their results would depend on the tiling.)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, -b.x), __fadd_rn(a.y, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 up2(float2 p, float q_x) { return make_float2(p.y, q_x); }     // {X(k+1), X(k+2)}
+__device__ __forceinline__ float2 dn2(float carried, float2 p) { return make_float2(carried, p.x); }   // {X(k-1), X(k)}
+
+// 4-byte asynchronous global -> shared copies (one per value, issued by the
+// thread that later reads it back, so no barrier guards the staging slot)
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// staging slot of one plane pair: the thread's own values, [field][EXY]
+enum StageField {
+  SF_DR0, SF_DR1, SF_DR2, SF_DRX0, SF_DRX1, SF_DRY0, SF_DRY1, SF_GX0, SF_GX1, SF_GY0, SF_GY1, SF_GZ0, SF_GZ1,
+  SF_PP0, SF_PP1, SF_NZ, kStageFields = SF_NZ + 12
+};
+
+// the finished values of a plane pair
+struct Pair2 {
+  float2 dr, gx, gy, gz, vx, vy, vz, pk;   // pk = c^2 delta rho + S Omega + p_ext
+  float2 s[6];                              // Sigma: xx, yy, zz, xy, xz, yz
+};
+
+// resident CTAs per SM the register budget is sized for (a 34 x 10 tile: 1)
+template <int EXY>
+constexpr int z2_min_ctas() {
+#ifdef IC_Z2_MIN_CTAS
+  return IC_Z2_MIN_CTAS;
+#else
+  return (34 * (IC_FP32_TILE_Y + 2) + EXY - 1) / EXY;
+#endif
+}
+
+template <int TX, int TY, int STAGE, bool NOISE>
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (TY + 2)>())
+    k_rk3_stage_z2(const StageArgs<float> a) {
+  constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
+  enum { GX = 0, GY, GZ, VX, VY, VZ };
+  enum { TXX = 0, TYY, TXY, TYX, TZX, TZY };
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);   // [2 slots][6 fields][EXY]
+  float2 *T = sm + 12 * EXY;                            // [6 fluxes][EXY]
+  float *stg = reinterpret_cast<float *>(T + 6 * EXY);  // [kStageFields][EXY]
+  const FluidConsts<float> &c = a.c;
+  const int NX = c.nx, NY = c.ny, NZ = c.nz;
+  const int t = threadIdx.x;
+  const int ex = t % EX, ey = t / EX;
+  const int eXm = ey * EX + max(ex - 1, 0), eXp = ey * EX + min(ex + 1, EX - 1);
+  const int eYm = max(ey - 1, 0) * EX + ex, eYp = min(ey + 1, EY - 1) * EX + ex;
+  // planes touched lie in [-2, NZ + 3): one compare-and-add wraps them (NZ >= 6)
+  const auto zwrap = [NZ](int kk) { return kk < 0 ? kk + NZ : (kk >= NZ ? kk - NZ : kk); };
+
+  const int64_t step = *a.step;
+  const float drive = c.drive[STAGE];
+  const float2 rho0 = splat2(c.rho0), half = splat2(0.5f), quarter = splat2(0.25f);
+  const float2 inv_h = splat2(c.inv_h), neg_inv_h = splat2(-c.inv_h), c2 = splat2(c.c2);
+  const float2 eta = splat2(c.eta), lam2 = splat2(c.lam2), two_eta = splat2(2.0f * c.eta);
+  const float2 nd = splat2(c.noise_diag), nt = splat2(c.noise_trace), ne = splat2(c.noise_edge);
+  const float beta = STAGE == 0 ? -1.7320508075688772f : (STAGE == 1 ? 1.7320508075688772f : 0.0f);
+  const RngKey key{c.k0, c.k1, c.box};
+  const uint32_t ustep = uint32_t(step);
+  const float2 ca = splat2(float(kStageA[STAGE])), cb = splat2(float(kStageB[STAGE])), dt = splat2(c.dt);
+  const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
+  float mode_acc = 0.0f;
+
+  const int units = a.ncols_x * a.ncols_y * NZ;
+  const int u_end = int((long long)units * (blockIdx.x + 1) / gridDim.x);
+  for (int u = int((long long)units * blockIdx.x / gridDim.x); u < u_end;) {
+    const int col = u / NZ;
+    const int z0 = u - col * NZ;
+    const int z1 = min(NZ, z0 + (u_end - u));
+    u += z1 - z0;
+    const int gx_raw = (col % a.ncols_x) * TX + ex - 1;
+    const int gy_raw = (col / a.ncols_x) * TY + ey - 1;
+    const int x = wrap(gx_raw, NX), y = wrap(gy_raw, NY);
+    const int xp = (x + 1 == NX) ? 0 : x + 1;
+    const int yp = (y + 1 == NY) ? 0 : y + 1;
+    const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx_raw < NX && gy_raw < NY;
+    const uint32_t o_c = uint32_t(x) + uint32_t(NX) * uint32_t(y);
+    const uint32_t o_xp = uint32_t(xp) + uint32_t(NX) * uint32_t(y);
+    const uint32_t o_yp = uint32_t(x) + uint32_t(NX) * uint32_t(yp);
+    const float cos_xy = c.wave_axis < 2 ? c.cos_table[c.wave_axis == 0 ? x : y] : 0.0f;
+    auto cosw = [&](int kk) -> float { return c.wave_axis < 2 ? cos_xy : c.cos_table[zwrap(kk)]; };
+    auto profile = [&](int kk) -> float {
+      if (c.forcing == IC_FORCE_MODE) return cosw(kk);
+      if (c.forcing == IC_FORCE_PLANE) {
+        const int coord = c.wave_axis == 0 ? x : (c.wave_axis == 1 ? y : zwrap(kk));
+        return coord == c.plane_index ? 1.0f : 0.0f;
+      }
+      return 0.0f;
+    };
+    const auto stored = [&](int kk) { return interior && kk >= z0 && kk < z1; };
+
+    // asynchronous loads of the planes kk, kk + 1 into this thread's staging slot
+    auto issue2 = [&](int kk) {
+      const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n,
+                     b2 = uint32_t(zwrap(kk + 2)) * plane_n;
+      const float *S0 = a.s[0];
+      cp_async4(stg + SF_DR0 * EXY + t, S0 + o_c + b0);
+      cp_async4(stg + SF_DR1 * EXY + t, S0 + o_c + b1);
+      cp_async4(stg + SF_DR2 * EXY + t, S0 + o_c + b2);
+      cp_async4(stg + SF_DRX0 * EXY + t, S0 + o_xp + b0);
+      cp_async4(stg + SF_DRX1 * EXY + t, S0 + o_xp + b1);
+      cp_async4(stg + SF_DRY0 * EXY + t, S0 + o_yp + b0);
+      cp_async4(stg + SF_DRY1 * EXY + t, S0 + o_yp + b1);
+      cp_async4(stg + SF_GX0 * EXY + t, a.s[1] + o_c + b0);
+      cp_async4(stg + SF_GX1 * EXY + t, a.s[1] + o_c + b1);
+      cp_async4(stg + SF_GY0 * EXY + t, a.s[2] + o_c + b0);
+      cp_async4(stg + SF_GY1 * EXY + t, a.s[2] + o_c + b1);
+      cp_async4(stg + SF_GZ0 * EXY + t, a.s[3] + o_c + b0);
+      cp_async4(stg + SF_GZ1 * EXY + t, a.s[3] + o_c + b1);
+      if (a.pp) {
+        cp_async4(stg + SF_PP0 * EXY + t, a.pp + o_c + b0);
+        cp_async4(stg + SF_PP1 * EXY + t, a.pp + o_c + b1);
+      }
+      if (NOISE && STAGE != 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          cp_async4(stg + (SF_NZ + 2 * j) * EXY + t, a.noise_in[j] + o_c + b0);
+          cp_async4(stg + (SF_NZ + 2 * j + 1) * EXY + t, a.noise_in[j] + o_c + b1);
+        }
+      }
+      cp_async_commit();
+    };
+    // finished values of the planes kk, kk + 1 from the staged loads
+    auto finish2 = [&](int kk) -> Pair2 {
+      const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n;
+      cp_async_wait_all();
+      auto ld = [&](int f) { return stg[f * EXY + t]; };
+      const float2 dr = make_float2(ld(SF_DR0), ld(SF_DR1));
+      const float2 drx = make_float2(ld(SF_DRX0), ld(SF_DRX1));
+      const float2 dry = make_float2(ld(SF_DRY0), ld(SF_DRY1));
+      const float2 drz = make_float2(dr.y, ld(SF_DR2));
+      Pair2 P;
+      P.dr = dr;
+      P.gx = make_float2(ld(SF_GX0), ld(SF_GX1));
+      P.gy = make_float2(ld(SF_GY0), ld(SF_GY1));
+      P.gz = make_float2(ld(SF_GZ0), ld(SF_GZ1));
+      const float2 pp = a.pp ? make_float2(ld(SF_PP0), ld(SF_PP1)) : splat2(0.0f);
+      const float2 rfx = fma2(half, add2(dr, drx), rho0);
+      const float2 rfy = fma2(half, add2(dr, dry), rho0);
+      const float2 rfz = fma2(half, add2(dr, drz), rho0);
+      P.vx = make_float2(__fdividef(P.gx.x, rfx.x), __fdividef(P.gx.y, rfx.y));
+      P.vy = make_float2(__fdividef(P.gy.x, rfy.x), __fdividef(P.gy.y, rfy.y));
+      P.vz = make_float2(__fdividef(P.gz.x, rfz.x), __fdividef(P.gz.y, rfz.y));
+      P.pk = add2(fma2(c2, dr, pp), mul2(splat2(drive), make_float2(profile(kk), profile(kk + 1))));
+      if (NOISE) {
+        float2 w[6];
+        if (STAGE == 0) {
+          // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const uint32_t i = o_c + (e == 0 ? b0 : b1);
+            float wa[6], wb[6];
+            stress_normals_ab(key, i, ustep, wa, wb);
+            const bool st = stored(kk + e);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+              const float v = fma_rn(beta, wb[j], wa[j]);
+              if (e == 0) w[j].x = v; else w[j].y = v;
+              if (st) {
+                a.noise_out[j][i] = fma_rn(1.7320508075688772f, wb[j], wa[j]);
+                a.noise_out[6 + j][i] = wa[j];
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 6; ++j) w[j] = make_float2(ld(SF_NZ + 2 * j), ld(SF_NZ + 2 * j + 1));
+        }
+        const float2 tr = add2(add2(w[0], w[1]), w[2]);
+        const float2 ntr = mul2(nt, tr);
+        P.s[0] = fma2(nd, w[0], ntr);
+        P.s[1] = fma2(nd, w[1], ntr);
+        P.s[2] = fma2(nd, w[2], ntr);
+        P.s[3] = mul2(ne, w[3]);
+        P.s[4] = mul2(ne, w[4]);
+        P.s[5] = mul2(ne, w[5]);
+      }
+      return P;
+    };
+    auto store_pair = [&](int slot, const Pair2 &v) {
+      float2 *B = sm + slot * 6 * EXY;
+      B[GX * EXY + t] = v.gx;
+      B[GY * EXY + t] = v.gy;
+      B[GZ * EXY + t] = v.gz;
+      B[VX * EXY + t] = v.vx;
+      B[VY * EXY + t] = v.vy;
+      B[VZ * EXY + t] = v.vz;
+    };
+
+    __syncthreads();   // the previous run's last reads of shared memory are done
+    // one pair below the run supplies the values carried into its first plane
+    issue2(z0 - 2);
+    Pair2 P = finish2(z0 - 2);
+    issue2(z0);
+    store_pair(0, P);
+    float gz_m = 0.0f, txz_m = 0.0f, tyz_m = 0.0f, tzz_k = 0.0f, div_k = 0.0f;
+    int slot = 0;
+    for (int k = z0 - 2; k < z1; k += 2, slot ^= 1) {
+      // U^n of the output planes
+      const bool out0 = stored(k), out1 = stored(k + 1);
+      const uint32_t i0 = o_c + uint32_t(zwrap(k)) * plane_n, i1 = o_c + uint32_t(zwrap(k + 1)) * plane_n;
+      float2 un[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        un[j] = splat2(0.0f);
+        if (STAGE != 0) {
+          if (out0) un[j].x = a.n[j][i0];
+          if (out1) un[j].y = a.n[j][i1];
+        }
+      }
+      const Pair2 Q = finish2(k + 2);
+      if (k + 2 < z1) issue2(k + 4);   // the next iteration's pair; overlaps this flux work
+      store_pair(slot ^ 1, Q);
+      __syncthreads();
+      const float2 *Ps = sm + slot * 6 * EXY;
+      const float2 *Qs = sm + (slot ^ 1) * 6 * EXY;
+      const float2 gx_xm = Ps[GX * EXY + eXm], vx_xm = Ps[VX * EXY + eXm];
+      const float2 gy_ym = Ps[GY * EXY + eYm], vy_ym = Ps[VY * EXY + eYm];
+      const float2 gx_yp = Ps[GX * EXY + eYp], vx_yp = Ps[VX * EXY + eYp];
+      const float2 gy_xp = Ps[GY * EXY + eXp], vy_xp = Ps[VY * EXY + eXp];
+      const float2 gz_xp = Ps[GZ * EXY + eXp], vz_xp = Ps[VZ * EXY + eXp];
+      const float2 gz_yp = Ps[GZ * EXY + eYp], vz_yp = Ps[VZ * EXY + eYp];
+      const float qvx_xm = Qs[VX * EXY + eXm].x, qvy_ym = Qs[VY * EXY + eYm].x;
+
+      // pairs one plane up: {k+1, k+2}
+      const float2 Uvx = up2(P.vx, Q.vx.x), Uvy = up2(P.vy, Q.vy.x), Uvz = up2(P.vz, Q.vz.x);
+      const float2 Ugx = up2(P.gx, Q.gx.x), Ugy = up2(P.gy, Q.gy.x), Ugz = up2(P.gz, Q.gz.x);
+      const float2 div_up = mul2(add2(add2(sub2(Uvx, up2(vx_xm, qvx_xm)), sub2(Uvy, up2(vy_ym, qvy_ym))),
+                                      sub2(Uvz, P.vz)),
+                                 inv_h);
+      const float2 div = dn2(div_k, div_up);   // {div(k), div(k+1)}
+
+      float2 txx = add2(mul2(mul2(quarter, add2(gx_xm, P.gx)), add2(vx_xm, P.vx)), P.pk);
+      txx = sub2(txx, fma2(mul2(two_eta, sub2(P.vx, vx_xm)), inv_h, mul2(lam2, div)));
+      float2 tyy = add2(mul2(mul2(quarter, add2(gy_ym, P.gy)), add2(vy_ym, P.vy)), P.pk);
+      tyy = sub2(tyy, fma2(mul2(two_eta, sub2(P.vy, vy_ym)), inv_h, mul2(lam2, div)));
+      float2 tzz_up = add2(mul2(mul2(quarter, add2(P.gz, Ugz)), add2(P.vz, Uvz)), up2(P.pk, Q.pk.x));
+      tzz_up = sub2(tzz_up, fma2(mul2(two_eta, sub2(Uvz, P.vz)), inv_h, mul2(lam2, div_up)));
+      const float2 visc_xy = mul2(mul2(eta, add2(sub2(vx_yp, P.vx), sub2(vy_xp, P.vy))), inv_h);
+      float2 txy = sub2(mul2(mul2(quarter, add2(P.gx, gx_yp)), add2(P.vy, vy_xp)), visc_xy);
+      float2 tyx = sub2(mul2(mul2(quarter, add2(P.gy, gy_xp)), add2(P.vx, vx_yp)), visc_xy);
+      const float2 visc_xz = mul2(mul2(eta, add2(sub2(Uvx, P.vx), sub2(vz_xp, P.vz))), inv_h);
+      float2 txz = sub2(mul2(mul2(quarter, add2(P.gx, Ugx)), add2(P.vz, vz_xp)), visc_xz);
+      float2 tzx = sub2(mul2(mul2(quarter, add2(P.gz, gz_xp)), add2(P.vx, Uvx)), visc_xz);
+      const float2 visc_yz = mul2(mul2(eta, add2(sub2(Uvy, P.vy), sub2(vz_yp, P.vz))), inv_h);
+      float2 tyz = sub2(mul2(mul2(quarter, add2(P.gy, Ugy)), add2(P.vz, vz_yp)), visc_yz);
+      float2 tzy = sub2(mul2(mul2(quarter, add2(P.gz, gz_yp)), add2(P.vy, Uvy)), visc_yz);
+      if (NOISE) {
+        txx = sub2(txx, P.s[0]);
+        tyy = sub2(tyy, P.s[1]);
+        tzz_up = sub2(tzz_up, up2(P.s[2], Q.s[2].x));
+        txy = sub2(txy, P.s[3]);
+        tyx = sub2(tyx, P.s[3]);
+        txz = sub2(txz, P.s[4]);
+        tzx = sub2(tzx, P.s[4]);
+        tyz = sub2(tyz, P.s[5]);
+        tzy = sub2(tzy, P.s[5]);
+      }
+      T[TXX * EXY + t] = txx;
+      T[TYY * EXY + t] = tyy;
+      T[TXY * EXY + t] = txy;
+      T[TYX * EXY + t] = tyx;
+      T[TZX * EXY + t] = tzx;
+      T[TZY * EXY + t] = tzy;
+      __syncthreads();
+
+      if (out0 || out1) {
+        const float2 r_rho =
+            mul2(add2(add2(sub2(P.gx, gx_xm), sub2(P.gy, gy_ym)), sub2(P.gz, dn2(gz_m, P.gz))), neg_inv_h);
+        const float2 r_gx = mul2(add2(add2(sub2(T[TXX * EXY + eXp], txx), sub2(txy, T[TXY * EXY + eYm])),
+                                      sub2(txz, dn2(txz_m, txz))),
+                                 neg_inv_h);
+        const float2 r_gy = mul2(add2(add2(sub2(T[TYY * EXY + eYp], tyy), sub2(tyx, T[TYX * EXY + eXm])),
+                                      sub2(tyz, dn2(tyz_m, tyz))),
+                                 neg_inv_h);
+        const float2 r_gz = mul2(add2(add2(sub2(tzz_up, dn2(tzz_k, tzz_up)), sub2(tzx, T[TZX * EXY + eXm])),
+                                      sub2(tzy, T[TZY * EXY + eYm])),
+                                 neg_inv_h);
+        float2 o[4] = {fma2(dt, r_rho, P.dr), fma2(dt, r_gx, P.gx), fma2(dt, r_gy, P.gy), fma2(dt, r_gz, P.gz)};
+        if (STAGE != 0) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = fma2(ca, un[j], mul2(cb, o[j]));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (out0) a.o[j][i0] = o[j].x;
+          if (out1) a.o[j][i1] = o[j].y;
+        }
+        if (STAGE == 2) {
+          if (out0) mode_acc = fmaf(o[0].x, cosw(k), mode_acc);
+          if (out1) mode_acc = fmaf(o[0].y, cosw(k + 1), mode_acc);
+        }
+      }
+      gz_m = P.gz.y;
+      txz_m = txz.y;
+      tyz_m = tyz.y;
+      tzz_k = tzz_up.y;
+      div_k = div_up.y;
+      P = Q;
+    }
+  }
+
+  if (STAGE == 2) {
+    // per-CTA partial of sum (rho - rho0) cos(k x), fixed reduction order
+    const float v = warp_sum(mode_acc);
+    __shared__ float s_red[32];
     const int lane = t & 31, wid = t >> 5;
     if (lane == 0) s_red[wid] = v;
     __syncthreads();
@@ -360,8 +733,9 @@ FluidConsts<real> fluid_consts(const ic_ctx *ctx) {
 }
 
 // Tile shapes of the stage kernel: variant 0 is the wide tile tuned for large
-// boxes; variant 1 halves the x extent so that 16- and 48-cell boxes fill
-// their tiles (the autotuner picks between them and the z chunk).
+// boxes; variant 1 is a 16 x 8 (FP32) or 16 x 4 (FP64) tile that boxes with
+// edges of 16, 24, 32 or 48 cells fill exactly (the autotuner picks between
+// them and the z chunk).
 template <typename real, int V>
 struct TileShape;
 template <>
@@ -370,7 +744,7 @@ struct TileShape<float, 0> {
 };
 template <>
 struct TileShape<float, 1> {
-  static constexpr int TX = 16, TY = IC_FP32_TILE_Y;
+  static constexpr int TX = 16, TY = 8;
 };
 template <>
 struct TileShape<double, 0> {
@@ -394,15 +768,43 @@ struct StageLayout {
   int ncols_x, ncols_y, ctas;
 };
 
+// The pair kernel runs the wide FP32 tile; the scalar kernel the narrow FP32
+// tile (small boxes, short runs) and FP64.  Both evaluate the same rounded
+// operations per plane.
+template <typename real, int TX>
+constexpr bool use_pair_kernel() { return sizeof(real) == 4 && TX == 32; }
+
+// CTAs per SM the launched stage kernel is budgeted for
+template <typename real, int TX, int TY>
+constexpr int stage_min_ctas() {
+  if constexpr (use_pair_kernel<real, TX>()) return z2_min_ctas<(TX + 2) * (TY + 2)>();
+  return min_ctas<real, (TX + 2) * (TY + 2)>();
+}
+
+template <int TX, int TY, int STAGE, bool NOISE, typename real>
+void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream) {
+  constexpr int EXY = (TX + 2) * (TY + 2);
+  if constexpr (use_pair_kernel<real, TX>()) {
+    const size_t smem = 18 * EXY * sizeof(float2) + kStageFields * EXY * sizeof(float);
+    auto kern = k_rk3_stage_z2<TX, TY, STAGE, NOISE>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    kern<<<ctas, EXY, smem, stream>>>(a);
+  } else {
+    const size_t smem = 18 * EXY * sizeof(real);
+    auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    kern<<<ctas, EXY, smem, stream>>>(a);
+  }
+}
+
 template <typename real, int V>
 StageLayout stage_layout_v(const ic_grid_params &p, int zchunk, int sm_count) {
   constexpr int TX = TileShape<real, V>::TX, TY = TileShape<real, V>::TY;
-  constexpr int EXY = (TX + 2) * (TY + 2);
   StageLayout l;
   l.ncols_x = (p.nx + TX - 1) / TX;
   l.ncols_y = (p.ny + TY - 1) / TY;
   const long long units = (long long)l.ncols_x * l.ncols_y * p.nz;
-  const long long resident = (long long)min_ctas<real, EXY>() * sm_count;
+  const long long resident = (long long)stage_min_ctas<real, TX, TY>() * sm_count;
   l.ctas = int(std::max<long long>(1, std::min<long long>(resident, (units + zchunk - 1) / zchunk)));
   return l;
 }
@@ -417,7 +819,6 @@ template <typename real, int V, int STAGE, bool NOISE>
 cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const in_n[4],
                            void *const out[4]) {
   constexpr int TX = TileShape<real, V>::TX, TY = TileShape<real, V>::TY;
-  constexpr int EXY = (TX + 2) * (TY + 2);
   StageArgs<real> a;
   for (int j = 0; j < 4; ++j) {
     a.s[j] = static_cast<const real *>(in_s[j]);
@@ -434,10 +835,7 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   const StageLayout l = stage_layout_v<real, V>(ctx->p, zchunk_for(ctx), ctx->sm_count);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
-  const size_t smem = 18 * EXY * sizeof(real);
-  auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  kern<<<l.ctas, EXY, smem, ctx->stream>>>(a);
+  launch_stage_kernel<TX, TY, STAGE, NOISE>(a, l.ctas, ctx->stream);
   return cudaGetLastError();
 }
 
@@ -625,7 +1023,8 @@ bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk) {
 void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk) {
   const bool f = ctx->p.precision == IC_FP32, v1 = ctx->tile_variant == 1;
   *tx = v1 ? 16 : 32;
-  *ty = f ? TileShape<float, 0>::TY : TileShape<double, 0>::TY;
+  *ty = f ? (v1 ? TileShape<float, 1>::TY : TileShape<float, 0>::TY)
+          : (v1 ? TileShape<double, 1>::TY : TileShape<double, 0>::TY);
   *zchunk = zchunk_for(ctx);
 }
 
@@ -641,7 +1040,6 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
                                void *const noise[12], const int64_t *step, double *partials,
                                cudaStream_t stream) {
   constexpr int TX = TileShape<real, 0>::TX, TY = TileShape<real, 0>::TY;
-  constexpr int EXY = (TX + 2) * (TY + 2);
   StageArgs<real> a;
   for (int j = 0; j < 4; ++j) {
     a.s[j] = static_cast<const real *>(in_s[j]);
@@ -658,23 +1056,14 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
   const StageLayout l = stage_layout_v<real, 0>(p, std::min<int>(p.nz, IC_ZCHUNK), 1 << 20);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
-  const dim3 grid(l.ctas);
-  const size_t smem = 18 * EXY * sizeof(real);
   const bool noise_on = p.kT > 0.0;
   switch (stage * 2 + (noise_on ? 1 : 0)) {
-#define IC_RAW(S, N)                                                                       \
-  {                                                                                        \
-    auto kern = k_rk3_stage<real, TX, TY, S, N>;                                            \
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-    kern<<<grid, EXY, smem, stream>>>(a);                                                   \
-  } break;
-    case 0: IC_RAW(0, false)
-    case 1: IC_RAW(0, true)
-    case 2: IC_RAW(1, false)
-    case 3: IC_RAW(1, true)
-    case 4: IC_RAW(2, false)
-    default: IC_RAW(2, true)
-#undef IC_RAW
+    case 0: launch_stage_kernel<TX, TY, 0, false>(a, l.ctas, stream); break;
+    case 1: launch_stage_kernel<TX, TY, 0, true>(a, l.ctas, stream); break;
+    case 2: launch_stage_kernel<TX, TY, 1, false>(a, l.ctas, stream); break;
+    case 3: launch_stage_kernel<TX, TY, 1, true>(a, l.ctas, stream); break;
+    case 4: launch_stage_kernel<TX, TY, 2, false>(a, l.ctas, stream); break;
+    default: launch_stage_kernel<TX, TY, 2, true>(a, l.ctas, stream); break;
   }
   return cudaGetLastError();
 }
