@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--workload", default="box", choices=["box", "ensemble"],
                     help="box: the 128^3 single box (default); ensemble: the batched 256-box ensemble")
     ap.add_argument("--boxes", type=int, default=256)
+    ap.add_argument("--tile", type=int, nargs=2, metavar=("TILE_X", "ZCHUNK"), default=None,
+                    help="fixed stage-kernel tiling instead of the autotuner's (e.g. for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -301,7 +303,11 @@ def main():
             dist.barrier()
 
     # stage-kernel tiling picked by the library's autotuner, then warm-up (captures the graphs)
-    tiling = grid.autotune(reps=3)
+    if args.tile:
+        grid.set_tile(*args.tile)
+        tiling = grid.tile()
+    else:
+        tiling = grid.autotune(reps=3)
     grid.step(args.warmup)
     grid.sync()
 
@@ -353,7 +359,9 @@ def main():
     if os.path.exists(tfile):
         with open(tfile) as f:
             tj = json.load(f)
-        if tj.get("precision") == args.precision and tj.get("cells") == cells:
+        # ncu DRAM bytes of the same kernel (same precision, size and tile width)
+        if (tj.get("precision") == args.precision and tj.get("cells") == cells
+                and tj.get("tile_x") == tiling[0]):
             traffic = tj.get("bytes_per_launch")
 
     # end-to-end through the public API with host buffers: one step per call,
@@ -396,7 +404,8 @@ def main():
             "particle_steps_per_s": pvalue,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_rk3_stage (3 launches per step)",
+                         "kernel": "k_rk3_stage (3 launches per step)", "traffic_unit": "bytes per launch",
+                         "alg_bytes_per_launch": alg_bytes / 3,
                          "alg_bytes_per_step": alg_bytes, "stage_ms_per_step": stage_ms_per_step,
                          "particle_ms_per_step": part_ms / args.steps, "end_ms_per_step": end_ms / args.steps},
             "gpu_launches": int(round(launches_per_step * args.steps)),
