@@ -132,6 +132,26 @@ def single_particle_config(n=32, steps=2000, k_spring=1.0, mirror=False, mass_ra
     return gp, parts, steps
 
 
+def paper_protocol_config(mass_ratio, kappa_ratio, k_spring, zeta, n=32, h=10.0, precision="fp32"):
+    """The force protocol of Sec. 6 in the Table I regime.
+
+    32^3 cells of h = 10, c_f = 4, eta = 0.5, dt = 0.1 h / c_f; the paper's
+    drive (Eq. (pext)): a pressure on the grid plane z = 0 (``forcing='plane'``)
+    holding the standing wave along z at density amplitude 1e-3 rho0 (phase
+    pi/2, so that ``velocity_phase_wave_fields`` is the matching start); two
+    tethered particles at (L/2, L/2, 3L/8) and (0, 0, -3L/8), whose radiation
+    forces are equal and opposite.
+    """
+    gp = grid_params(n, h=h, zeta=zeta, wave_amp=1e-3, forcing="plane", wave_axis=2, plane_index=0,
+                     seed=0, precision=precision, wave_phase=0.5 * np.pi)
+    L = n * h
+    q = np.array([[L / 2.0, L / 2.0, 3.0 * L / 8.0], [0.0, 0.0, 5.0 * L / 8.0]])
+    vol = KERNEL_VOLUME_CELLS * h ** 3
+    parts = dict(q=q, m_e=np.full(2, (mass_ratio - 1.0) * gp["rho0"] * vol),
+                 kappa_ratio=np.full(2, float(kappa_ratio)), k_spring=np.full(2, float(k_spring)))
+    return gp, parts
+
+
 def many_particle_config(n, n_particles, *, kT=1e-3, wave_amp=5e-3, wave_nlambda=1, seed=1,
                          min_sep=0.0, mass_range=(0.5, 2.0), kappa_range=(0.0, 2.0),
                          kappa_min=0.04, fixed_contrast=None, k_spring=0.0, precision="fp64",
