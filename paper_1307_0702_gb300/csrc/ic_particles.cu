@@ -396,7 +396,27 @@ __device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int 
 
   // face stencils of two particles can share a face only if their centre
   // bases are within 3 cells on every axis
+  // p's own term on each of its faces: the face sits at offsets (r % 3, r / 3 % 3,
+  // r / 9) - 1 of p's stencils, so it needs no offset test
+  real self_term[kFacesPerLane];
+  __syncwarp(L.mask);
+  for (int i = L.sub; i < 18; i += kGroup) sm->w[i] = P.w[18 * p + i];
+  if (L.sub < 3) sm->vec[L.sub] = vec[3 * p + L.sub];
+  __syncwarp(L.mask);
+#pragma unroll
+  for (int j = 0; j < kFacesPerLane; ++j) {
+    const int r = (L.sub + kGroup * j) % 27;
+    const int a = axis_of(j), b1 = a == 2 ? 0 : a + 1, b2 = a == 0 ? 2 : a - 1;
+    const real wt = sm->w[9 + 3 * a + r % 3] * sm->w[3 * b1 + (r / 3) % 3] * sm->w[3 * b2 + r / 9];
+    self_term[j] = wt * sm->vec[a];
+  }
+
   for_near_members(P, p, pb, 3, pc, L, [&](int m) {
+    if (m == p) {
+#pragma unroll
+      for (int j = 0; j < kFacesPerLane; ++j) total[j] += self_term[j] * pc.inv_h3;
+      return;
+    }
     __syncwarp(L.mask);
     if (L.sub < 6) sm->base[L.sub] = P.base[6 * m + L.sub];
     for (int i = L.sub; i < 18; i += kGroup) sm->w[i] = P.w[18 * m + i];
