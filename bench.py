@@ -365,11 +365,12 @@ def main():
             traffic = tj.get("bytes_per_launch")
 
     # end-to-end through the public API with host buffers: one step per call,
-    # weight uploaded from pinned memory, particle forces read back every step
+    # its averaging weight uploaded from pinned memory, the step's result -- the
+    # constraint force lambda on every particle -- read back every step
     e2e = None
     if not args.no_e2e:
         pinned_w = torch.ones(1, dtype=torch.float64).pin_memory().numpy()
-        outs = tuple(torch.empty((npart, 3), dtype=torch.float64).pin_memory().numpy() for _ in range(3))
+        outs = (torch.empty((npart, 3), dtype=torch.float64).pin_memory().numpy(), None, None)
         grid.step(1, pinned_w)
         grid.forces(outs)
         barrier()
@@ -383,8 +384,11 @@ def main():
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         el = float(tt.item())
+        # bytes the library moves: weight + (first step, count) header in; lambda
+        # in the state precision + the device status word out
         e2e = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
-               "h2d_bytes_per_step": 8 + 8, "d2h_bytes_per_step": 3 * npart * 3 * 8,
+               "h2d_bytes_per_step": 8 + 16,
+               "d2h_bytes_per_step": 3 * npart * (4 if args.precision == "fp32" else 8) + 4,
                "particle_steps_per_s": world * npart * args.steps / el}
 
     base = None

@@ -187,10 +187,18 @@ ic_status download_real(ic_ctx *ctx, double *host, const void *dev, double offse
   return IC_OK;
 }
 
+ic_status status_error(ic_ctx *ctx, int st);
+
 ic_status check_device_status(ic_ctx *ctx) {
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   int st = 0;
   IC_CUDA(ctx, cudaMemcpy(&st, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return status_error(ctx, st);
+}
+
+// The status word as read back with other data: IC_OK, or the error it flags
+// (the flags are cleared).
+ic_status status_error(ic_ctx *ctx, int st) {
   if (st == 0) return IC_OK;
   IC_CUDA(ctx, cudaMemset(ctx->d.status, 0, sizeof(int)));
   if (st & ic::kStatusNonfinite)
@@ -512,20 +520,38 @@ ic_status ic_sync(ic_ctx *ctx) {
 
 ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q) {
   if (!ctx) return IC_ERR_ARG;
-  const size_t n3 = 3 * size_t(ctx->ps.n);
-  if (ctx->ps.n > 0) {
-    ic_status st = IC_OK;
-    if (lambda) st = download_real(ctx, lambda, ctx->ps.lam, 0.0, n3);
-    if (!st && u) st = download_real(ctx, u, ctx->ps.u, 0.0, n3);
-    if (st) return st;
-    if (q) {
-      std::vector<long long> qdev(n3);
-      IC_CUDA(ctx, cudaMemcpyAsync(qdev.data(), ctx->ps.q, n3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-      IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      ic::positions_to_host(ctx, qdev.data(), n3, q);
-    }
+  // one pinned staging area, all copies queued, one synchronisation
+  const size_t n3 = 3 * size_t(ctx->ps.n), rb = n3 * ctx->real_size, need = 2 * rb + 8 * n3 + sizeof(int);
+  if (need > ctx->download_cap) {
+    if (ctx->download) cudaFreeHost(ctx->download);
+    ctx->download = nullptr;
+    ctx->download_cap = 0;
+    IC_CUDA(ctx, cudaMallocHost(&ctx->download, need));
+    ctx->download_cap = need;
   }
-  return check_device_status(ctx);
+  unsigned char *h_lam = ctx->download, *h_u = h_lam + rb, *h_q = h_u + rb, *h_st = h_q + 8 * n3;
+  if (n3) {
+    if (lambda) IC_CUDA(ctx, cudaMemcpyAsync(h_lam, ctx->ps.lam, rb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (u) IC_CUDA(ctx, cudaMemcpyAsync(h_u, ctx->ps.u, rb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (q) IC_CUDA(ctx, cudaMemcpyAsync(h_q, ctx->ps.q, 8 * n3, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  IC_CUDA(ctx, cudaMemcpyAsync(h_st, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (n3) {
+    for (int j = 0; j < 2; ++j) {
+      double *dst = j == 0 ? lambda : u;
+      const unsigned char *src = j == 0 ? h_lam : h_u;
+      if (!dst) continue;
+      if (ctx->p.precision == IC_FP32)
+        from_real<float>(src, 0.0, dst, n3);
+      else
+        from_real<double>(src, 0.0, dst, n3);
+    }
+    if (q) ic::positions_to_host(ctx, h_q, n3, q);
+  }
+  int st = 0;
+  std::memcpy(&st, h_st, sizeof(int));
+  return status_error(ctx, st);
 }
 
 ic_status ic_particle_density(ic_ctx *ctx, double *jrho) {
@@ -946,6 +972,7 @@ void ic_destroy(ic_ctx *ctx) {
   for (cudaEvent_t ev : ctx->event_pool) cudaEventDestroy(ev);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   if (ctx->staging) cudaFreeHost(ctx->staging);
+  if (ctx->download) cudaFreeHost(ctx->download);
   while (ctx->n_allocs > 0) dev_free(ctx, ctx->allocs[ctx->n_allocs - 1]);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -83,6 +83,8 @@ struct ic_ctx {
   int64_t host_wcount = 0;          // weights count currently on the device
   double *staging = nullptr;        // pinned host staging for weights (cap + 3)
   cudaEvent_t staging_done = nullptr;
+  unsigned char *download = nullptr;  // pinned host staging for per-step particle read-back
+  size_t download_cap = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
   uint64_t generation = 0;                          // bumped whenever the captured step changes
   int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)
