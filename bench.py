@@ -174,9 +174,10 @@ ENSEMBLE_METRIC = "cell-updates/s and particle-steps/s (ensemble of 256 boxes, e
 
 
 def run_ensemble(args):
-    """Batched ensemble: 256 FP32 boxes advanced by ic_batch_step (one CUDA graph
-    launch per step), after ic_batch_autotune; beside it the same ensemble with
-    the default tiling and unbatched (one ic_step per box per step)."""
+    """Batched ensemble: 256 FP32 boxes advanced by ic_batch_step after
+    ic_batch_autotune; beside it the same ensemble with the default tiling,
+    as one captured graph per ensemble step, and unbatched (one ic_step per
+    box per step)."""
     import torch
 
     from paper_1307_0702_gb300 import Batch, workloads as W
@@ -222,6 +223,10 @@ def run_ensemble(args):
     time.sleep(0.3)
     t_batch, wall_batch = timed(lambda: batch.step(1), args.steps)
     clocks = sampler.stop()
+    os.environ["IC_BATCH_GRAPH"] = "1"        # the whole ensemble step as one graph
+    batch.step(args.warmup)
+    t_one, wall_one = timed(lambda: batch.step(1), args.steps)
+    os.environ.pop("IC_BATCH_GRAPH")
     for g in grids:
         g.step(args.warmup)
     t_unb, wall_unb = timed(unbatched, args.steps)
@@ -233,12 +238,14 @@ def run_ensemble(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ensemble: 256 FP32 boxes, edges uniform in {16,24,32,48}, 1-200 particles each "
-                               "(min sep 2h), kT=1e-3, Philox seed = box index, one CUDA graph per step",
+                               "(min sep 2h), kT=1e-3, Philox seed = box index, ic_batch_step",
                    "boxes": len(grids), "cells": cells, "particles": npart,
                    "l2": "flushed between timed steps (512 MB write, outside the step events)"},
         "particle_steps_per_s": npart * args.steps / t_batch,
         "tiles_by_edge": {k: v[0] for k, v in sorted(by_edge.items(), key=lambda kv: int(kv[0]))},
         "default_tiling": {"value": cells * args.steps / t_default, "ms_per_step": 1e3 * t_default / args.steps},
+        "one_graph_per_step": {"value": cells * args.steps / t_one, "ms_per_step": 1e3 * t_one / args.steps,
+                               "wall_ms_per_step": 1e3 * wall_one / args.steps},
         "unbatched": {"value": cells * args.steps / t_unb, "ms_per_step": 1e3 * t_unb / args.steps,
                       "wall_ms_per_step": 1e3 * wall_unb / args.steps},
         "wall_ms_per_step": 1e3 * wall_batch / args.steps,

@@ -168,16 +168,19 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes);
 ic_status ic_device_views(ic_ctx *ctx, ic_views *out);
 
 /* Batched ensemble: many independent boxes (distinct contexts on the current
- * device, e.g. different sizes, seeds or box ids) advanced together.
- * ic_batch_step captures the whole ensemble step -- every box's kernels as a
- * branch on the box's stream; boxes that share a stream run one after the
- * other in it -- into one CUDA graph per buffer parity and
- * launches it once per step; each box evolves exactly as under its own
- * ic_step (the observables of the method are ensemble averages, Sec. 6).
- * The batch does not own the contexts; modifying a context (adding
- * particles, restoring) makes the batch re-capture.  All boxes must be at the
- * same step parity (stepped the same number of times).  w: nsteps weights
- * applied to every box, or NULL. */
+ * device, e.g. different sizes, seeds or box ids) advanced together, the
+ * observables of the method being ensemble averages (Sec. 6).  ic_batch_step
+ * uploads the weights of every box, then launches each box's own step graph
+ * on the box's stream, step by step across the ensemble, so that the boxes
+ * advance independently (no ensemble-wide join between steps).  With
+ * IC_BATCH_GRAPH=1 in the environment it instead captures the whole ensemble
+ * step -- every box's kernels as a branch on the box's stream (boxes sharing
+ * a stream run one after the other in it) -- into one CUDA graph per buffer
+ * parity and launches that once per step.  Either way each box evolves
+ * exactly as under its own ic_step.  The batch does not own the contexts;
+ * modifying a context (adding particles, restoring) makes the batch
+ * re-capture.  All boxes must be at the same step parity (stepped the same
+ * number of times).  w: nsteps weights applied to every box, or NULL. */
 typedef struct ic_batch ic_batch;
 ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out);
 ic_status ic_batch_step(ic_batch *batch, int nsteps, const double *w);

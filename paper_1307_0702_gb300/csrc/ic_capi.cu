@@ -291,6 +291,30 @@ ic_status upload_drive(ic_ctx *ctx, int64_t step) {
   return IC_OK;
 }
 
+// One step on the context's stream: its CUDA graph for the current buffer
+// parity (captured on first use), or the kernels one by one while profiling.
+ic_status launch_one_step(ic_ctx *ctx) {
+  if (graphs_enabled() && !ctx->profiling) {
+    cudaGraphExec_t &g = ctx->graph[ctx->cur];
+    if (!g) {
+      cudaGraph_t graph;
+      IC_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t le = enqueue_step(ctx, ctx->cur);
+      const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+      if (le != cudaSuccess) return cuda_fail(ctx, le, "kernel launch during capture");
+      if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+      const cudaError_t ie = cudaGraphInstantiate(&g, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    }
+    IC_CUDA(ctx, cudaGraphLaunch(g, ctx->stream));
+  } else {
+    IC_CUDA(ctx, enqueue_step(ctx, ctx->cur));
+  }
+  ctx->cur = 1 - ctx->cur;
+  return IC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -488,26 +512,9 @@ ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w) {
     const ic_status st = upload_weights(ctx, nsteps, w);
     if (st) return st;
   }
-  const bool use_graph = graphs_enabled() && !ctx->profiling;
   for (int i = 0; i < nsteps; ++i) {
-    if (use_graph) {
-      cudaGraphExec_t &g = ctx->graph[ctx->cur];
-      if (!g) {
-        cudaGraph_t graph;
-        IC_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t le = enqueue_step(ctx, ctx->cur);
-        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
-        if (le != cudaSuccess) return cuda_fail(ctx, le, "kernel launch during capture");
-        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-        const cudaError_t ie = cudaGraphInstantiate(&g, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
-      }
-      IC_CUDA(ctx, cudaGraphLaunch(g, ctx->stream));
-    } else {
-      IC_CUDA(ctx, enqueue_step(ctx, ctx->cur));
-    }
-    ctx->cur = 1 - ctx->cur;
+    const ic_status st = launch_one_step(ctx);
+    if (st) return st;
   }
   ctx->host_step += nsteps;
   return IC_OK;
@@ -726,6 +733,14 @@ struct ic_batch {
 };
 
 namespace {
+// IC_BATCH_GRAPH=1: capture the whole ensemble step into one graph per step
+// (fork to every box's stream, join back) instead of launching the boxes'
+// own step graphs
+bool batch_one_graph() {
+  const char *v = std::getenv("IC_BATCH_GRAPH");
+  return v && v[0] == '1';
+}
+
 void batch_drop_graphs(ic_batch *b) {
   for (int i = 0; i < 2; ++i)
     if (b->graph[i]) {
@@ -767,6 +782,17 @@ ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
     if (c->cur != parity || c->profiling) return fail(c, IC_ERR_STATE, "batched boxes must share the step parity");
     const ic_status st = upload_weights(c, nsteps, w);
     if (st) return st;
+  }
+  if (!batch_one_graph()) {
+    // every box's own step graph on its stream, step-major over the boxes:
+    // boxes advance independently, with no ensemble-wide join between steps
+    for (int s = 0; s < nsteps; ++s)
+      for (ic_ctx *c : b->ctxs) {
+        const ic_status st = launch_one_step(c);
+        if (st) return st;
+      }
+    for (ic_ctx *c : b->ctxs) c->host_step += nsteps;
+    return IC_OK;
   }
   // the boxes' own work (weight uploads, earlier steps) precedes the batch graph
   for (ic_ctx *c : b->ctxs) {

@@ -141,3 +141,22 @@ def test_autotune_keeps_state_and_results():
         assert np.array_equal(u, v)
     for g in (a, b, c):
         g.close()
+
+
+def test_batch_as_one_graph_equals_individual_steps(monkeypatch):
+    from paper_1307_0702_gb300 import Batch
+
+    monkeypatch.setenv("IC_BATCH_GRAPH", "1")
+    w = np.linspace(0.3, 1.0, 5)
+    a_grids, _ = make_boxes("fp32")
+    with Batch(a_grids) as batch:
+        batch.step(5, w)
+    monkeypatch.delenv("IC_BATCH_GRAPH")
+    b_grids, _ = make_boxes("fp32")
+    for g in b_grids:
+        g.step(5, w)
+    for ga, gb in zip(a_grids, b_grids):
+        for u, v in zip(snapshot(ga), snapshot(gb)):
+            assert np.array_equal(u, v)
+    for g in a_grids + b_grids:
+        g.close()
