@@ -23,7 +23,9 @@
 // of one cell; the in-plane neighbours come from shared memory and the z
 // neighbours from registers carried between planes.  Per plane: one load of
 // the next plane, one flux evaluation, and one fused combination with U^n.
-// State stores delta rho = rho - rho0.
+// State stores delta rho = rho - rho0.  Stage 1 draws W_A and W_B of each
+// cell (Philox), uses W_1 and stores W_2 and W_3 for stages 2 and 3 (storing
+// them costs less than drawing them three times).
 //
 // Schedule.  The (column, plane) pairs are numbered column by column and split
 // into gridDim.x equal contiguous ranges, one per CTA; a range that crosses a
