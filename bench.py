@@ -48,7 +48,8 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi SM clock and throttle reasons sampled during the timed region."""
+    """nvidia-smi SM clock and throttle reasons, sampled every 50 ms; only the
+    samples taken inside the timed window are summarised."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,7 +63,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -70,9 +71,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -80,9 +81,13 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        lines = self.lines
+        if window is not None:
+            inside = [x for x in lines if window[0] <= x[0] <= window[1]]
+            lines = inside if inside else lines
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         sm, mx, reasons = [], [], set()
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 6:
                 continue
@@ -96,8 +101,9 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
+        n_inside = 0 if window is None else sum(1 for x in self.lines if window[0] <= x[0] <= window[1])
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": n_inside}
 
 
 def setup_box(gp, parts, seed_thermal):
@@ -221,8 +227,9 @@ def run_ensemble(args):
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     time.sleep(0.3)
+    w0 = time.perf_counter()
     t_batch, wall_batch = timed(lambda: batch.step(1), args.steps)
-    clocks = sampler.stop()
+    clocks = sampler.stop((w0, time.perf_counter()))
     os.environ["IC_BATCH_GRAPH"] = "1"        # the whole ensemble step as one graph
     batch.step(args.warmup)
     t_one, wall_one = timed(lambda: batch.step(1), args.steps)
@@ -260,7 +267,7 @@ def run_ensemble(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
@@ -333,8 +340,9 @@ def main():
         with torch.cuda.stream(stream):
             ev[i][1].record(stream)
     barrier()
-    wall = time.perf_counter() - wall0
-    clocks = sampler.stop()
+    wall1 = time.perf_counter()
+    wall = wall1 - wall0
+    clocks = sampler.stop((wall0, wall1))
     grid.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = float(np.sum(step_ms)) / 1e3
