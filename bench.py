@@ -36,6 +36,12 @@ WORKLOAD = ("128^3 staggered grid FP32 state + FP64 accumulators, 1e4 free parti
 # algorithmic bytes of the stage-wise SSP-RK3 sweep per cell and step (FP32):
 # stage 1 reads U_s (4 words) and writes 4; stages 2-3 read U_s and U^n (8) and write 4
 ALG_BYTES_PER_CELL_STEP = {"fp32": 128, "fp64": 256}
+# The FP64 form is bound by GB300's FP64 units, not HBM: its roofline counts the
+# floating-point operations of the three stages as written (an FMA is 2; a
+# division, logarithm, square root, sine or cosine 1), 580 per cell and step,
+# against the nominal 1.25 TFLOP/s FP64 rate of the part (no measured figure).
+ALG_FP64_FLOPS_PER_CELL_STEP = 580
+FP64_PEAK_TFLOPS = 1.25
 
 
 def load_peaks():
@@ -410,6 +416,18 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
 
+    if args.precision == "fp32":
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "peak_kind": peak_kind, "traffic_unit": "bytes per launch",
+                    "alg_bytes_per_launch": alg_bytes / 3, "alg_bytes_per_step": alg_bytes}
+    else:
+        tflops = ALG_FP64_FLOPS_PER_CELL_STEP * cells / (stage_ms_per_step * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal (FP64 units)",
+                    "alg_flops_per_step": ALG_FP64_FLOPS_PER_CELL_STEP * cells,
+                    "hbm_frac_for_reference": achieved / peak}
+    roofline.update({"kernel": "k_rk3_stage (3 launches per step)", "stage_ms_per_step": stage_ms_per_step,
+                     "particle_ms_per_step": part_ms / args.steps, "end_ms_per_step": end_ms / args.steps})
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -421,12 +439,7 @@ def main():
                        "l2": "flushed between timed steps (512 MB write, outside the step events)",
                        "stage_tiling": list(tiling), "particle_steps_per_s": pvalue},
             "particle_steps_per_s": pvalue,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_rk3_stage (3 launches per step)", "traffic_unit": "bytes per launch",
-                         "alg_bytes_per_launch": alg_bytes / 3,
-                         "alg_bytes_per_step": alg_bytes, "stage_ms_per_step": stage_ms_per_step,
-                         "particle_ms_per_step": part_ms / args.steps, "end_ms_per_step": end_ms / args.steps},
+            "roofline": roofline,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,
             "e2e": e2e,
