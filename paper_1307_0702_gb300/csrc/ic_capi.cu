@@ -622,10 +622,11 @@ struct CkptHeader {
   double scalars[3];
 };
 
-size_t ckpt_size(const ic_ctx *ctx) {
-  const size_t r = ctx->real_size, n = size_t(ctx->ps.n);
+size_t ckpt_size_for(const ic_ctx *ctx, size_t n) {
+  const size_t r = ctx->real_size;
   return sizeof(CkptHeader) + 4 * size_t(ctx->cells) * r + n * (24 + 24 + 48) + n * r * (3 + 1 + 1 + 1 + 3 + 3);
 }
+size_t ckpt_size(const ic_ctx *ctx) { return ckpt_size_for(ctx, size_t(ctx->ps.n)); }
 }  // namespace
 
 ic_status ic_checkpoint(ic_ctx *ctx, void *buf, size_t *bytes) {
@@ -675,12 +676,17 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
     return fail(ctx, IC_ERR_ARG, "not a libic checkpoint");
   if (hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny || hd.nz != ctx->p.nz)
     return fail(ctx, IC_ERR_ARG, "checkpoint grid or precision differs from this context");
+  // checked before anything of the context changes: a rejected blob leaves it as it was
+  if (hd.np < 0 || bytes < ckpt_size_for(ctx, size_t(hd.np))) return fail(ctx, IC_ERR_ARG, "checkpoint truncated");
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int n_before = ctx->ps.n;
   ctx->ps.n = 0;
   ic_status st = grow_particles(ctx, hd.np);
-  if (st) return st;
+  if (st) {
+    ctx->ps.n = n_before;
+    return st;
+  }
   ctx->ps.n = hd.np;
-  if (bytes < ckpt_size(ctx)) return fail(ctx, IC_ERR_ARG, "checkpoint truncated");
   const char *in = static_cast<const char *>(buf) + sizeof(hd);
   ctx->cur = 0;
   const size_t r = ctx->real_size, fb = size_t(ctx->cells) * r, n = size_t(hd.np);
