@@ -133,3 +133,42 @@ def test_density_variance_converges_with_cfl_number():
     e1, e2 = abs(np.var(s1) / var - 1.0), abs(np.var(s2) / var - 1.0)
     assert e2 < 0.04
     assert e1 > 2.0 * e2, (e1, e2)
+
+
+def test_ensemble_averaged_force_in_a_thermal_bath():
+    """Thirty-two fluctuating boxes (Philox box ids 0..31) of the Table I
+    dipolar case and one deterministic box, advanced as one batch: thermal
+    noise scatters the per-box time-averaged forces, and their ensemble mean
+    (Sec. 6) agrees with the deterministic force within its statistical error;
+    the deterministic force is Gor'kov's within the dipolar tolerance above."""
+    from paper_1307_0702_gb300 import Batch, Grid
+
+    nsteps, skip, k_s, h = 24000, 8000, 1.0, 10.0
+    w = W.blackman_harris(nsteps, skip)
+    L = 32 * h
+    q = np.array([[L / 8, L / 2, L / 2], [7 * L / 8, L / 2, L / 2]])
+    grids = []
+    for b in range(33):
+        gp, _, _ = W.single_particle_config(n=32, k_spring=k_s, mirror=True, mass_ratio=2.0, kappa_ratio=1.0)
+        gp.update(h=h, dt=0.1 * h / gp["c"], zeta=1.0, precision="fp32", kT=1e-7 if b else 0.0, seed=77, box=b)
+        rho, g = W.velocity_phase_wave_fields(gp)
+        grid = Grid(gp)
+        grid.set_state(rho, g)
+        grid.add_particles(q, (2.0 - 1.0) * 8 * h ** 3, 1.0, k_s)
+        grids.append(grid)
+    with Batch(grids) as batch:
+        batch.step(nsteps, w)
+    forces, a2s = [], []
+    for grid in grids:
+        f, _, a2 = grid.time_average()
+        forces.append(-f[0, 0])
+        a2s.append(a2)
+        grid.close()
+    f_det, thermal = forces[0], np.array(forces[1:])
+    mean, sem = thermal.mean(), thermal.std(ddof=1) / np.sqrt(len(thermal))
+    assert np.std(thermal) > 0 and sem < 0.1 * abs(f_det)      # independent, resolvable fluctuations
+    assert abs(mean - f_det) < 4 * sem, (mean, f_det, sem)
+    k = 2 * np.pi / L
+    omega = theory.discrete_sound_frequency(4.0, h, 32)
+    fg = theory.gorkov_force(4.0, np.sqrt(2 * a2s[0]), 8 * h ** 3, k, 1.0, 1.0, 8 * h ** 3 - k_s / omega ** 2, L / 8)
+    assert 0.97 <= f_det / fg <= 1.07
