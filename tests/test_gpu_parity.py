@@ -121,3 +121,38 @@ def test_chunked_steps_equal_one_call():
     for k in ("u", "q", "lam", "f_avg", "lam_avg"):
         assert np.array_equal(a[k], b[k]), k
     assert a["a2"] == b["a2"]
+
+
+@pytest.mark.parametrize("case", range(10))
+def test_random_configurations(case):
+    """Seeded random cases over the whole parameter space: grid edges from the
+    minimum 6 up to 40 cells, both precisions, deterministic and thermal,
+    every drive and wave axis, 0-12 particles anywhere (overlapping, on the
+    periodic seam), tethered or free, any tiling; three steps against the
+    oracle."""
+    rng = np.random.default_rng(1000 + case)
+    shape = tuple(int(x) for x in rng.integers(6, 41, 3))
+    prec = ["fp64", "fp32"][case % 2]
+    forcing = ["none", "mode", "plane"][int(rng.integers(3))]
+    axis = int(rng.integers(3))
+    kT = [0.0, 1e-3][int(rng.integers(2))]
+    gp = W.grid_params(shape, kT=kT, wave_amp=float(rng.uniform(5e-4, 3e-3)), forcing=forcing, wave_axis=axis,
+                       plane_index=int(rng.integers((shape[axis]))), zeta=float(rng.uniform(0.0, 1.0)),
+                       seed=int(rng.integers(2 ** 62)), precision=prec, wave_phase=float(rng.uniform(0, 6.3)))
+    rho, g = W.random_fields(gp, seed=case)
+    npart = int(rng.integers(0, 13))
+    parts = None
+    if npart:
+        L = np.array(shape, dtype=float)
+        q = rng.uniform(0.0, 1.0, (npart, 3)) * L
+        if npart > 2:
+            q[1] = (q[0] + rng.uniform(-1.0, 1.0, 3)) % L     # overlapping kernels
+            q[2, 0] = L[0] - 0.05                              # on the periodic seam
+        parts = dict(q=q, m_e=rng.uniform(-2.0, 8.0, npart), kappa_ratio=rng.uniform(0.3, 2.0, npart),
+                     k_spring=np.where(rng.uniform(size=npart) < 0.5, rng.uniform(0.1, 1.0, npart), 0.0))
+    tile = ([32, 16][int(rng.integers(2))], int(rng.integers(8, 33)))
+    out = run_gpu(gp, rho, g, parts, nsteps=3, weights=np.ones(3), thermal_seed=7 if kT else None, tile=tile)
+    sim = run_oracle(gp, rho, g, parts, nsteps=3, weights=np.ones(3), thermal_seed=7 if kT else None)
+    errs = compare(out, sim, gp, q0=None if parts is None else parts["q"])
+    bad = {k: v for k, v in errs.items() if not v <= TOL[prec]}
+    assert not bad, (shape, prec, forcing, axis, kT, npart, tile, errs)
