@@ -236,6 +236,62 @@ ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset)
 ic_status ic_fluid_step_noalloc(const ic_grid_params *params, const void *const in[4], void *const out[4],
                                 int64_t step);
 
+/* ------------------------------------------------------------------------
+ * Adjoint of the deterministic step (kT = 0): reverse-mode gradients of
+ *
+ *   Phi = sum_n weight_n sum_p d_p . F_p^{n+1/2}
+ *
+ * (F = -k_s (q^{n+1/2} - q_eq) the tether force of App. A.2 substep 2 that
+ * Sec. 6 reads the acoustic force from; d_p a direction per particle) with
+ * respect to every particle's m_e and epsilon_pf, the drive amplitude A
+ * (ic_grid_params.wave_amp) and the state (delta rho, g, q, u) at the start
+ * of the reversed steps.  The reverse sweep is the transpose of substeps 7 to
+ * 1 of App. A.2 with J and S swapping roles (they are adjoint, Eq. (adj)).
+ *
+ * Use: ic_adjoint_enable once the particles are in place; then, for the steps
+ * n = N-1 down to 0: restore the state at the start of step n (for instance
+ * with ic_snapshot_load), ic_step_record (step n forward, keeping the tape),
+ * ic_adjoint_step(weight_n).  ic_adjoint_read returns the accumulated
+ * gradients and the adjoint of the state at the start of the last reversed
+ * step.  Gradients with respect to kappa_p/kappa_f follow from
+ * epsilon_pf = c^2 (kappa_f/kappa_p - 1): dPhi/d(kappa_p/kappa_f) =
+ * -c^2 / (kappa_p/kappa_f)^2 dPhi/d epsilon_pf.  The adjoint spreads with
+ * atomic adds: it is reproducible to rounding, not bit for bit.
+ *
+ * ic_adjoint_enable allocates the tape and adjoint fields (26 grid fields in
+ * the context's precision, 17 doubles per particle) and zeroes them; it
+ * returns IC_ERR_STATE if kT > 0, IC_ERR_OOM if allocation fails.  Adding
+ * particles afterwards makes the other calls return IC_ERR_STATE until it is
+ * called again. */
+ic_status ic_adjoint_enable(ic_ctx *ctx);
+/* Zeroes the adjoint state and the gradients and sets the directions d_p
+ * (n x 3 doubles, host; NULL: the x axis for every particle). */
+ic_status ic_adjoint_reset(ic_ctx *ctx, const double *direction);
+/* One forward step, as ic_step(ctx, 1, NULL), that keeps what the reverse
+ * sweep of that step needs (q^n, u^n, the first RK stage and the momenta
+ * before substep 6).  The time averages are not updated. */
+ic_status ic_step_record(ic_ctx *ctx);
+/* Reverses the step recorded last: the adjoint held by the context goes from
+ * the state after that step to the state before it, and the gradients gain
+ * the step's terms, weight * sum_p d_p . F_p included.  IC_ERR_STATE if no
+ * step is recorded or the state has moved on since. */
+ic_status ic_adjoint_step(ic_ctx *ctx, double weight);
+/* Reads (each pointer may be NULL): grad_m_e[n], grad_eps[n], *grad_A, the
+ * adjoint of delta rho and g (nx*ny*nz doubles each, [z][y][x]) and of q and u
+ * (n x 3).  Synchronises the stream. */
+ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, double *grad_A, double *rho_bar,
+                          double *gx_bar, double *gy_bar, double *gz_bar, double *q_bar, double *u_bar);
+
+/* Device snapshots of the state a rollout needs to restart a step (fields,
+ * q, u, step counter): the caller owns dev_buf, device memory of
+ * ic_snapshot_size bytes, 16-byte aligned (IC_ERR_ARG otherwise).  Save
+ * enqueues device copies on the context's stream; load restores them (and
+ * the step's drive) and returns IC_ERR_ARG if the snapshot is of another grid,
+ * precision or particle count.  The time averages are not part of it. */
+ic_status ic_snapshot_size(const ic_ctx *ctx, size_t *bytes);
+ic_status ic_snapshot_save(ic_ctx *ctx, void *dev_buf);
+ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf);
+
 const char *ic_last_error(const ic_ctx *ctx);
 void ic_destroy(ic_ctx *ctx);
 

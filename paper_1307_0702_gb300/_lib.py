@@ -60,6 +60,14 @@ SIGNATURES = {
     "ic_profile": (c_int, [c_void_p, c_int]),
     "ic_profile_read": (c_int, [c_void_p, PD, POINTER(c_int64), c_int]),
     "ic_fluid_step_noalloc": (c_int, [POINTER(GridParams), POINTER(c_void_p), POINTER(c_void_p), c_int64]),
+    "ic_adjoint_enable": (c_int, [c_void_p]),
+    "ic_adjoint_reset": (c_int, [c_void_p, PD]),
+    "ic_step_record": (c_int, [c_void_p]),
+    "ic_adjoint_step": (c_int, [c_void_p, c_double]),
+    "ic_adjoint_read": (c_int, [c_void_p, PD, PD, PD, PD, PD, PD, PD, PD, PD]),
+    "ic_snapshot_size": (c_int, [c_void_p, POINTER(c_size_t)]),
+    "ic_snapshot_save": (c_int, [c_void_p, c_void_p]),
+    "ic_snapshot_load": (c_int, [c_void_p, c_void_p]),
     "ic_last_error": (c_char_p, [c_void_p]),
     "ic_destroy": (None, [c_void_p]),
 }

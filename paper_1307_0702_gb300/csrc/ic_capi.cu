@@ -110,12 +110,21 @@ cudaError_t timed_launch(ic_ctx *ctx, int cls, F &&fn) {
 }
 
 // Enqueue one full time step with U^n in buffer `cur`; U^{n+1} lands in 1 - cur.
-cudaError_t enqueue_step(ic_ctx *ctx, int cur) {
+// With `record`, the intermediates the adjoint needs and the step overwrites
+// (q^n, u^n, U_1 and the momenta g~ before substep 6) are copied to the tape.
+cudaError_t enqueue_step(ic_ctx *ctx, int cur, bool record = false) {
   void *const *U0 = ctx->U[cur];
   void *const *U1 = ctx->U[1 - cur];
   void *const *U2 = ctx->U[2];
   const bool parts = ctx->ps.n > 0;
+  const size_t fb = size_t(ctx->cells) * ctx->real_size;
   cudaError_t e;
+  auto tape = [&](void *const *dst, void *const *src, int n) {
+    cudaError_t te = cudaSuccess;
+    for (int j = 0; j < n && te == cudaSuccess; ++j)
+      te = cudaMemcpyAsync(dst[j], src[j], fb, cudaMemcpyDeviceToDevice, ctx->stream);
+    return te;
+  };
   auto fluid = [&](int stage, void *const *s, void *const *n, void *const *o) {
     return timed_launch(ctx, 0, [&] { return ic::launch_stage(ctx, stage, s, n, o); });
   };
@@ -127,17 +136,24 @@ cudaError_t enqueue_step(ic_ctx *ctx, int cur) {
     if ((e = (x)) != cudaSuccess) return e; \
   } while (0)
   const bool springs = parts && ctx->any_spring;
+  if (record && parts) {
+    const size_t n = size_t(ctx->ps.n);
+    IC_TRY(cudaMemcpyAsync(ctx->adj.tq, ctx->ps.q, 24 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    IC_TRY(cudaMemcpyAsync(ctx->adj.tu, ctx->ps.u, 3 * ctx->real_size * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
   if (parts) IC_TRY(part(ic::kHalfStep, 0, U0));
   if (parts) IC_TRY(part(ic::kPressure, 0, U0));
   IC_TRY(fluid(0, U0, U0, U1));
   if (springs) IC_TRY(part(ic::kForce, 0, U1));
+  if (record) IC_TRY(tape(ctx->adj.tU1, U1, 4));
   if (parts) IC_TRY(part(ic::kPressure, 1, U1));
   IC_TRY(fluid(1, U1, U0, U2));
   if (springs) IC_TRY(part(ic::kForce, 1, U2));
   if (parts) IC_TRY(part(ic::kPressure, 2, U2));
   IC_TRY(fluid(2, U2, U0, U1));
+  if (springs) IC_TRY(part(ic::kForce, 2, U1));
+  if (record) IC_TRY(tape(ctx->adj.tG3, U1 + 1, 3));
   if (parts) {
-    if (springs) IC_TRY(part(ic::kForce, 2, U1));
     IC_TRY(part(ic::kImpulse, 0, U1));
     IC_TRY(part(ic::kSpread, 0, U1));
     IC_TRY(part(ic::kFinal, 0, U1));
@@ -728,6 +744,214 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- adjoint
+namespace {
+
+ic_status adjoint_zero(ic_ctx *ctx, const double *direction) {
+  ic::AdjointStore &A = ctx->adj;
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(A.np);
+  for (int j = 0; j < 4; ++j) IC_CUDA(ctx, cudaMemsetAsync(A.bar[j], 0, fb, ctx->stream));
+  IC_CUDA(ctx, cudaMemsetAsync(A.part_block, 0, (17 * n + 1) * sizeof(double), ctx->stream));
+  std::vector<double> dir(3 * n, 0.0);
+  for (size_t i = 0; i < n; ++i) {
+    if (direction)
+      for (int a = 0; a < 3; ++a) dir[3 * i + a] = direction[3 * i + a];
+    else
+      dir[3 * i] = 1.0;
+  }
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (n) IC_CUDA(ctx, cudaMemcpy(A.dir, dir.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice));
+  A.rec_cur = -1;
+  return IC_OK;
+}
+
+ic_status adjoint_ready(ic_ctx *ctx) {
+  if (!ctx->adj.on) return fail(ctx, IC_ERR_STATE, "ic_adjoint_enable has not been called");
+  if (ctx->adj.np != ctx->ps.n)
+    return fail(ctx, IC_ERR_STATE, "particles were added after ic_adjoint_enable; enable it again");
+  return IC_OK;
+}
+
+constexpr uint64_t kSnapMagic = 0x31504e53434943ull;   // "ICSNP1"
+
+struct SnapHeader {
+  uint64_t magic;
+  int64_t step;
+  int32_t np, precision, nx, ny, nz, pad;
+  uint64_t pad2[3];
+};
+static_assert(sizeof(SnapHeader) == 64, "snapshot header is 64 bytes");
+
+size_t snapshot_bytes(const ic_ctx *ctx) {
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n);
+  return sizeof(SnapHeader) + 4 * ((fb + 15) / 16 * 16) + (24 * n + 15) / 16 * 16 + 3 * ctx->real_size * n;
+}
+
+}  // namespace
+
+extern "C" {
+
+ic_status ic_adjoint_enable(ic_ctx *ctx) {
+  if (!ctx) return IC_ERR_ARG;
+  if (ctx->p.kT != 0.0) return fail(ctx, IC_ERR_STATE, "the adjoint covers the deterministic step (kT = 0)");
+  ic::AdjointStore &A = ctx->adj;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dev_free(ctx, A.grid_block);
+  dev_free(ctx, A.part_block);
+  A = ic::AdjointStore{};
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n);
+  const size_t fstride = (fb + 255) / 256 * 256;
+  constexpr int kFields = 26;
+  const size_t tape_q = (24 * n + 255) / 256 * 256;
+  char *g = static_cast<char *>(dev_alloc(ctx, kFields * fstride + tape_q + 3 * ctx->real_size * n));
+  double *pd = static_cast<double *>(dev_alloc(ctx, (17 * n + 1) * sizeof(double)));
+  if (!g || !pd) {
+    dev_free(ctx, g);
+    dev_free(ctx, pd);
+    return fail(ctx, IC_ERR_OOM, "adjoint buffers");
+  }
+  IC_CUDA(ctx, cudaMemsetAsync(g, 0, kFields * fstride, ctx->stream));
+  A.grid_block = g;
+  A.part_block = pd;
+  void **slots[kFields] = {&A.tU1[0], &A.tU1[1], &A.tU1[2], &A.tU1[3], &A.tG3[0], &A.tG3[1], &A.tG3[2],
+                           &A.bar[0], &A.bar[1], &A.bar[2], &A.bar[3], &A.acc[0], &A.acc[1], &A.acc[2],
+                           &A.acc[3], &A.vbar[0], &A.vbar[1], &A.vbar[2], &A.gpart[0], &A.gpart[1],
+                           &A.gpart[2], &A.rfbar[0], &A.rfbar[1], &A.rfbar[2], &A.pibar, &A.rhox};
+  for (int k = 0; k < kFields; ++k) *slots[k] = g + k * fstride;
+  A.tq = g + kFields * fstride;
+  A.tu = g + kFields * fstride + tape_q;
+  double **ps[8] = {&A.qbar, &A.ubar, &A.qhbar, &A.fbar, &A.jvnh, &A.dir, &A.gme, &A.geps};
+  const size_t len[8] = {3 * n, 3 * n, 3 * n, 3 * n, 3 * n, 3 * n, n, n};
+  size_t off = 0;
+  for (int k = 0; k < 8; ++k) {
+    *ps[k] = pd + off;
+    off += len[k];
+  }
+  A.gA = pd + off;
+  A.np = int(n);
+  A.on = true;
+  return adjoint_zero(ctx, nullptr);
+}
+
+ic_status ic_adjoint_reset(ic_ctx *ctx, const double *direction) {
+  if (!ctx) return IC_ERR_ARG;
+  const ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  return adjoint_zero(ctx, direction);
+}
+
+ic_status ic_step_record(ic_ctx *ctx) {
+  if (!ctx) return IC_ERR_ARG;
+  ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  st = upload_weights(ctx, 1, nullptr);
+  if (st) return st;
+  const int cur = ctx->cur;
+  IC_CUDA(ctx, enqueue_step(ctx, cur, true));
+  ctx->adj.rec_cur = cur;
+  ctx->adj.rec_step = ctx->host_step;
+  ctx->cur = 1 - cur;
+  ctx->host_step += 1;
+  return IC_OK;
+}
+
+ic_status ic_adjoint_step(ic_ctx *ctx, double weight) {
+  if (!ctx) return IC_ERR_ARG;
+  const ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  if (ctx->adj.rec_cur < 0) return fail(ctx, IC_ERR_STATE, "no recorded step to reverse (call ic_step_record)");
+  if (ctx->adj.rec_cur != 1 - ctx->cur)
+    return fail(ctx, IC_ERR_STATE, "the state moved on after ic_step_record; record the step again");
+  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, weight));
+  ctx->adj.rec_cur = -1;
+  return IC_OK;
+}
+
+ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, double *grad_A, double *rho_bar,
+                          double *gx_bar, double *gy_bar, double *gz_bar, double *q_bar, double *u_bar) {
+  if (!ctx) return IC_ERR_ARG;
+  ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  const ic::AdjointStore &A = ctx->adj;
+  const size_t n = size_t(A.np);
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double *fields[4] = {rho_bar, gx_bar, gy_bar, gz_bar};
+  for (int j = 0; j < 4; ++j)
+    if (fields[j]) {
+      st = download_real(ctx, fields[j], A.bar[j], 0.0, size_t(ctx->cells));
+      if (st) return st;
+    }
+  if (grad_m_e && n) IC_CUDA(ctx, cudaMemcpy(grad_m_e, A.gme, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (grad_eps && n) IC_CUDA(ctx, cudaMemcpy(grad_eps, A.geps, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (grad_A) IC_CUDA(ctx, cudaMemcpy(grad_A, A.gA, sizeof(double), cudaMemcpyDeviceToHost));
+  if (q_bar && n) IC_CUDA(ctx, cudaMemcpy(q_bar, A.qbar, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (u_bar && n) IC_CUDA(ctx, cudaMemcpy(u_bar, A.ubar, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  return check_device_status(ctx);
+}
+
+ic_status ic_snapshot_size(const ic_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return IC_ERR_ARG;
+  *bytes = snapshot_bytes(ctx);
+  return IC_OK;
+}
+
+ic_status ic_snapshot_save(ic_ctx *ctx, void *dev_buf) {
+  if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, fs = (fb + 15) / 16 * 16, n = size_t(ctx->ps.n);
+  SnapHeader hd{};
+  hd.magic = kSnapMagic;
+  hd.step = ctx->host_step;
+  hd.np = ctx->ps.n;
+  hd.precision = ctx->p.precision;
+  hd.nx = ctx->p.nx;
+  hd.ny = ctx->p.ny;
+  hd.nz = ctx->p.nz;
+  char *out = static_cast<char *>(dev_buf);
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  IC_CUDA(ctx, cudaMemcpy(out, &hd, sizeof(hd), cudaMemcpyHostToDevice));
+  out += sizeof(hd);
+  for (int j = 0; j < 4; ++j, out += fs)
+    IC_CUDA(ctx, cudaMemcpyAsync(out, ctx->U[ctx->cur][j], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (n) {
+    IC_CUDA(ctx, cudaMemcpyAsync(out, ctx->ps.q, 24 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    out += (24 * n + 15) / 16 * 16;
+    IC_CUDA(ctx, cudaMemcpyAsync(out, ctx->ps.u, 3 * ctx->real_size * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return IC_OK;
+}
+
+ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf) {
+  if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
+  SnapHeader hd{};
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  IC_CUDA(ctx, cudaMemcpy(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost));
+  if (hd.magic != kSnapMagic || hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny ||
+      hd.nz != ctx->p.nz || hd.np != ctx->ps.n)
+    return fail(ctx, IC_ERR_ARG, "not a snapshot of this context's grid and particles");
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, fs = (fb + 15) / 16 * 16, n = size_t(ctx->ps.n);
+  const char *in = static_cast<const char *>(dev_buf) + sizeof(hd);
+  for (int j = 0; j < 4; ++j, in += fs)
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->U[ctx->cur][j], in, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (n) {
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->ps.q, in, 24 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->ps.q_build, in, 24 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    in += (24 * n + 15) / 16 * 16;
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->ps.u, in, 3 * ctx->real_size * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->host_step = hd.step;
+  ctx->host_wcount = 0;
+  const int64_t steps[3] = {hd.step, hd.step, 0};
+  IC_CUDA(ctx, cudaMemcpy(ctx->d.step, steps, sizeof(steps), cudaMemcpyHostToDevice));
+  const int one = 1;
+  IC_CUDA(ctx, cudaMemcpy(ctx->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice));
+  ctx->adj.rec_cur = -1;
+  return upload_drive(ctx, hd.step);
+}
+
+}  // extern "C"
+
 
 struct ic_batch {
   std::vector<ic_ctx *> ctxs;

@@ -58,6 +58,24 @@ struct Device {
   double *partials = nullptr;     // per-CTA partial sums
 };
 
+// Adjoint of the deterministic step: the tape of the last recorded step and
+// the adjoint fields (allocated by ic_adjoint_enable).
+struct AdjointStore {
+  bool on = false;
+  int np = 0;                          // particles when enabled
+  void *tU1[4] = {}, *tG3[3] = {};     // tape: U_1 and g~ (the momenta before substep 6)
+  void *tq = nullptr, *tu = nullptr;   // tape: q^n (8 bytes per component) and u^n
+  int rec_cur = -1;                    // buffer of U^n of the recorded step (-1: none to reverse)
+  int64_t rec_step = 0;
+  // grid adjoint fields in the context's precision
+  void *bar[4] = {}, *acc[4] = {}, *vbar[3] = {}, *gpart[3] = {}, *rfbar[3] = {};
+  void *pibar = nullptr, *rhox = nullptr;
+  // particle adjoints and gradients (FP64)
+  double *qbar = nullptr, *ubar = nullptr, *qhbar = nullptr, *fbar = nullptr, *jvnh = nullptr;
+  double *gme = nullptr, *geps = nullptr, *gA = nullptr, *dir = nullptr;
+  void *grid_block = nullptr, *part_block = nullptr;
+};
+
 }  // namespace ic
 
 struct ic_ctx {
@@ -70,6 +88,7 @@ struct ic_ctx {
   int cur = 0;             // buffer holding U^n (0 or 1); buffer 2 holds U^{n+1/2}
   ic::Device d{};
   ic::ParticleStore ps{};
+  ic::AdjointStore adj{};
   void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
   void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
   bool any_spring = false;  // some particle is tethered: the stage force source is launched
@@ -135,6 +154,9 @@ cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *
                              void *const tgt[4]);
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]);
 cudaError_t launch_particle_momentum(ic_ctx *ctx, double *dev_out3);
+
+// adjoint (ic_adjoint.cu): reverse sweep of the recorded step
+cudaError_t launch_adjoint_step(ic_ctx *ctx, double weight);
 void positions_to_device(const ic_ctx *ctx, const double *q, size_t n3, void *out);
 void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q);
 }  // namespace ic

@@ -179,6 +179,54 @@ class Grid:
         self._check(self._lib.ic_restore(self._ctx, buf, len(blob)))
         self.n_particles = int(np.frombuffer(blob[28:32], dtype=np.int32)[0])
 
+    # ---------------------------------------------------------------- adjoint
+    def adjoint_enable(self):
+        """Allocate the tape and adjoint fields (deterministic boxes only)."""
+        self._check(self._lib.ic_adjoint_enable(self._ctx))
+
+    def adjoint_reset(self, direction=None):
+        """Zero the adjoint and gradients; direction (n, 3) of the objective (default x)."""
+        d = None if direction is None else _f64(direction).reshape(self.n_particles, 3)
+        self._check(self._lib.ic_adjoint_reset(self._ctx, _ptr(d)))
+
+    def step_record(self):
+        """One step forward that keeps the tape of its reverse sweep."""
+        self._check(self._lib.ic_step_record(self._ctx))
+
+    def adjoint_step(self, weight):
+        """Reverse the recorded step, adding weight * sum_p d_p . F_p to the objective."""
+        self._check(self._lib.ic_adjoint_step(self._ctx, float(weight)))
+
+    def adjoint_read(self):
+        """Gradients and state adjoints: dict m_e, eps (n,), A, rho, g (3 fields), q, u (n, 3)."""
+        n = self.n_particles
+        me, eps, A = np.empty(n), np.empty(n), np.empty(1)
+        rho = np.empty(self.shape)
+        g = [np.empty(self.shape) for _ in range(3)]
+        q, u = np.empty((n, 3)), np.empty((n, 3))
+        self._check(self._lib.ic_adjoint_read(self._ctx, _ptr(me), _ptr(eps), _ptr(A), _ptr(rho), _ptr(g[0]),
+                                              _ptr(g[1]), _ptr(g[2]), _ptr(q), _ptr(u)))
+        return dict(m_e=me, eps=eps, A=float(A[0]), rho=rho, g=g, q=q, u=u)
+
+    def snapshot_size(self):
+        size = ctypes.c_size_t()
+        self._check(self._lib.ic_snapshot_size(self._ctx, ctypes.byref(size)))
+        return size.value
+
+    def new_snapshot(self):
+        """A device buffer (torch uint8 tensor) for one snapshot of this box."""
+        import torch
+
+        return torch.empty(self.snapshot_size(), dtype=torch.uint8, device=self.device)
+
+    def snapshot_save(self, buf):
+        """Enqueue a device copy of the state (fields, q, u, step) into buf."""
+        self._check(self._lib.ic_snapshot_save(self._ctx, ctypes.c_void_p(buf.data_ptr())))
+
+    def snapshot_load(self, buf):
+        """Restore a state saved by snapshot_save."""
+        self._check(self._lib.ic_snapshot_load(self._ctx, ctypes.c_void_p(buf.data_ptr())))
+
     def set_tile(self, tile_x, zchunk):
         """Stage-kernel tiling (tile_x 32 or 16, zchunk >= 8 planes); results are unchanged."""
         self._check(self._lib.ic_set_tile(self._ctx, int(tile_x), int(zchunk)))

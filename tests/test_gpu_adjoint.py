@@ -1,0 +1,215 @@
+"""GPU adjoint of the deterministic IC step (through the C ABI) against the
+oracle's FP64 adjoint and against central finite differences of the GPU's own
+forward rollout.
+
+Objective: Phi = sum_p d_p . <F_p>_w, the weighted time average of the tether
+forces (Sec. 6).  Gradients with respect to m_e, kappa_p/kappa_f, the drive
+amplitude A and the initial state.  FP64 agrees with the oracle to 1e-9
+normwise (the adjoint spreads with atomic adds, so its rounding order is not
+the oracle's); FP32 to 2e-3; finite differences (step 1e-6) to 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle import ic as oic
+from paper_1307_0702_gb300 import workloads as W
+from pairs import oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 2e-3}
+
+
+def case(prec, shape=(12, 10, 9), forcing="mode", nsteps=10, seed=3, amp=2e-3, u_amp=1e-3, wave_amp=3e-3):
+    gp = W.grid_params(shape, kT=0.0, wave_amp=wave_amp, forcing=forcing, zeta=0.3, precision=prec, plane_index=2,
+                       wave_phase=0.4)
+    rng = np.random.default_rng(seed)
+    L = np.array(shape, dtype=float)
+    q = rng.uniform(0.1, 0.9, (4, 3)) * L
+    q[1] = (q[0] + np.array([1.2, -0.7, 0.5])) % L         # overlapping kernels
+    q[2, 0] = L[0] - 0.3                                   # near the periodic seam
+    parts = dict(q=q, m_e=rng.uniform(0.5, 6.0, 4), kappa_ratio=rng.uniform(0.3, 1.5, 4),
+                 k_spring=rng.uniform(0.2, 0.8, 4), u=u_amp * rng.normal(size=(4, 3)))
+    rho, g = W.random_fields(gp, seed=seed, amp_rho=amp, amp_g=amp)
+    weights = np.linspace(0.5, 1.5, nsteps)
+    direction = rng.normal(size=(4, 3))
+    return gp, rho, g, parts, weights, direction
+
+
+def gpu_gradient(gp, rho, g, parts, weights, direction, K):
+    from paper_1307_0702_gb300 import Grid
+    from paper_1307_0702_gb300.adjoint import Rollout
+
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
+        roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K)
+        phi = roll.forward(weights, direction)
+        return phi, roll.backward()
+
+
+def oracle_gradient(gp, rho, g, parts, weights, direction, K=None):
+    p = oracle_params(gp)
+    op = oadj.make_parts(parts["q"], parts["u"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], p.c)
+    drho = np.asarray(rho, dtype=np.float64) - p.rho0
+    return oadj.rollout_gradient(p, drho, g, op, weights, direction, checkpoint_every=K)
+
+
+def compare(gr, orc):
+    errs = {k: rel_err(gr[k], orc[k]) for k in ("m_e", "kappa_ratio", "eps")}
+    errs["A"] = abs(gr["A"] - orc["A"]) / abs(orc["A"])
+    st = orc["state"]
+    errs["rho"] = rel_err(gr["rho"], st["drho"])
+    for a in range(3):
+        errs[f"g{a}"] = rel_err(gr["g"][a], st["g"][a])
+    errs["q"] = rel_err(gr["q"], st["q"])
+    errs["u"] = rel_err(gr["u"], st["u"])
+    return errs
+
+
+@pytest.mark.parametrize("prec,forcing", [("fp64", "mode"), ("fp64", "plane"), ("fp32", "mode")])
+def test_rollout_gradient_matches_the_oracle_adjoint(prec, forcing):
+    gp, rho, g, parts, weights, direction = case(prec, forcing=forcing)
+    phi, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=4)
+    ophi, orc = oracle_gradient(gp, rho, g, parts, weights, direction)
+    assert abs(phi - ophi) <= (1e-11 if prec == "fp64" else 1e-4) * abs(ophi)
+    errs = compare(gr, orc)
+    bad = {k: v for k, v in errs.items() if not v <= TOL[prec]}
+    assert not bad, errs
+
+
+def test_checkpoint_interval_changes_the_gradient_only_by_rounding():
+    gp, rho, g, parts, weights, direction = case("fp64", nsteps=9)
+    ref = gpu_gradient(gp, rho, g, parts, weights, direction, K=9)[1]
+    for K in (1, 4):
+        got = gpu_gradient(gp, rho, g, parts, weights, direction, K=K)[1]
+        for k in ("m_e", "kappa_ratio"):
+            assert rel_err(got[k], ref[k]) < 1e-12
+        assert abs(got["A"] - ref["A"]) < 1e-12 * abs(ref["A"])
+        assert rel_err(got["rho"], ref["rho"]) < 1e-12
+
+
+def gpu_phi(gp, rho, g, parts, weights, direction):
+    from paper_1307_0702_gb300 import Grid
+
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
+        grid.step(len(weights), weights)
+        f_avg = grid.time_average()[0]
+    return float(np.sum(direction * f_avg))
+
+
+def test_gpu_gradient_against_central_differences_of_the_gpu_forward():
+    """Central differences of the GPU forward, step 1e-6: the gradient of each
+    parameter family (m_e and kappa_p/kappa_f of all particles) within 1e-5
+    of them normwise.  The rounding of Phi (~1e-13 relative after 64 FP64
+    steps) divided by the step leaves ~2e-9 of noise in each difference, so
+    a small component of a family is only resolved relative to the family's
+    largest; step 1e-4 (truncation ~1e-8) checks every component to 1e-6."""
+    gp, rho, g, parts, weights, direction = case("fp64", nsteps=64, amp=3e-2, u_amp=2e-2, wave_amp=5e-2)
+    phi, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=5)
+
+    def fd(key, j, e):
+        pp = {k: np.array(v, copy=True) for k, v in parts.items()}
+        pm = {k: np.array(v, copy=True) for k, v in parts.items()}
+        pp[key][j] += e
+        pm[key][j] -= e
+        return (gpu_phi(gp, rho, g, pp, weights, direction) - gpu_phi(gp, rho, g, pm, weights, direction)) / (2 * e)
+
+    for key in ("m_e", "kappa_ratio"):
+        d6 = np.array([fd(key, j, 1e-6) for j in range(4)])
+        assert np.max(np.abs(gr[key] - d6)) <= 1e-5 * np.max(np.abs(d6)), (key, gr[key], d6)
+        d4 = np.array([fd(key, j, 1e-4) for j in range(4)])
+        assert np.allclose(gr[key], d4, rtol=1e-6, atol=0), (key, gr[key], d4)
+    # the drive amplitude (initial state held fixed)
+    e = 1e-6
+    fa = (gpu_phi({**gp, "wave_amp": gp["wave_amp"] * (1 + e)}, rho, g, parts, weights, direction) -
+          gpu_phi({**gp, "wave_amp": gp["wave_amp"] * (1 - e)}, rho, g, parts, weights, direction)) / (
+              2 * e * gp["wave_amp"])
+    assert gr["A"] == pytest.approx(fa, rel=1e-5)
+
+
+def test_autograd_function_with_the_standing_wave_start():
+    """torch.autograd through time_averaged_force: the initial density
+    rho0 + A cos(k x) is built in torch, so dPhi/dA collects the drive and the
+    initial state; checked against central differences of the GPU forward."""
+    import torch
+
+    from paper_1307_0702_gb300.adjoint import time_averaged_force
+
+    gp = W.grid_params((16, 8, 8), kT=0.0, wave_amp=5e-2, forcing="mode", precision="fp64")
+    n = 3
+    q = np.array([[2.0, 4.0, 4.0], [6.5, 4.2, 3.9], [12.0, 3.5, 4.5]])
+    weights = np.ones(64)
+    k = 2 * np.pi / 16.0
+    cosk = torch.as_tensor(np.cos(k * np.arange(16.0)), dtype=torch.float64).reshape(1, 1, 16)
+
+    def phi(m_e, kappa, A):
+        rho = 1.0 + A * cosk.expand(8, 8, 16)
+        return time_averaged_force(gp, q, m_e, kappa, np.full(n, 1.0), A, rho, weights=weights, checkpoint_every=7)
+
+    m_e = torch.tensor([4.0, 1.0, 2.5], dtype=torch.float64, requires_grad=True)
+    kappa = torch.tensor([0.5, 0.8, 1.3], dtype=torch.float64, requires_grad=True)
+    A = torch.tensor(5e-2, dtype=torch.float64, requires_grad=True)
+    out = phi(m_e, kappa, A)
+    dm, dk, dA = torch.autograd.grad(out, (m_e, kappa, A))
+    e = 1e-6
+    with torch.no_grad():
+        fd_A = (phi(m_e, kappa, A * (1 + e)) - phi(m_e, kappa, A * (1 - e))) / (2 * e * A)
+        d = torch.tensor([e, 0.0, 0.0], dtype=torch.float64)
+        fd_m = (phi(m_e + d, kappa, A) - phi(m_e - d, kappa, A)) / (2 * e)
+        fd_k = (phi(m_e, kappa + d, A) - phi(m_e, kappa - d, A)) / (2 * e)
+    assert float(dA) == pytest.approx(float(fd_A), rel=1e-5)
+    assert float(dm[0]) == pytest.approx(float(fd_m), rel=1e-5)
+    assert float(dk[0]) == pytest.approx(float(fd_k), rel=1e-5)
+
+
+def test_adjoint_calls_are_refused_in_the_wrong_state():
+    from paper_1307_0702_gb300 import Grid, ICError
+
+    gp = W.grid_params(8, kT=1e-3, precision="fp64")
+    with Grid(gp) as grid:
+        with pytest.raises(ICError):
+            grid.adjoint_enable()            # thermal box
+    gp = W.grid_params(8, kT=0.0, precision="fp64")
+    with Grid(gp) as grid:
+        grid.add_particles([[2.0, 3.0, 4.0]], 1.0, 0.5, 0.3)
+        with pytest.raises(ICError):
+            grid.step_record()               # not enabled
+        grid.adjoint_enable()
+        with pytest.raises(ICError):
+            grid.adjoint_step(1.0)           # nothing recorded
+        grid.step_record()
+        grid.step(1)
+        with pytest.raises(ICError):
+            grid.adjoint_step(1.0)           # the state moved on
+        grid.add_particles([[5.0, 5.0, 5.0]], 1.0, 0.5, 0.3)
+        with pytest.raises(ICError):
+            grid.step_record()               # particles added after enabling
+        snap = grid.new_snapshot()
+        grid.snapshot_save(snap)
+        with Grid(W.grid_params(9, kT=0.0, precision="fp64")) as other:
+            with pytest.raises(ICError):
+                other.snapshot_load(snap)    # another grid
+
+
+def test_snapshot_round_trip_reproduces_the_steps():
+    from paper_1307_0702_gb300 import Grid
+
+    gp, rho, g, parts, weights, direction = case("fp32", nsteps=4)
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
+        grid.step(3)
+        snap = grid.new_snapshot()
+        grid.snapshot_save(snap)
+        grid.step(5)
+        a = grid.get_state(), grid.forces()
+        grid.snapshot_load(snap)
+        assert grid.stats()[2] == 3
+        grid.step(5)
+        b = grid.get_state(), grid.forces()
+    assert np.array_equal(a[0][0], b[0][0]) and all(np.array_equal(a[0][1][i], b[0][1][i]) for i in range(3))
+    assert all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
