@@ -259,7 +259,7 @@ ic_status ic_fluid_step_noalloc(const ic_grid_params *params, const void *const 
  * atomic adds: it is reproducible to rounding, not bit for bit.
  *
  * ic_adjoint_enable allocates the tape and adjoint fields (26 grid fields in
- * the context's precision, 17 doubles per particle) and zeroes them; it
+ * the context's precision, 20 doubles per particle) and zeroes them; it
  * returns IC_ERR_STATE if kT > 0, IC_ERR_OOM if allocation fails.  Adding
  * particles afterwards makes the other calls return IC_ERR_STATE until it is
  * called again. */

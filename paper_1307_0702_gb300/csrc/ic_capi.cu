@@ -748,11 +748,16 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
 // ------------------------------------------------------------- adjoint
 namespace {
 
+// FP64 words per particle of the adjoint's particle block: qbar, ubar, qhbar,
+// fbar, jvnh and the objective direction (3 each), the m_e and epsilon
+// gradients (1 each); one word more holds the amplitude gradient.
+constexpr size_t kAdjWordsPerParticle = 6 * 3 + 2;
+
 ic_status adjoint_zero(ic_ctx *ctx, const double *direction) {
   ic::AdjointStore &A = ctx->adj;
   const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(A.np);
   for (int j = 0; j < 4; ++j) IC_CUDA(ctx, cudaMemsetAsync(A.bar[j], 0, fb, ctx->stream));
-  IC_CUDA(ctx, cudaMemsetAsync(A.part_block, 0, (17 * n + 1) * sizeof(double), ctx->stream));
+  IC_CUDA(ctx, cudaMemsetAsync(A.part_block, 0, (kAdjWordsPerParticle * n + 1) * sizeof(double), ctx->stream));
   std::vector<double> dir(3 * n, 0.0);
   for (size_t i = 0; i < n; ++i) {
     if (direction)
@@ -805,7 +810,7 @@ ic_status ic_adjoint_enable(ic_ctx *ctx) {
   constexpr int kFields = 26;
   const size_t tape_q = (24 * n + 255) / 256 * 256;
   char *g = static_cast<char *>(dev_alloc(ctx, kFields * fstride + tape_q + 3 * ctx->real_size * n));
-  double *pd = static_cast<double *>(dev_alloc(ctx, (17 * n + 1) * sizeof(double)));
+  double *pd = static_cast<double *>(dev_alloc(ctx, (kAdjWordsPerParticle * n + 1) * sizeof(double)));
   if (!g || !pd) {
     dev_free(ctx, g);
     dev_free(ctx, pd);
@@ -829,6 +834,7 @@ ic_status ic_adjoint_enable(ic_ctx *ctx) {
     off += len[k];
   }
   A.gA = pd + off;
+  if (off != kAdjWordsPerParticle * n) return fail(ctx, IC_ERR_STATE, "adjoint particle block layout");
   A.np = int(n);
   A.on = true;
   return adjoint_zero(ctx, nullptr);

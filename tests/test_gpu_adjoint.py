@@ -213,3 +213,90 @@ def test_snapshot_round_trip_reproduces_the_steps():
         b = grid.get_state(), grid.forces()
     assert np.array_equal(a[0][0], b[0][0]) and all(np.array_equal(a[0][1][i], b[0][1][i]) for i in range(3))
     assert all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
+
+
+# ---------------------------------------------------------------- the 64^3 rollout
+def line_case(prec, A=1e-3, nsteps=1000, offset=0.0):
+    """64^3, 16 particles evenly spaced on a line along x at y = z = L/2 (every
+    4 cells from x = 2; all three coordinates shifted by `offset`), contrasts
+    m_e = 4 and kappa_p/kappa_f = 0.5, tethers k = 1; the standing-wave
+    eigenmode rho0 + A cos(k x) as start and the mode drive; 1000 steps of
+    unit weight."""
+    gp = W.grid_params(64, kT=0.0, wave_amp=A, forcing="mode", precision=prec)
+    rho, g = W.standing_wave_fields(gp)
+    q = np.stack([2.0 + 4.0 * np.arange(16), np.full(16, 32.0), np.full(16, 32.0)], axis=1) + offset
+    parts = dict(q=q, m_e=np.full(16, 4.0), kappa_ratio=np.full(16, 0.5), k_spring=np.full(16, 1.0),
+                 u=np.zeros((16, 3)))
+    return gp, rho, g, parts, np.ones(nsteps)
+
+
+def test_line_of_particles_amplitude_homogeneity():
+    """With 16 particles spaced evenly over one wavelength, the objective
+    Phi = sum_p sin(2 k x_p) <F_x,p> is even in A: A -> -A is the shift by
+    half a wavelength, which maps the line onto itself and leaves every
+    sin(2 k x_p) unchanged.  So Phi = a_2 A^2 + a_4 A^4 + ..., the radiation
+    force being quadratic in the amplitude at leading order
+    (Eq. (eq:acousticForce2)), and the adjoint's A dPhi/dA / Phi = 2 + 2 (a_4/a_2) A^2 + ...:
+    within 1e-4 of 2 at A = 1e-3, and its excess over 2 grows as A^2 (the
+    exponent between A = 2.5e-4 and 1e-3 within 0.1 of 2; the next term
+    moves it by a few hundredths).  The line sits a quarter cell off the
+    grid points: a particle oscillating about a point where the 3-point
+    function's second derivative jumps (|r| = 1/2, App. A.1) adds a term in
+    |A|^3 to Phi, which is even but not analytic in A."""
+    import torch
+
+    from paper_1307_0702_gb300.adjoint import time_averaged_force
+
+    def log_slope(amp):
+        gp, rho, g, parts, weights = line_case("fp64", A=amp, offset=0.25)
+        k = 2 * np.pi / 64.0
+        direction = np.zeros((16, 3))
+        direction[:, 0] = np.sin(2 * k * parts["q"][:, 0])
+        cosk = torch.as_tensor(np.cos(k * np.arange(64.0)), dtype=torch.float64).reshape(1, 1, 64)
+        A = torch.tensor(amp, dtype=torch.float64, requires_grad=True)
+        rho_t = 1.0 + A * cosk.expand(64, 64, 64)
+        phi = time_averaged_force(gp, parts["q"], torch.tensor(parts["m_e"]), torch.tensor(parts["kappa_ratio"]),
+                                  parts["k_spring"], A, rho_t, weights=weights, direction=direction,
+                                  checkpoint_every=50)
+        (dA,) = torch.autograd.grad(phi, (A,))
+        phi = float(phi.detach())
+        assert abs(phi) > 0
+        return amp * float(dA) / phi
+
+    small, large = log_slope(2.5e-4), log_slope(1e-3)
+    assert large == pytest.approx(2.0, abs=1e-4), (small, large)
+    exponent = np.log((large - 2.0) / (small - 2.0)) / np.log(4.0)
+    assert exponent == pytest.approx(2.0, abs=0.1), (small, large)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_line_of_particles_gradient(prec):
+    """The 64^3 rollout of 1000 steps with a checkpoint every 50 steps:
+    gradients of sum_p <F_x,p> with respect to each particle's m_e and
+    kappa_p/kappa_f.  FP64 against central differences of the GPU forward
+    within 1e-5 normwise (A = 1e-2 and step 1e-3: the rounding of Phi over
+    1000 steps puts ~3e-9 of noise into a difference of step 1e-5, while
+    step 1e-3 is limited by truncation at ~1e-7); FP32 within 1e-3 of FP64.
+    The line and the wave are symmetric under x -> -x, which makes the summed
+    x force vanish for every A, so its A-gradient is zero."""
+    gp, rho, g, parts, weights = line_case(prec, A=1e-2)
+    direction = np.tile([1.0, 0.0, 0.0], (16, 1))
+    phi, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=50)
+    if prec == "fp64":
+        e = 1e-3
+        for key in ("m_e", "kappa_ratio"):
+            fd = []
+            for j in (0, 5):
+                pp = {kk: np.array(v, copy=True) for kk, v in parts.items()}
+                pm = {kk: np.array(v, copy=True) for kk, v in parts.items()}
+                pp[key][j] += e
+                pm[key][j] -= e
+                fd.append((gpu_phi(gp, rho, g, pp, weights, direction) -
+                           gpu_phi(gp, rho, g, pm, weights, direction)) / (2 * e))
+            got = gr[key][[0, 5]]
+            assert np.max(np.abs(got - fd)) <= 1e-5 * np.max(np.abs(fd)), (key, got, fd)
+        assert abs(gr["A"]) < 1e-12
+    else:
+        _, ref = gpu_gradient({**gp, "precision": "fp64"}, rho, g, parts, weights, direction, K=50)
+        for key in ("m_e", "kappa_ratio"):
+            assert rel_err(gr[key], ref[key]) < 1e-3, (key, rel_err(gr[key], ref[key]))
