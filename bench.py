@@ -182,6 +182,119 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+ADJOINT_METRIC = ("rollout-gradient steps/s (64^3, 16 tethered particles, 1000 steps, checkpoint every 50; "
+                  "gradient of the time-averaged force w.r.t. m_e, kappa_p/kappa_f, A and the initial state)")
+# the adjoint of the RK3 stage rates (the dominant adjoint kernel) per cell and launch:
+# reads U_s (4 words) and the adjoint of U_{s+1} (4), writes gpart (3), rfbar (3), pibar (1)
+ALG_ADJ_WORDS_PER_CELL = 15
+# its floating-point operations as written once per cell (an FMA is 2, a division 1)
+ALG_ADJ_FLOPS_PER_CELL = 280
+
+
+def run_adjoint(args):
+    """Differentiable rollout (the gradient of the time-averaged tether force,
+    deterministic): one unit of work is one step of the rollout run forward
+    and reversed (checkpoints every 50 steps, each segment recomputed and its
+    steps recorded and reversed).  FP32 is the line's value; FP64 rides along."""
+    import torch
+
+    from paper_1307_0702_gb300 import Grid, workloads as W
+    from paper_1307_0702_gb300.adjoint import Rollout
+
+    nsteps, K = args.adj_steps, 50
+    peak, peak_kind = load_peaks()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for prec in ("fp32", "fp64"):
+        gp, rho, g, parts = W.line_config(64, 16, wave_amp=1e-3, precision=prec)
+        cells = gp["nx"] * gp["ny"] * gp["nz"]
+        grid = Grid(gp)
+        grid.set_state(rho, g)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
+        tiling = grid.autotune(reps=3)           # stage-kernel tiling for 64^3 (results do not depend on it)
+        roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K)
+        roll.forward(np.ones(max(args.warmup, 3)))      # warm-up: graphs captured, snapshots allocated
+        roll.backward()
+        grid.snapshot_load(roll.checkpoints[0])
+        sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        sampler.start()
+        time.sleep(0.3)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi = roll.forward(np.ones(nsteps))
+        t1 = time.perf_counter()
+        gr = roll.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        clocks = sampler.stop((t0, t2))
+        # the same rollout once more with every kernel bracketed by events
+        grid.snapshot_load(roll.checkpoints[0])
+        grid.profile(True)
+        roll.forward(np.ones(nsteps))
+        roll.backward()
+        prof = grid.profile_read()
+        grid.profile(False)
+        grid.close()
+        st_ms, st_n = prof["adjoint_stage"]
+        per_launch = st_ms / st_n * 1e-3
+        words = 4 if prec == "fp32" else 8
+        rec = {"value": nsteps / (t2 - t0), "unit": "rollout-gradient steps/s", "phi": phi,
+               "ms_per_step": 1e3 * (t2 - t0) / nsteps, "forward_ms_per_step": 1e3 * (t1 - t0) / nsteps,
+               "reverse_ms_per_step": 1e3 * (t2 - t1) / nsteps,
+               "cell_steps_per_s": cells * nsteps / (t2 - t0),
+               "kernel_ms_per_step": {k: v[0] / nsteps for k, v in prof.items()},
+               "launches_per_step": sum(v[1] for v in prof.values()) / nsteps,
+               "grad_m_e_0": float(gr["m_e"][0]), "grad_A": float(gr["A"]), "clocks": clocks,
+               "stage_tiling": list(tiling)}
+        if prec == "fp32":
+            achieved = ALG_ADJ_WORDS_PER_CELL * words * cells / per_launch / 1e9
+            rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                               "kernel": "k_adj_stage_rates (3 launches per reversed step)",
+                               "alg_bytes_per_launch": ALG_ADJ_WORDS_PER_CELL * words * cells,
+                               "note": "the 64^3 working set (15 fields, 16 MB) is L2-resident"}
+        else:
+            tflops = ALG_ADJ_FLOPS_PER_CELL * cells / per_launch / 1e12
+            rec["roofline"] = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                               "peak_kind": "nominal (FP64 units)",
+                               "kernel": "k_adj_stage_rates (3 launches per reversed step)",
+                               "alg_flops_per_launch": ALG_ADJ_FLOPS_PER_CELL * cells}
+        out[prec] = rec
+    r = out["fp32"]
+    line = {
+        "metric": ADJOINT_METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": nsteps,
+        "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiable rollout: 64^3, 16 tethered particles on a line along x, A=1e-3, "
+                               "kT=0, 1000 steps, checkpoint every 50 (FP32; FP64 in 'fp64')",
+                   "l2": "flushed before the timed rollout; the 64^3 state stays L2-resident within it"},
+        "roofline": r["roofline"], "gpu_launches": int(round(r["launches_per_step"] * nsteps)),
+        "clocks": r["clocks"], "fp32": r, "fp64": out["fp64"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = adjoint_cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_cpu_baseline(nsteps=12):
+    """The oracle's checkpointed reverse sweep on the same 64^3 line, a
+    bounded number of steps."""
+    from oracle import adjoint as oadj, ic as oic
+    from paper_1307_0702_gb300 import workloads as W
+
+    gp, rho, g, parts = W.line_config(64, 16, wave_amp=1e-3, precision="fp64")
+    p = oic.GridParams(**{k: v for k, v in gp.items() if k in oic.GridParams.__dataclass_fields__})
+    op = oadj.make_parts(parts["q"], parts["u"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], p.c)
+    d = np.tile([1.0, 0.0, 0.0], (16, 1))
+    t0 = time.perf_counter()
+    oadj.rollout_gradient(p, rho - p.rho0, g, op, np.ones(nsteps), d, checkpoint_every=6)
+    el = time.perf_counter() - t0
+    return {"value": nsteps / el, "unit": "rollout-gradient steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"the same 64^3 line, {nsteps} steps, checkpoint every 6, {el:.1f} s (numpy FP64, 1 thread)"}
+
+
 ENSEMBLE_METRIC = "cell-updates/s and particle-steps/s (ensemble of 256 boxes, edges 16/24/32/48, 1-200 particles)"
 
 
@@ -281,7 +394,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "ensemble"],
+    ap.add_argument("--adj-steps", type=int, default=1000)
+    ap.add_argument("--workload", default="box", choices=["box", "ensemble", "adjoint"],
                     help="box: the 128^3 single box (default); ensemble: the batched 256-box ensemble")
     ap.add_argument("--boxes", type=int, default=256)
     ap.add_argument("--tile", type=int, nargs=2, metavar=("TILE_X", "ZCHUNK"), default=None,
@@ -303,6 +417,10 @@ def main():
     if args.workload == "ensemble":
         if rank == 0:
             run_ensemble(args)
+        return
+    if args.workload == "adjoint":
+        if rank == 0:
+            run_adjoint(args)
         return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))

@@ -207,11 +207,14 @@ ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice);
 ic_status ic_batch_autotune(ic_batch *batch, int reps);
 
 /* Kernel timing for measurement.  While enabled, ic_step launches without
- * CUDA graphs and brackets every kernel with CUDA events on the context's
- * stream.  ic_profile_read synchronises and returns, per kernel class
- * (0: fluid RK3 stages, 1: particle kernels, 2: end-of-step reduction), the
- * summed device milliseconds (ms[3]) and launch counts (launches[3]) since
- * the last reset. */
+ * CUDA graphs and brackets every kernel (and ic_adjoint_step every adjoint
+ * kernel) with CUDA events on the context's stream.  ic_profile_read
+ * synchronises and returns, per kernel class (0: fluid RK3 stages, 1:
+ * particle kernels, 2: end-of-step reduction, 3: adjoint of the RK3 stage
+ * rates, 4: other adjoint grid kernels, 5: adjoint particle kernels), the
+ * summed device milliseconds (ms[IC_PROFILE_CLASSES]) and launch counts
+ * (launches[IC_PROFILE_CLASSES]) since the last reset. */
+#define IC_PROFILE_CLASSES 6
 ic_status ic_profile(ic_ctx *ctx, int enable);
 ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset);
 
@@ -258,7 +261,7 @@ ic_status ic_fluid_step_noalloc(const ic_grid_params *params, const void *const 
  * -c^2 / (kappa_p/kappa_f)^2 dPhi/d epsilon_pf.  The adjoint spreads with
  * atomic adds: it is reproducible to rounding, not bit for bit.
  *
- * ic_adjoint_enable allocates the tape and adjoint fields (26 grid fields in
+ * ic_adjoint_enable allocates the tape and adjoint fields (29 grid fields in
  * the context's precision, 20 doubles per particle) and zeroes them; it
  * returns IC_ERR_STATE if kT > 0, IC_ERR_OOM if allocation fails.  Adding
  * particles afterwards makes the other calls return IC_ERR_STATE until it is
@@ -285,9 +288,12 @@ ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, doubl
 /* Device snapshots of the state a rollout needs to restart a step (fields,
  * q, u, step counter): the caller owns dev_buf, device memory of
  * ic_snapshot_size bytes, 16-byte aligned (IC_ERR_ARG otherwise).  Save
- * enqueues device copies on the context's stream; load restores them (and
- * the step's drive) and returns IC_ERR_ARG if the snapshot is of another grid,
- * precision or particle count.  The time averages are not part of it. */
+ * enqueues device copies on the context's stream; load enqueues the copies
+ * back (and the step's drive).  Neither synchronises when the buffer was last
+ * saved by the same context (its header is remembered); a buffer from
+ * elsewhere has its header read back and checked: IC_ERR_ARG if it is of
+ * another grid, precision or particle count.  The time averages are not part
+ * of a snapshot. */
 ic_status ic_snapshot_size(const ic_ctx *ctx, size_t *bytes);
 ic_status ic_snapshot_save(ic_ctx *ctx, void *dev_buf);
 ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf);

@@ -72,17 +72,18 @@ class Rollout:
         n = len(self.weights)
         W = float(np.sum(self.weights))
         g.adjoint_reset(self.direction)
-        pool = [g.new_snapshot() for _ in range(min(self.K, n))]
+        pool = [g.new_snapshot() for _ in range(min(self.K, n) - 1)]
         for seg in range(len(self.checkpoints) - 1, -1, -1):
             start = seg * self.K
             stop = min(start + self.K, n)
-            g.snapshot_load(self.checkpoints[seg])
-            pool[0].copy_(self.checkpoints[seg])
+            # the segment's states: its checkpoint, then one snapshot per recomputed step
+            states = [self.checkpoints[seg]] + pool[:stop - start - 1]
+            g.snapshot_load(states[0])
             for j in range(1, stop - start):
                 g.step(1)
-                g.snapshot_save(pool[j])
+                g.snapshot_save(states[j])
             for j in range(stop - start - 1, -1, -1):
-                g.snapshot_load(pool[j])
+                g.snapshot_load(states[j])
                 g.step_record()
                 g.adjoint_step(self.weights[start + j] / W)
         out = g.adjoint_read()

@@ -36,7 +36,9 @@ namespace ic {
 namespace {
 
 constexpr int kAdjThreads = 256;
-constexpr int kAdjParticleThreads = 64;
+constexpr int kAdjParticleThreads = 128;   // one warp per particle
+// kernel classes of ic_profile_read
+constexpr int kClassStage = 3, kClassGrid = 4, kClassParticles = 5;
 
 // SSP-RK3 coefficients: U_{s+1} = a_s U^n + b_s (U_s + dt R(U_s))
 constexpr double kA[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -128,88 +130,116 @@ struct StageAdjConsts {
   double dpdA;          // d (drive amplitude of this stage) / d A
 };
 
-// Transpose of the rates R(U_s, pi) applied to lambda (App. A.2 flux form):
+// Face velocities v^a = g^a / rho^a of the stage state U_s, read many times
+// by the stage adjoint below.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_face_velocity(State<real> U, Geo G, real rho0, real *v0, real *v1,
+                                                                    real *v2) {
+  real *v[3] = {v0, v1, v2};
+  const size_t cells = size_t(G.nx) * G.ny * G.nz;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cells; i += size_t(gridDim.x) * blockDim.x) {
+    int x, y, z;
+    grid_coords<real>(i, G, x, y, z);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a][i] = U.g[a][i] / face_rho(U, G, rho0, a, x, y, z);
+  }
+}
+
+template <typename real>
+struct StageIn {
+  const real *lam[4];   // adjoint of U_{s+1} (delta rho, g_x, g_y, g_z), scaled by coef when read
+  const real *v[3];     // face velocities of U_s
+  State<real> U;        // U_s
+};
+
+// Transpose of the rates R(U_s, pi) applied to lambda = coef * (adjoint of
+// U_{s+1}) (App. A.2 flux form), for the A-faces of cell i:
 //   Tbar_a(c)  = (lambda_a(c) - lambda_a(c - a)) / h        diagonal flux at centre c
 //   Fbar_ab(c) = (lambda_a(c + b) - lambda_a(c)) / h        a-momentum flux along b on c's edge
-// gathered into the face adjoints of cell i:
-//   gpart_a(i) = gbar_a(i) + vbar_a(i) / rho^a_i  (the advective momenta, the mass flux and V^T),
-//   rfbar_a(i) = -vbar_a(i) v_a(i) / rho^a_i      (for the density part, summed by the next kernel),
-//   pibar(i)   = sum_a Tbar_a(i)                    (adjoint of the centre pressure).
-// Also adds dpdA * sum_i pibar(i) profile(i) to *gA (the drive is linear in A).
+// gathered into
+//   gp = gbar_A(i) + vbar_A(i) / rho^A_i  (the advective momenta, the mass flux and V^T),
+//   rf = -vbar_A(i) v_A(i) / rho^A_i      (for the density part, summed by the next kernel),
+//   T0 = Tbar_A(i)                        (its sum over A is the adjoint of the centre pressure).
+template <typename real, int A>
+__device__ __forceinline__ void stage_face(const StageIn<real> &In, const Geo &G, real coef, real inv_h, real eta,
+                                           real lam2, real rho0, int x, int y, int z, size_t i, real &gp, real &rf,
+                                           real &T0) {
+  constexpr int ax = A == 0, ay = A == 1, az = A == 2;
+  const auto L = [&](int a, int xx, int yy, int zz) { return coef * In.lam[1 + a][G.at(xx, yy, zz)]; };
+  const auto Tb = [&](int a, int xx, int yy, int zz) {
+    return (L(a, xx, yy, zz) - L(a, xx - (a == 0), yy - (a == 1), zz - (a == 2))) * inv_h;
+  };
+  const auto Fb = [&](int a, int b, int xx, int yy, int zz) {
+    return (L(a, xx + (b == 0), yy + (b == 1), zz + (b == 2)) - L(a, xx, yy, zz)) * inv_h;
+  };
+  const auto V = [&](int a, int xx, int yy, int zz) { return In.v[a][G.at(xx, yy, zz)]; };
+  const auto Gm = [&](int a, int xx, int yy, int zz) { return In.U.g[a][G.at(xx, yy, zz)]; };
+  // dvbar_A(c) = -2 eta Tbar_A(c) - lam2 sum_a Tbar_a(c)
+  const auto DV = [&](int xx, int yy, int zz) {
+    const real t0 = Tb(0, xx, yy, zz), t1 = Tb(1, xx, yy, zz), t2 = Tb(2, xx, yy, zz);
+    return real(-2) * eta * (A == 0 ? t0 : (A == 1 ? t1 : t2)) - lam2 * (t0 + t1 + t2);
+  };
+  // diagonal fluxes at the centres i and i + A
+  T0 = Tb(A, x, y, z);
+  const real T1 = Tb(A, x + ax, y + ay, z + az);
+  const real vm = V(A, x - ax, y - ay, z - az), v0 = In.v[A][i], vp = V(A, x + ax, y + ay, z + az);
+  const real gm = Gm(A, x - ax, y - ay, z - az), g0 = In.U.g[A][i], gpl = Gm(A, x + ax, y + ay, z + az);
+  real gb = real(0.25) * (T0 * (vm + v0) + T1 * (v0 + vp));
+  real vb = real(0.25) * (T0 * (gm + g0) + T1 * (g0 + gpl));
+  vb += (DV(x, y, z) - DV(x + ax, y + ay, z + az)) * inv_h;
+  // edge fluxes on the edges of i and i - B
+#pragma unroll
+  for (int B = 0; B < 3; ++B) {
+    if (B == A) continue;
+    const int bx = B == 0, by = B == 1, bz = B == 2;
+    const real Fab0 = Fb(A, B, x, y, z), Fab1 = Fb(A, B, x - bx, y - by, z - bz);
+    const real Fba0 = Fb(B, A, x, y, z), Fba1 = Fb(B, A, x - bx, y - by, z - bz);
+    gb += real(0.25) * (Fab0 * (V(B, x, y, z) + V(B, x + ax, y + ay, z + az)) +
+                        Fab1 * (V(B, x - bx, y - by, z - bz) + V(B, x - bx + ax, y - by + ay, z - bz + az)));
+    vb += real(0.25) * (Fba0 * (Gm(B, x, y, z) + Gm(B, x + ax, y + ay, z + az)) +
+                        Fba1 * (Gm(B, x - bx, y - by, z - bz) + Gm(B, x - bx + ax, y - by + ay, z - bz + az)));
+    // the viscous part of the (A, B) edge flux, shared by F_AB and F_BA
+    vb += eta * inv_h * ((Fab0 + Fba0) - (Fab1 + Fba1));
+  }
+  // mass flux: d rho/dt = -(1/h) sum_a (g_a(i) - g_a(i - a))
+  gb -= coef * (In.lam[0][i] - In.lam[0][G.at(x + ax, y + ay, z + az)]) * inv_h;
+  const real rfv = face_rho(In.U, G, rho0, A, x, y, z);
+  gp = gb + vb / rfv;
+  rf = -vb * v0 / rfv;
+}
+
+// The stage adjoint's grid part for every cell (stage_face of the three
+// face sets), and dpdA * sum_i pibar(i) profile(i) added to *gA (the drive is
+// linear in A).
 template <typename real>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(State<real> U, Geo G, StageAdjConsts k,
-                                                                  const real *__restrict__ cos_table,
-                                                                  const real *__restrict__ b0, const real *__restrict__ b1,
-                                                                  const real *__restrict__ b2, const real *__restrict__ b3,
-                                                                  real *gp0, real *gp1, real *gp2, real *rf0, real *rf1,
+__global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(StageIn<real> In, Geo G, StageAdjConsts k,
+                                                                  const real *__restrict__ cos_table, real *gp0,
+                                                                  real *gp1, real *gp2, real *rf0, real *rf1,
                                                                   real *rf2, real *pibar, double *gA) {
-  const real *bg[3] = {b1, b2, b3};
-  real *gp[3] = {gp0, gp1, gp2};
-  real *rfo[3] = {rf0, rf1, rf2};
   const real coef = real(k.coef), inv_h = real(k.inv_h), eta = real(k.eta), lam2 = real(k.lam2),
              rho0 = real(k.rho0);
   const size_t cells = size_t(G.nx) * G.ny * G.nz;
-  const auto Lg = [&](int a, int x, int y, int z) { return coef * bg[a][G.at(x, y, z)]; };
-  const auto Lr = [&](int x, int y, int z) { return coef * b0[G.at(x, y, z)]; };
-  const auto Tb = [&](int a, int x, int y, int z) {
-    return (Lg(a, x, y, z) - Lg(a, x - ex(a), y - ey(a), z - ez(a))) * inv_h;
-  };
-  const auto Fb = [&](int a, int b, int x, int y, int z) {
-    return (Lg(a, x + ex(b), y + ey(b), z + ez(b)) - Lg(a, x, y, z)) * inv_h;
-  };
-  const auto V = [&](int a, int x, int y, int z) { return face_v(U, G, rho0, a, x, y, z); };
-  const auto Gm = [&](int a, int x, int y, int z) { return U.g[a][G.at(x, y, z)]; };
-  // dvbar_a(c) = -2 eta Tbar_a(c) - lam2 sum_c' Tbar_c'(c)
-  const auto DV = [&](int a, int x, int y, int z) {
-    const real t0 = Tb(0, x, y, z), t1 = Tb(1, x, y, z), t2 = Tb(2, x, y, z);
-    const real ta = a == 0 ? t0 : (a == 1 ? t1 : t2);
-    return real(-2) * eta * ta - lam2 * (t0 + t1 + t2);
-  };
   double acc_A = 0.0;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cells; i += size_t(gridDim.x) * blockDim.x) {
     int x, y, z;
     grid_coords<real>(i, G, x, y, z);
-    real pb = real(0);
-#pragma unroll 1
-    for (int a = 0; a < 3; ++a) {
-      const int ax = ex(a), ay = ey(a), az = ez(a);
-      real gb = real(0), vb = real(0);
-      // diagonal fluxes at the centres i and i + a
-      const real T0 = Tb(a, x, y, z), T1 = Tb(a, x + ax, y + ay, z + az);
-      pb += T0;
-      const real vm = V(a, x - ax, y - ay, z - az), v0 = V(a, x, y, z), vp = V(a, x + ax, y + ay, z + az);
-      const real gm = Gm(a, x - ax, y - ay, z - az), g0 = U.g[a][i], gpl = Gm(a, x + ax, y + ay, z + az);
-      gb += real(0.25) * (T0 * (vm + v0) + T1 * (v0 + vp));
-      vb += real(0.25) * (T0 * (gm + g0) + T1 * (g0 + gpl));
-      vb += (DV(a, x, y, z) - DV(a, x + ax, y + ay, z + az)) * inv_h;
-      // edge fluxes on the edges of i and i - b
-#pragma unroll 1
-      for (int b = 0; b < 3; ++b) {
-        if (b == a) continue;
-        const int bx = ex(b), by = ey(b), bz = ez(b);
-        const real Fab0 = Fb(a, b, x, y, z), Fab1 = Fb(a, b, x - bx, y - by, z - bz);
-        const real Fba0 = Fb(b, a, x, y, z), Fba1 = Fb(b, a, x - bx, y - by, z - bz);
-        gb += real(0.25) * (Fab0 * (V(b, x, y, z) + V(b, x + ax, y + ay, z + az)) +
-                            Fab1 * (V(b, x - bx, y - by, z - bz) + V(b, x - bx + ax, y - by + ay, z - bz + az)));
-        vb += real(0.25) * (Fba0 * (Gm(b, x, y, z) + Gm(b, x + ax, y + ay, z + az)) +
-                            Fba1 * (Gm(b, x - bx, y - by, z - bz) + Gm(b, x - bx + ax, y - by + ay, z - bz + az)));
-        // the viscous part of the (a, b) edge flux, shared by F_ab and F_ba
-        vb += eta * inv_h * ((Fab0 + Fba0) - (Fab1 + Fba1));
-      }
-      // mass flux: d rho/dt = -(1/h) sum_a (g_a(i) - g_a(i - a))
-      gb -= (Lr(x, y, z) - Lr(x + ax, y + ay, z + az)) * inv_h;
-      const real rf = face_rho(U, G, rho0, a, x, y, z);
-      gp[a][i] = gb + vb / rf;
-      rfo[a][i] = -vb * v0 / rf;
-    }
+    real g0, r0, t0, g1, r1, t1, g2, r2, t2;
+    stage_face<real, 0>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g0, r0, t0);
+    stage_face<real, 1>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g1, r1, t1);
+    stage_face<real, 2>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g2, r2, t2);
+    gp0[i] = g0;
+    gp1[i] = g1;
+    gp2[i] = g2;
+    rf0[i] = r0;
+    rf1[i] = r1;
+    rf2[i] = r2;
+    const real pb = t0 + t1 + t2;
     pibar[i] = pb;
-    if (k.forcing == IC_FORCE_MODE) {
-      const int c = k.wave_axis == 0 ? x : (k.wave_axis == 1 ? y : z);
+    const int c = k.wave_axis == 0 ? x : (k.wave_axis == 1 ? y : z);
+    if (k.forcing == IC_FORCE_MODE)
       acc_A += double(pb) * double(cos_table[c]);
-    } else if (k.forcing == IC_FORCE_PLANE) {
-      const int c = k.wave_axis == 0 ? x : (k.wave_axis == 1 ? y : z);
-      if (c == k.plane_index) acc_A += double(pb);
-    }
+    else if (k.forcing == IC_FORCE_PLANE && c == k.plane_index)
+      acc_A += double(pb);
   }
   if (k.forcing != IC_FORCE_NONE) {
     acc_A = warp_sum(acc_A);
@@ -217,9 +247,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(State<real> U, 
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc_A;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < int(blockDim.x) / 32; ++w) s += red[w];
-      atomicAdd(gA, k.dpdA * s);
+      double sum = 0.0;
+      for (int w = 0; w < int(blockDim.x) / 32; ++w) sum += red[w];
+      atomicAdd(gA, k.dpdA * sum);
     }
   }
 }
@@ -296,43 +326,64 @@ __device__ void stencil_at(const typename Pos<real>::T *q, const PConsts<real> &
   }
 }
 
-// Visit the 27 points of location set `set` (0 centre, 1 + a the a-faces):
-// f(cell index, x, y, z, w, dw/dq_x, dw/dq_y, dw/dq_z).
-template <typename real, typename F>
-__device__ __forceinline__ void for_points(const Sten<real> &S, int set, const Geo &G, F f) {
+// One warp per particle: lane t < 27 holds point t = (t % 3, (t / 3) % 3,
+// t / 9) - 1 of a location set (0 centre, 1 + a the a-faces).  Returns false
+// on the other lanes; else the cell, its coordinates, the weight and its
+// gradient with respect to q.
+template <typename real>
+__device__ __forceinline__ bool point_of(const Sten<real> &S, int set, const Geo &G, int lane, size_t &i, int &x,
+                                         int &y, int &z, real &w, real dw[3]) {
+  if (lane >= 27) return false;
+  const int dx = lane % 3, dy = (lane / 3) % 3, dz = lane / 9;
   const int sx = set == 1, sy = set == 2, sz = set == 3;
-  for (int dz = 0; dz < 3; ++dz)
-    for (int dy = 0; dy < 3; ++dy)
-      for (int dx = 0; dx < 3; ++dx) {
-        const real wx = S.w[sx][0][dx], wy = S.w[sy][1][dy], wz = S.w[sz][2][dz];
-        const real gx = S.dw[sx][0][dx], gy = S.dw[sy][1][dy], gz = S.dw[sz][2][dz];
-        const int x = pw(S.b[sx][0] + dx - 1, G.nx), y = pw(S.b[sy][1] + dy - 1, G.ny),
-                  z = pw(S.b[sz][2] + dz - 1, G.nz);
-        f(G.at(x, y, z), x, y, z, wx * wy * wz, gx * wy * wz, wx * gy * wz, wx * wy * gz);
-      }
+  const real wx = S.w[sx][0][dx], wy = S.w[sy][1][dy], wz = S.w[sz][2][dz];
+  x = pw(S.b[sx][0] + dx - 1, G.nx);
+  y = pw(S.b[sy][1] + dy - 1, G.ny);
+  z = pw(S.b[sz][2] + dz - 1, G.nz);
+  i = G.at(x, y, z);
+  w = wx * wy * wz;
+  dw[0] = S.dw[sx][0][dx] * wy * wz;
+  dw[1] = wx * S.dw[sy][1][dy] * wz;
+  dw[2] = wx * wy * S.dw[sz][2][dz];
+  return true;
+}
+
+// warp sum, the same value (lane 0's) on every lane
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // J f (FP64 sum) and its gradient with respect to q; val(i, x, y, z) gives f
 template <typename real, typename Val>
-__device__ __forceinline__ void interp_grad(const Sten<real> &S, int set, const Geo &G, Val val, double &J,
+__device__ __forceinline__ void interp_grad(const Sten<real> &S, int set, const Geo &G, int lane, Val val, double &J,
                                             double dJ[3]) {
-  J = 0.0;
-  dJ[0] = dJ[1] = dJ[2] = 0.0;
-  for_points<real>(S, set, G, [&](size_t i, int x, int y, int z, real w, real gx, real gy, real gz) {
+  double j = 0.0, a = 0.0, b = 0.0, c = 0.0;
+  size_t i;
+  int x, y, z;
+  real w, dw[3];
+  if (point_of<real>(S, set, G, lane, i, x, y, z, w, dw)) {
     const double f = double(val(i, x, y, z));
-    J += double(w) * f;
-    dJ[0] += double(gx) * f;
-    dJ[1] += double(gy) * f;
-    dJ[2] += double(gz) * f;
-  });
+    j = double(w) * f;
+    a = double(dw[0]) * f;
+    b = double(dw[1]) * f;
+    c = double(dw[2]) * f;
+  }
+  J = wsum(j);
+  dJ[0] = wsum(a);
+  dJ[1] = wsum(b);
+  dJ[2] = wsum(c);
 }
 
 // transpose of J: point i of set `set` receives w_i * value
 template <typename real>
-__device__ __forceinline__ void spread_T(const Sten<real> &S, int set, const Geo &G, real *field, double value) {
-  for_points<real>(S, set, G, [&](size_t i, int, int, int, real w, real, real, real) {
-    atomicAdd(field + i, real(double(w) * value));
-  });
+__device__ __forceinline__ void spread_T(const Sten<real> &S, int set, const Geo &G, int lane, real *field,
+                                         double value) {
+  size_t i;
+  int x, y, z;
+  real w, dw[3];
+  if (point_of<real>(S, set, G, lane, i, x, y, z, w, dw)) atomicAdd(field + i, real(double(w) * value));
 }
 
 template <typename real>
@@ -395,12 +446,15 @@ struct Fields3 {
   real *f[3];
 };
 
+__device__ __forceinline__ int warp_particle() { return int((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+
 // Substep 7 reversed: jv_new_bar = jv_nh_bar = dt/2 qbar (kept for the last
 // kernel); vbar_a += J^T jv_new_bar_a at q^{n+1/2};
 // qhbar = sum_a jv_new_bar_a d(J v^{n+1}_a)/dq; fbar = 0.
 template <typename real>
-__global__ void k_adj_p_final(AdjParticles<real> P, State<real> Unew, Geo G, PConsts<real> pc, Fields3<real> vb) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_final(AdjParticles<real> P, State<real> Unew, Geo G,
+                                                                      PConsts<real> pc, Fields3<real> vb) {
+  const int p = warp_particle(), lane = threadIdx.x & 31;
   if (p >= P.n) return;
   Sten<real> S;
   stencil_at<real>(P.q_half + 3 * p, pc, S);
@@ -408,14 +462,17 @@ __global__ void k_adj_p_final(AdjParticles<real> P, State<real> Unew, Geo G, PCo
 #pragma unroll 1
   for (int a = 0; a < 3; ++a) {
     const double jb = 0.5 * double(pc.dt) * P.qbar[3 * p + a];
-    P.jvnh[3 * p + a] = jb;
-    P.fbar[3 * p + a] = 0.0;
     double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, FaceV<real>{Unew, G, pc.rho0, a}, J, dJ);
+    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Unew, G, pc.rho0, a}, J, dJ);
     for (int c = 0; c < 3; ++c) qh[c] += jb * dJ[c];
-    spread_T<real>(S, 1 + a, G, vb.f[a], jb);
+    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb);
+    if (lane == 0) {
+      P.jvnh[3 * p + a] = jb;
+      P.fbar[3 * p + a] = 0.0;
+    }
   }
-  for (int c = 0; c < 3; ++c) P.qhbar[3 * p + c] = qh[c];
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) P.qhbar[3 * p + c] = qh[c];
 }
 
 // Substeps 6, 5 and 4 reversed (after V^T of v^{n+1} has been added to bar):
@@ -426,9 +483,11 @@ __global__ void k_adj_p_final(AdjParticles<real> P, State<real> Unew, Geo G, PCo
 //   vbar_a += J_a^T jvt_bar_a                              (J v~ at q^{n+1/2})
 // plus every term's gradient with respect to q^{n+1/2}.
 template <typename real>
-__global__ void k_adj_p_impulse(AdjParticles<real> P, State<real> U3, Geo G, PConsts<real> pc, Fields3<real> vb,
-                                const real *gbar0, const real *gbar1, const real *gbar2, real *rhobar) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_impulse(AdjParticles<real> P, State<real> U3, Geo G,
+                                                                        PConsts<real> pc, Fields3<real> vb,
+                                                                        const real *gbar0, const real *gbar1,
+                                                                        const real *gbar2, real *rhobar) {
+  const int p = warp_particle(), lane = threadIdx.x & 31;
   if (p >= P.n) return;
   const real *gb[3] = {gbar0, gbar1, gbar2};
   Sten<real> S;
@@ -438,33 +497,38 @@ __global__ void k_adj_p_impulse(AdjParticles<real> P, State<real> U3, Geo G, PCo
   double dgb[3], jvt[3], djvt[3][3];
   for (int a = 0; a < 3; ++a) {
     double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, FieldV<real>{gb[a], real(1)}, J, dJ);
+    interp_grad<real>(S, 1 + a, G, lane, FieldV<real>{gb[a], real(1)}, J, dJ);
     dgb[a] = -J * inv_h3;
     const double dga = double(P.dg[3 * p + a]);
     for (int c = 0; c < 3; ++c) qh[c] -= dga * inv_h3 * dJ[c];
-    interp_grad<real>(S, 1 + a, G, FaceV<real>{U3, G, pc.rho0, a}, jvt[a], djvt[a]);
+    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{U3, G, pc.rho0, a}, jvt[a], djvt[a]);
   }
   double Jr, dJr[3];
-  interp_grad<real>(S, 0, G, FieldV<real>{U3.d, real(1)}, Jr, dJr);
+  interp_grad<real>(S, 0, G, lane, FieldV<real>{U3.d, real(1)}, Jr, dJr);
   const double me = double(P.m_e[p]), mf = vol * (double(pc.rho0) + Jr), tot = me + mf;
   const double r = mf / tot, mu = me * r;
-  double su = 0.0, sg = 0.0, jvtb[3];
+  double su = 0.0, sg = 0.0, jvtb[3], ub_new[3];
   for (int a = 0; a < 3; ++a) {
     const double ub = P.ubar[3 * p + a], d = jvt[a] - double(P.u_n[3 * p + a]);
     jvtb[a] = r * ub + mu * dgb[a];
-    P.ubar[3 * p + a] = (1.0 - r) * ub - mu * dgb[a];
+    ub_new[a] = (1.0 - r) * ub - mu * dgb[a];
     su += ub * d;
     sg += dgb[a] * d;
   }
   const double mfb = me / (tot * tot) * su + me * me / (tot * tot) * sg;
-  P.gme[p] += -mf / (tot * tot) * su + mf * mf / (tot * tot) * sg;
-  spread_T<real>(S, 0, G, rhobar, vol * mfb);
+  spread_T<real>(S, 0, G, lane, rhobar, vol * mfb);
   for (int c = 0; c < 3; ++c) qh[c] += vol * mfb * dJr[c];
   for (int a = 0; a < 3; ++a) {
     for (int c = 0; c < 3; ++c) qh[c] += jvtb[a] * djvt[a][c];
-    spread_T<real>(S, 1 + a, G, vb.f[a], jvtb[a]);
+    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jvtb[a]);
   }
-  for (int c = 0; c < 3; ++c) P.qhbar[3 * p + c] = qh[c];
+  if (lane == 0) {
+    P.gme[p] += -mf / (tot * tot) * su + mf * mf / (tot * tot) * sg;
+    for (int c = 0; c < 3; ++c) {
+      P.ubar[3 * p + c] = ub_new[c];
+      P.qhbar[3 * p + c] = qh[c];
+    }
+  }
 }
 
 // The particle terms of one RK stage reversed (before the stage's combine):
@@ -473,9 +537,11 @@ __global__ void k_adj_p_impulse(AdjParticles<real> P, State<real> U3, Geo G, PCo
 //   F_bar_a += J_a lambda_a / h^3 with lambda = coef * gbar           (the source S F)
 // plus their gradients with respect to q^{n+1/2}.
 template <typename real>
-__global__ void k_adj_p_stage(AdjParticles<real> P, State<real> Us, Geo G, PConsts<real> pc, const real *pibar,
-                              const real *gbar0, const real *gbar1, const real *gbar2, real coef, real *rhox) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_stage(AdjParticles<real> P, State<real> Us, Geo G,
+                                                                      PConsts<real> pc, const real *pibar,
+                                                                      const real *gbar0, const real *gbar1,
+                                                                      const real *gbar2, real coef, real *rhox) {
+  const int p = warp_particle(), lane = threadIdx.x & 31;
   if (p >= P.n) return;
   const real *gb[3] = {gbar0, gbar1, gbar2};
   Sten<real> S;
@@ -483,20 +549,26 @@ __global__ void k_adj_p_stage(AdjParticles<real> P, State<real> Us, Geo G, PCons
   const double inv_h3 = double(pc.inv_h3), vol = double(pc.vol), eps = double(P.eps[p]);
   double qh[3] = {P.qhbar[3 * p], P.qhbar[3 * p + 1], P.qhbar[3 * p + 2]};
   double Jp, dJp[3], Jr, dJr[3];
-  interp_grad<real>(S, 0, G, FieldV<real>{pibar, real(1)}, Jp, dJp);
-  interp_grad<real>(S, 0, G, FieldV<real>{Us.d, real(1)}, Jr, dJr);
+  interp_grad<real>(S, 0, G, lane, FieldV<real>{pibar, real(1)}, Jp, dJp);
+  interp_grad<real>(S, 0, G, lane, FieldV<real>{Us.d, real(1)}, Jr, dJr);
   const double ob = Jp * inv_h3, om = eps * vol * Jr;
-  P.geps[p] += vol * Jr * ob;
-  spread_T<real>(S, 0, G, rhox, eps * vol * ob);
+  spread_T<real>(S, 0, G, lane, rhox, eps * vol * ob);
   for (int c = 0; c < 3; ++c) qh[c] += om * inv_h3 * dJp[c] + eps * vol * ob * dJr[c];
+  double fb[3];
   for (int a = 0; a < 3; ++a) {
     double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, FieldV<real>{gb[a], coef}, J, dJ);
-    P.fbar[3 * p + a] += J * inv_h3;
+    interp_grad<real>(S, 1 + a, G, lane, FieldV<real>{gb[a], coef}, J, dJ);
+    fb[a] = J * inv_h3;
     const double Fa = double(P.force[3 * p + a]);
     for (int c = 0; c < 3; ++c) qh[c] += Fa * inv_h3 * dJ[c];
   }
-  for (int c = 0; c < 3; ++c) P.qhbar[3 * p + c] = qh[c];
+  if (lane == 0) {
+    P.geps[p] += vol * Jr * ob;
+    for (int c = 0; c < 3; ++c) {
+      P.fbar[3 * p + c] += fb[c];
+      P.qhbar[3 * p + c] = qh[c];
+    }
+  }
 }
 
 // Substeps 2 and 1 reversed, with the objective's own term:
@@ -505,23 +577,24 @@ __global__ void k_adj_p_stage(AdjParticles<real> P, State<real> Us, Geo G, PCons
 //   qbar += qhbar; jv_n_bar = dt/2 qhbar; vbar_a += J_a^T jv_n_bar_a at q^n
 // plus the gradients with respect to q^{n+1/2} and q^n.
 template <typename real>
-__global__ void k_adj_p_start(AdjParticles<real> P, State<real> Un, Geo G, PConsts<real> pc, Fields3<real> vb,
-                              double weight) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_start(AdjParticles<real> P, State<real> Un, Geo G,
+                                                                      PConsts<real> pc, Fields3<real> vb,
+                                                                      double weight) {
+  const int p = warp_particle(), lane = threadIdx.x & 31;
   if (p >= P.n) return;
   Sten<real> S;
   stencil_at<real>(P.q_half + 3 * p, pc, S);
   double qh[3];
   for (int c = 0; c < 3; ++c) {
-    const double fb = P.fbar[3 * p + c] + weight * P.dir[3 * p + c];
-    qh[c] = P.qhbar[3 * p + c] - double(P.k_s[p]) * fb;
+    const double fbar = P.fbar[3 * p + c] + weight * P.dir[3 * p + c];
+    qh[c] = P.qhbar[3 * p + c] - double(P.k_s[p]) * fbar;
   }
   for (int a = 0; a < 3; ++a) {
     const double jb = P.jvnh[3 * p + a];
     double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
+    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
     for (int c = 0; c < 3; ++c) qh[c] += jb * dJ[c];
-    spread_T<real>(S, 1 + a, G, vb.f[a], jb);
+    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb);
   }
   Sten<real> S0;
   stencil_at<real>(P.q_n + 3 * p, pc, S0);
@@ -530,11 +603,12 @@ __global__ void k_adj_p_start(AdjParticles<real> P, State<real> Un, Geo G, PCons
   for (int a = 0; a < 3; ++a) {
     const double jb = 0.5 * double(pc.dt) * qh[a];
     double J, dJ[3];
-    interp_grad<real>(S0, 1 + a, G, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
+    interp_grad<real>(S0, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
     for (int c = 0; c < 3; ++c) qb[c] += jb * dJ[c];
-    spread_T<real>(S0, 1 + a, G, vb.f[a], jb);
+    spread_T<real>(S0, 1 + a, G, lane, vb.f[a], jb);
   }
-  for (int c = 0; c < 3; ++c) P.qbar[3 * p + c] = qb[c];
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) P.qbar[3 * p + c] = qb[c];
 }
 
 // ---------------------------------------------------------------- host
@@ -549,9 +623,10 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
   cudaStream_t st = ctx->stream;
   const int gblocks = int(std::min<size_t>((cells + kAdjThreads - 1) / kAdjThreads, size_t(ctx->sm_count) * 8));
   const int n = ctx->ps.n;
-  const int pblocks = (n + kAdjParticleThreads - 1) / kAdjParticleThreads;
+  constexpr int kParticlesPerBlock = kAdjParticleThreads / 32;
+  const int pblocks = (n + kParticlesPerBlock - 1) / kParticlesPerBlock;
   const AdjParticles<real> P = adj_particles<real>(ctx);
-  real *bar[4], *acc[4], *gp[3], *rf[3];
+  real *bar[4], *acc[4], *gp[3], *rf[3], *vel[3];
   Fields3<real> vb;
   for (int j = 0; j < 4; ++j) {
     bar[j] = static_cast<real *>(A.bar[j]);
@@ -561,6 +636,7 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
     vb.f[a] = static_cast<real *>(A.vbar[a]);
     gp[a] = static_cast<real *>(A.gpart[a]);
     rf[a] = static_cast<real *>(A.rfbar[a]);
+    vel[a] = static_cast<real *>(A.vel[a]);
   }
   real *pibar = static_cast<real *>(A.pibar), *rhox = static_cast<real *>(A.rhox);
   // the recorded step's states
@@ -570,9 +646,11 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
   void *const *Ustage[3] = {Un, A.tU1, ctx->U[2]};
   const real rho0 = real(p.rho0);
   auto vt = [&](void *const *U) {
-    k_adj_velocity_T<real><<<gblocks, kAdjThreads, 0, st>>>(state_of<real>(U), G, rho0, vb.f[0], vb.f[1], vb.f[2],
-                                                             bar[0], bar[1], bar[2], bar[3]);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = timed_launch(ctx, kClassGrid, [&] {
+      k_adj_velocity_T<real><<<gblocks, kAdjThreads, 0, st>>>(state_of<real>(U), G, rho0, vb.f[0], vb.f[1],
+                                                               vb.f[2], bar[0], bar[1], bar[2], bar[3]);
+      return cudaGetLastError();
+    });
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = cudaMemsetAsync(vb.f[a], 0, fb, st);
     return e;
   };
@@ -583,12 +661,16 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
   } while (0)
   for (int j = 0; j < 4; ++j) IC_ADJ_TRY(cudaMemsetAsync(acc[j], 0, fb, st));
   if (n > 0) {
-    k_adj_p_final<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(Unew), G, pc, vb);
-    IC_ADJ_TRY(cudaGetLastError());
+    IC_ADJ_TRY(timed_launch(ctx, kClassParticles, [&] {
+      k_adj_p_final<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(Unew), G, pc, vb);
+      return cudaGetLastError();
+    }));
     IC_ADJ_TRY(vt(Unew));
-    k_adj_p_impulse<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(U3v), G, pc, vb, bar[1], bar[2],
-                                                                   bar[3], bar[0]);
-    IC_ADJ_TRY(cudaGetLastError());
+    IC_ADJ_TRY(timed_launch(ctx, kClassParticles, [&] {
+      k_adj_p_impulse<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(U3v), G, pc, vb, bar[1],
+                                                                     bar[2], bar[3], bar[0]);
+      return cudaGetLastError();
+    }));
     IC_ADJ_TRY(vt(U3v));
   }
   const double gamma = (4.0 * p.eta / 3.0 + p.zeta) / (2.0 * p.rho0);
@@ -607,23 +689,39 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
     k.plane_index = p.plane_index;
     k.dpdA = per_A * std::sin(ctx->omega * (double(A.rec_step) + kStageTimes[s]) * p.dt + p.wave_phase);
     const State<real> Us = state_of<real>(Ustage[s]);
-    k_adj_stage_rates<real><<<gblocks, kAdjThreads, 0, st>>>(Us, G, k, cos_table, bar[0], bar[1], bar[2], bar[3],
-                                                             gp[0], gp[1], gp[2], rf[0], rf[1], rf[2], pibar, A.gA);
-    IC_ADJ_TRY(cudaGetLastError());
+    StageIn<real> In;
+    for (int j = 0; j < 4; ++j) In.lam[j] = bar[j];
+    for (int a = 0; a < 3; ++a) In.v[a] = vel[a];
+    In.U = Us;
+    IC_ADJ_TRY(timed_launch(ctx, kClassGrid, [&] {
+      k_adj_face_velocity<real><<<gblocks, kAdjThreads, 0, st>>>(Us, G, rho0, vel[0], vel[1], vel[2]);
+      return cudaGetLastError();
+    }));
+    IC_ADJ_TRY(timed_launch(ctx, kClassStage, [&] {
+      k_adj_stage_rates<real><<<gblocks, kAdjThreads, 0, st>>>(In, G, k, cos_table, gp[0], gp[1], gp[2], rf[0],
+                                                               rf[1], rf[2], pibar, A.gA);
+      return cudaGetLastError();
+    }));
     if (n > 0) {
-      k_adj_p_stage<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, Us, G, pc, pibar, bar[1], bar[2], bar[3],
-                                                                   real(k.coef), rhox);
-      IC_ADJ_TRY(cudaGetLastError());
+      IC_ADJ_TRY(timed_launch(ctx, kClassParticles, [&] {
+        k_adj_p_stage<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, Us, G, pc, pibar, bar[1], bar[2], bar[3],
+                                                                     real(k.coef), rhox);
+        return cudaGetLastError();
+      }));
     }
-    k_adj_stage_combine<real><<<gblocks, kAdjThreads, 0, st>>>(G, real(kA[s]), real(kB[s]), real(p.c * p.c), s == 0,
-                                                               bar[0], bar[1], bar[2], bar[3], acc[0], acc[1], acc[2],
-                                                               acc[3], gp[0], gp[1], gp[2], rf[0], rf[1], rf[2], pibar,
-                                                               rhox);
-    IC_ADJ_TRY(cudaGetLastError());
+    IC_ADJ_TRY(timed_launch(ctx, kClassGrid, [&] {
+      k_adj_stage_combine<real><<<gblocks, kAdjThreads, 0, st>>>(G, real(kA[s]), real(kB[s]), real(p.c * p.c),
+                                                                 s == 0, bar[0], bar[1], bar[2], bar[3], acc[0],
+                                                                 acc[1], acc[2], acc[3], gp[0], gp[1], gp[2], rf[0],
+                                                                 rf[1], rf[2], pibar, rhox);
+      return cudaGetLastError();
+    }));
   }
   if (n > 0) {
-    k_adj_p_start<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(Un), G, pc, vb, weight);
-    IC_ADJ_TRY(cudaGetLastError());
+    IC_ADJ_TRY(timed_launch(ctx, kClassParticles, [&] {
+      k_adj_p_start<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(Un), G, pc, vb, weight);
+      return cudaGetLastError();
+    }));
     IC_ADJ_TRY(vt(Un));
   }
 #undef IC_ADJ_TRY

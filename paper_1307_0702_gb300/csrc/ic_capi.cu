@@ -87,27 +87,7 @@ void invalidate_graphs(ic_ctx *ctx) {
     }
 }
 
-cudaEvent_t pooled_event(ic_ctx *ctx) {
-  if (ctx->event_next == ctx->event_pool.size()) {
-    cudaEvent_t ev;
-    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
-    ctx->event_pool.push_back(ev);
-  }
-  return ctx->event_pool[ctx->event_next++];
-}
-
-// Launch `fn` and, while profiling, bracket it with events of class `cls`.
-template <typename F>
-cudaError_t timed_launch(ic_ctx *ctx, int cls, F &&fn) {
-  if (!ctx->profiling) return fn();
-  cudaEvent_t a = pooled_event(ctx), b = pooled_event(ctx);
-  if (!a || !b) return cudaErrorMemoryAllocation;
-  cudaEventRecord(a, ctx->stream);
-  const cudaError_t e = fn();
-  cudaEventRecord(b, ctx->stream);
-  ctx->timed.push_back({a, b, cls});
-  return e;
-}
+using ic::timed_launch;
 
 // Enqueue one full time step with U^n in buffer `cur`; U^{n+1} lands in 1 - cur.
 // With `record`, the intermediates the adjoint needs and the step overwrites
@@ -788,6 +768,33 @@ struct SnapHeader {
 };
 static_assert(sizeof(SnapHeader) == 64, "snapshot header is 64 bytes");
 
+__global__ void k_snapshot_header(SnapHeader *out, uint64_t magic, int64_t step, int np, int precision, int nx,
+                                  int ny, int nz) {
+  SnapHeader h{};
+  h.magic = magic;
+  h.step = step;
+  h.np = np;
+  h.precision = precision;
+  h.nx = nx;
+  h.ny = ny;
+  h.nz = nz;
+  *out = h;
+}
+
+__global__ void k_snapshot_restart(int64_t *step, int64_t n, int *rebuild, double *drive, float *drive_f, double d0,
+                                   double d1, double d2) {
+  step[0] = n;
+  step[1] = n;
+  step[2] = 0;
+  *rebuild = 1;
+  drive[0] = d0;
+  drive[1] = d1;
+  drive[2] = d2;
+  drive_f[0] = float(d0);
+  drive_f[1] = float(d1);
+  drive_f[2] = float(d2);
+}
+
 size_t snapshot_bytes(const ic_ctx *ctx) {
   const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n);
   return sizeof(SnapHeader) + 4 * ((fb + 15) / 16 * 16) + (24 * n + 15) / 16 * 16 + 3 * ctx->real_size * n;
@@ -807,7 +814,7 @@ ic_status ic_adjoint_enable(ic_ctx *ctx) {
   A = ic::AdjointStore{};
   const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n);
   const size_t fstride = (fb + 255) / 256 * 256;
-  constexpr int kFields = 26;
+  constexpr int kFields = 29;
   const size_t tape_q = (24 * n + 255) / 256 * 256;
   char *g = static_cast<char *>(dev_alloc(ctx, kFields * fstride + tape_q + 3 * ctx->real_size * n));
   double *pd = static_cast<double *>(dev_alloc(ctx, (kAdjWordsPerParticle * n + 1) * sizeof(double)));
@@ -822,7 +829,8 @@ ic_status ic_adjoint_enable(ic_ctx *ctx) {
   void **slots[kFields] = {&A.tU1[0], &A.tU1[1], &A.tU1[2], &A.tU1[3], &A.tG3[0], &A.tG3[1], &A.tG3[2],
                            &A.bar[0], &A.bar[1], &A.bar[2], &A.bar[3], &A.acc[0], &A.acc[1], &A.acc[2],
                            &A.acc[3], &A.vbar[0], &A.vbar[1], &A.vbar[2], &A.gpart[0], &A.gpart[1],
-                           &A.gpart[2], &A.rfbar[0], &A.rfbar[1], &A.rfbar[2], &A.pibar, &A.rhox};
+                           &A.gpart[2], &A.rfbar[0], &A.rfbar[1], &A.rfbar[2], &A.pibar, &A.rhox,
+                           &A.vel[0],  &A.vel[1],  &A.vel[2]};
   for (int k = 0; k < kFields; ++k) *slots[k] = g + k * fstride;
   A.tq = g + kFields * fstride;
   A.tu = g + kFields * fstride + tape_q;
@@ -905,18 +913,12 @@ ic_status ic_snapshot_size(const ic_ctx *ctx, size_t *bytes) {
 ic_status ic_snapshot_save(ic_ctx *ctx, void *dev_buf) {
   if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
   const size_t fb = size_t(ctx->cells) * ctx->real_size, fs = (fb + 15) / 16 * 16, n = size_t(ctx->ps.n);
-  SnapHeader hd{};
-  hd.magic = kSnapMagic;
-  hd.step = ctx->host_step;
-  hd.np = ctx->ps.n;
-  hd.precision = ctx->p.precision;
-  hd.nx = ctx->p.nx;
-  hd.ny = ctx->p.ny;
-  hd.nz = ctx->p.nz;
   char *out = static_cast<char *>(dev_buf);
-  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  IC_CUDA(ctx, cudaMemcpy(out, &hd, sizeof(hd), cudaMemcpyHostToDevice));
-  out += sizeof(hd);
+  // the header by a one-thread kernel: stream-ordered, no host synchronisation
+  k_snapshot_header<<<1, 1, 0, ctx->stream>>>(reinterpret_cast<SnapHeader *>(out), kSnapMagic, ctx->host_step,
+                                              ctx->ps.n, ctx->p.precision, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+  IC_CUDA(ctx, cudaGetLastError());
+  out += sizeof(SnapHeader);
   for (int j = 0; j < 4; ++j, out += fs)
     IC_CUDA(ctx, cudaMemcpyAsync(out, ctx->U[ctx->cur][j], fb, cudaMemcpyDeviceToDevice, ctx->stream));
   if (n) {
@@ -924,19 +926,27 @@ ic_status ic_snapshot_save(ic_ctx *ctx, void *dev_buf) {
     out += (24 * n + 15) / 16 * 16;
     IC_CUDA(ctx, cudaMemcpyAsync(out, ctx->ps.u, 3 * ctx->real_size * n, cudaMemcpyDeviceToDevice, ctx->stream));
   }
+  ctx->snapshots[reinterpret_cast<uintptr_t>(dev_buf)] = {ctx->host_step, ctx->ps.n};
   return IC_OK;
 }
 
 ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf) {
   if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
-  SnapHeader hd{};
-  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  IC_CUDA(ctx, cudaMemcpy(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost));
-  if (hd.magic != kSnapMagic || hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny ||
-      hd.nz != ctx->p.nz || hd.np != ctx->ps.n)
-    return fail(ctx, IC_ERR_ARG, "not a snapshot of this context's grid and particles");
+  int64_t step = 0;
+  const auto known = ctx->snapshots.find(reinterpret_cast<uintptr_t>(dev_buf));
+  if (known != ctx->snapshots.end() && known->second.second == ctx->ps.n) {
+    step = known->second.first;     // saved by this context: its header is known
+  } else {
+    SnapHeader hd{};
+    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    IC_CUDA(ctx, cudaMemcpy(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost));
+    if (hd.magic != kSnapMagic || hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny ||
+        hd.nz != ctx->p.nz || hd.np != ctx->ps.n)
+      return fail(ctx, IC_ERR_ARG, "not a snapshot of this context's grid and particles");
+    step = hd.step;
+  }
   const size_t fb = size_t(ctx->cells) * ctx->real_size, fs = (fb + 15) / 16 * 16, n = size_t(ctx->ps.n);
-  const char *in = static_cast<const char *>(dev_buf) + sizeof(hd);
+  const char *in = static_cast<const char *>(dev_buf) + sizeof(SnapHeader);
   for (int j = 0; j < 4; ++j, in += fs)
     IC_CUDA(ctx, cudaMemcpyAsync(ctx->U[ctx->cur][j], in, fb, cudaMemcpyDeviceToDevice, ctx->stream));
   if (n) {
@@ -945,15 +955,16 @@ ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf) {
     in += (24 * n + 15) / 16 * 16;
     IC_CUDA(ctx, cudaMemcpyAsync(ctx->ps.u, in, 3 * ctx->real_size * n, cudaMemcpyDeviceToDevice, ctx->stream));
   }
-  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  ctx->host_step = hd.step;
+  // step counter (no weights), neighbour-list rebuild and the step's drive, stream-ordered
+  double d[3];
+  ic::drive_amplitudes(ctx, step, d);
+  k_snapshot_restart<<<1, 1, 0, ctx->stream>>>(ctx->d.step, step, ctx->d.rebuild, ctx->drive, ctx->drive_f, d[0],
+                                                d[1], d[2]);
+  IC_CUDA(ctx, cudaGetLastError());
+  ctx->host_step = step;
   ctx->host_wcount = 0;
-  const int64_t steps[3] = {hd.step, hd.step, 0};
-  IC_CUDA(ctx, cudaMemcpy(ctx->d.step, steps, sizeof(steps), cudaMemcpyHostToDevice));
-  const int one = 1;
-  IC_CUDA(ctx, cudaMemcpy(ctx->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice));
   ctx->adj.rec_cur = -1;
-  return upload_drive(ctx, hd.step);
+  return IC_OK;
 }
 
 }  // extern "C"
@@ -1206,15 +1217,15 @@ ic_status ic_profile(ic_ctx *ctx, int enable) {
 ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset) {
   if (!ctx) return IC_ERR_ARG;
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  double acc[3] = {0, 0, 0};
-  int64_t cnt[3] = {0, 0, 0};
+  double acc[IC_PROFILE_CLASSES] = {};
+  int64_t cnt[IC_PROFILE_CLASSES] = {};
   for (const auto &t : ctx->timed) {
     float v = 0.f;
     IC_CUDA(ctx, cudaEventElapsedTime(&v, t.a, t.b));
     acc[t.cls] += v;
     ++cnt[t.cls];
   }
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < IC_PROFILE_CLASSES; ++i) {
     if (ms) ms[i] = acc[i];
     if (launches) launches[i] = cnt[i];
   }

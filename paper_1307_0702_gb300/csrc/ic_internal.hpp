@@ -4,6 +4,8 @@
 
 #include <cstdint>
 #include <string>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/ic.h"
@@ -68,7 +70,7 @@ struct AdjointStore {
   int rec_cur = -1;                    // buffer of U^n of the recorded step (-1: none to reverse)
   int64_t rec_step = 0;
   // grid adjoint fields in the context's precision
-  void *bar[4] = {}, *acc[4] = {}, *vbar[3] = {}, *gpart[3] = {}, *rfbar[3] = {};
+  void *bar[4] = {}, *acc[4] = {}, *vbar[3] = {}, *gpart[3] = {}, *rfbar[3] = {}, *vel[3] = {};
   void *pibar = nullptr, *rhox = nullptr;
   // particle adjoints and gradients (FP64)
   double *qbar = nullptr, *ubar = nullptr, *qhbar = nullptr, *fbar = nullptr, *jvnh = nullptr;
@@ -89,6 +91,7 @@ struct ic_ctx {
   ic::Device d{};
   ic::ParticleStore ps{};
   ic::AdjointStore adj{};
+  std::unordered_map<uintptr_t, std::pair<int64_t, int>> snapshots;   // device snapshots saved: step, particles
   void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
   void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
   bool any_spring = false;  // some particle is tethered: the stage force source is launched
@@ -128,6 +131,30 @@ struct ic_ctx {
 
 namespace ic {
 void *dev_alloc(ic_ctx *ctx, size_t bytes);
+
+// Kernel timing (ic_profile): an event from the context's pool.
+inline cudaEvent_t pooled_event(ic_ctx *ctx) {
+  if (ctx->event_next == ctx->event_pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    ctx->event_pool.push_back(ev);
+  }
+  return ctx->event_pool[ctx->event_next++];
+}
+
+// Launch `fn` and, while profiling, bracket it with events of class `cls`
+// (the classes of ic_profile_read).
+template <typename F>
+cudaError_t timed_launch(ic_ctx *ctx, int cls, F &&fn) {
+  if (!ctx->profiling) return fn();
+  cudaEvent_t a = pooled_event(ctx), b = pooled_event(ctx);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, ctx->stream);
+  const cudaError_t e = fn();
+  cudaEventRecord(b, ctx->stream);
+  ctx->timed.push_back({a, b, cls});
+  return e;
+}
 void dev_free(ic_ctx *ctx, void *p);
 
 // fluid (ic_fluid.cu)

@@ -247,12 +247,15 @@ class Grid:
         """Kernel timing on/off (graphs are off while it is on)."""
         self._check(self._lib.ic_profile(self._ctx, 1 if enable else 0))
 
+    PROFILE_CLASSES = ("fluid", "particles", "end", "adjoint_stage", "adjoint_grid", "adjoint_particles")
+
     def profile_read(self, reset=True):
-        """{class: (ms, launches)} for 'fluid', 'particles', 'end' since the last reset."""
-        ms = np.empty(3)
-        n = (ctypes.c_int64 * 3)()
+        """{class: (ms, launches)} per kernel class (PROFILE_CLASSES) since the last reset."""
+        k = len(self.PROFILE_CLASSES)
+        ms = np.empty(k)
+        n = (ctypes.c_int64 * k)()
         self._check(self._lib.ic_profile_read(self._ctx, _ptr(ms), n, 1 if reset else 0))
-        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("fluid", "particles", "end"))}
+        return {c: (float(ms[i]), int(n[i])) for i, c in enumerate(self.PROFILE_CLASSES)}
 
     def views(self):
         """Zero-copy torch tensors over the current device state (delta rho, g, q)."""

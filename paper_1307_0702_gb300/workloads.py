@@ -189,6 +189,23 @@ def large_box_config(n=128, n_particles=10000):
                                 precision="fp32", place_seed=3)
 
 
+def line_config(n=64, n_particles=16, wave_amp=1e-3, precision="fp64", offset=0.0, k_spring=1.0):
+    """Deterministic box for the differentiable rollout: n^3, n_particles
+    tethered particles evenly spaced on a line along x at y = z = n/2 (every
+    n / n_particles cells from x = 2, all coordinates shifted by ``offset``),
+    m_e = 4 (m_p = 1.5 rho0 V) and kappa_p/kappa_f = 0.5, at rest in the
+    standing-wave eigenmode rho0 + A cos(k x) with the mode drive, kT = 0.
+    Returns (grid params, rho, g, particles)."""
+    gp = grid_params(n, kT=0.0, wave_amp=wave_amp, forcing="mode", precision=precision)
+    rho, g = standing_wave_fields(gp)
+    sp = n / n_particles
+    q = np.stack([2.0 + sp * np.arange(n_particles), np.full(n_particles, n / 2.0),
+                  np.full(n_particles, n / 2.0)], axis=1) + offset
+    parts = dict(q=q, m_e=np.full(n_particles, 4.0), kappa_ratio=np.full(n_particles, 0.5),
+                 k_spring=np.full(n_particles, float(k_spring)), u=np.zeros((n_particles, 3)))
+    return gp, rho, g, parts
+
+
 def ensemble_config(n_boxes=256, sizes=(16, 24, 32, 48), max_particles=200, seed=0):
     """Heterogeneous ensemble: box edges uniform over ``sizes``, 1..max_particles
     particles per box (uniform count, min separation 2h), contrasts of the

@@ -217,16 +217,9 @@ def test_snapshot_round_trip_reproduces_the_steps():
 
 # ---------------------------------------------------------------- the 64^3 rollout
 def line_case(prec, A=1e-3, nsteps=1000, offset=0.0):
-    """64^3, 16 particles evenly spaced on a line along x at y = z = L/2 (every
-    4 cells from x = 2; all three coordinates shifted by `offset`), contrasts
-    m_e = 4 and kappa_p/kappa_f = 0.5, tethers k = 1; the standing-wave
-    eigenmode rho0 + A cos(k x) as start and the mode drive; 1000 steps of
-    unit weight."""
-    gp = W.grid_params(64, kT=0.0, wave_amp=A, forcing="mode", precision=prec)
-    rho, g = W.standing_wave_fields(gp)
-    q = np.stack([2.0 + 4.0 * np.arange(16), np.full(16, 32.0), np.full(16, 32.0)], axis=1) + offset
-    parts = dict(q=q, m_e=np.full(16, 4.0), kappa_ratio=np.full(16, 0.5), k_spring=np.full(16, 1.0),
-                 u=np.zeros((16, 3)))
+    """64^3, 16 tethered particles on a line along x (workloads.line_config),
+    1000 steps of unit weight."""
+    gp, rho, g, parts = W.line_config(64, 16, wave_amp=A, precision=prec, offset=offset)
     return gp, rho, g, parts, np.ones(nsteps)
 
 
