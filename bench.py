@@ -205,7 +205,7 @@ def run_adjoint(args):
     peak, peak_kind = load_peaks()
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
     out = {}
-    for prec in ("fp32", "fp64"):
+    for prec in args.adj_precision:
         gp, rho, g, parts = W.line_config(64, 16, wave_amp=1e-3, precision=prec)
         cells = gp["nx"] * gp["ny"] * gp["nz"]
         grid = Grid(gp)
@@ -262,16 +262,18 @@ def run_adjoint(args):
                                "kernel": "k_adj_stage_rates (3 launches per reversed step)",
                                "alg_flops_per_launch": ALG_ADJ_FLOPS_PER_CELL * cells}
         out[prec] = rec
-    r = out["fp32"]
+    r = out[args.adj_precision[0]]
     line = {
         "metric": ADJOINT_METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": nsteps,
         "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "differentiable rollout: 64^3, 16 tethered particles on a line along x, A=1e-3, "
-                               "kT=0, 1000 steps, checkpoint every 50 (FP32; FP64 in 'fp64')",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.adj_precision[0] == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"differentiable rollout: 64^3, 16 tethered particles on a line along x, A=1e-3, "
+                               f"kT=0, {nsteps} steps, checkpoint every 50 ({args.adj_precision[0]}; "
+                               f"each precision run in its own key)",
                    "l2": "flushed before the timed rollout; the 64^3 state stays L2-resident within it"},
         "roofline": r["roofline"], "gpu_launches": int(round(r["launches_per_step"] * nsteps)),
-        "clocks": r["clocks"], "fp32": r, "fp64": out["fp64"],
+        "clocks": r["clocks"], **out,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = adjoint_cpu_baseline()
@@ -395,6 +397,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=1000)
+    ap.add_argument("--adj-precision", nargs="+", default=["fp32", "fp64"], choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="box", choices=["box", "ensemble", "adjoint"],
                     help="box: the 128^3 single box (default); ensemble: the batched 256-box ensemble")
     ap.add_argument("--boxes", type=int, default=256)
