@@ -41,6 +41,9 @@ ALG_BYTES_PER_CELL_STEP = {"fp32": 128, "fp64": 256}
 # division, logarithm, square root, sine or cosine 1), 580 per cell and step,
 # against the nominal 1.25 TFLOP/s FP64 rate of the part (no measured figure).
 ALG_FP64_FLOPS_PER_CELL_STEP = 580
+# revision of the stage kernels: the ncu traffic in profiles/stage_traffic.json
+# is reported only when it was captured on this revision
+STAGE_KERNEL_REV = "pair-scaled-fluxes"
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -503,7 +506,7 @@ def main():
             tj = json.load(f)
         # ncu DRAM bytes of the same kernel (same precision, size and tile width)
         if (tj.get("precision") == args.precision and tj.get("cells") == cells
-                and tj.get("tile_x") == tiling[0]):
+                and tj.get("tile_x") == tiling[0] and tj.get("kernel_rev") == STAGE_KERNEL_REV):
             traffic = tj.get("bytes_per_launch")
 
     # end-to-end through the public API with host buffers: one step per call,

@@ -117,16 +117,16 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   const auto zwrap = [NZ](int kk) { return kk < 0 ? kk + NZ : (kk >= NZ ? kk - NZ : kk); };
 
   const int64_t step = *a.step;
-  const real drive = c.drive[STAGE];
-  const real rho0 = c.rho0, half = real(0.5), quarter = real(0.25);
-  const real inv_h = c.inv_h, c2 = c.c2, eta = c.eta, lam2 = c.lam2;
-  const real two_eta = real(2) * eta;
-  const real nd = c.noise_diag, nt = c.noise_trace, ne = c.noise_edge;
+  const real four = real(4);
+  const real drive4 = four * c.drive[STAGE];
+  const real rho0 = c.rho0, half = real(0.5);
+  const real c2x4 = c.c2x4, visc_d = c.visc_d, visc_o = c.visc_o, lam2x4_h = c.lam2x4_h;
+  const real out_flux = c.out_flux, out_mass = c.out_mass;
+  const real nd = c.noise_d4, nt = c.noise_t4, ne = c.noise_e4;
   const real beta = STAGE == 0 ? real(-1.7320508075688772) : (STAGE == 1 ? real(1.7320508075688772) : real(0));
   const RngKey key{c.k0, c.k1, c.box};
   const uint32_t ustep = uint32_t(step);
   const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
-  const real dt = c.dt;
   const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
   real mode_acc = real(0);
 
@@ -255,26 +255,30 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     const real gz_yp = Pk[GZ * EXY + eYp], vz_yp = Pk[VZ * EXY + eYp];
     const real vx1_xm = Pq[VX * EXY + eXm], vy1_ym = Pq[VY * EXY + eYm];
 
-    const real div_k = mul_rn(add_rn(add_rn(sub_rn(P.vx, vx_xm), sub_rn(P.vy, vy_ym)), sub_rn(P.vz, vz_m)), inv_h);
-    const real div_k1 = mul_rn(add_rn(add_rn(sub_rn(Q.vx, vx1_xm), sub_rn(Q.vy, vy1_ym)), sub_rn(Q.vz, P.vz)), inv_h);
-    const real pk = add_rn(fma_rn(c2, P.dr, P.pp), mul_rn(drive, profile(k)));
-    const real pk1 = add_rn(fma_rn(c2, Q.dr, Q.pp), mul_rn(drive, profile(k + 1)));
+    // h div v of the planes k and k + 1
+    const real dsum_k = add_rn(add_rn(sub_rn(P.vx, vx_xm), sub_rn(P.vy, vy_ym)), sub_rn(P.vz, vz_m));
+    const real dsum_k1 = add_rn(add_rn(sub_rn(Q.vx, vx1_xm), sub_rn(Q.vy, vy1_ym)), sub_rn(Q.vz, P.vz));
+    // 4 pi = 4 (c^2 delta rho + S Omega + p_ext)
+    const real pk = add_rn(fma_rn(c2x4, P.dr, mul_rn(four, P.pp)), mul_rn(drive4, profile(k)));
+    const real pk1 = add_rn(fma_rn(c2x4, Q.dr, mul_rn(four, Q.pp)), mul_rn(drive4, profile(k + 1)));
+    const real bulk_k = mul_rn(lam2x4_h, dsum_k), bulk_k1 = mul_rn(lam2x4_h, dsum_k1);
 
-    real txx = add_rn(mul_rn(mul_rn(quarter, add_rn(gx_xm, P.gx)), add_rn(vx_xm, P.vx)), pk);
-    txx = sub_rn(txx, fma_rn(mul_rn(two_eta, sub_rn(P.vx, vx_xm)), inv_h, mul_rn(lam2, div_k)));
-    real tyy = add_rn(mul_rn(mul_rn(quarter, add_rn(gy_ym, P.gy)), add_rn(vy_ym, P.vy)), pk);
-    tyy = sub_rn(tyy, fma_rn(mul_rn(two_eta, sub_rn(P.vy, vy_ym)), inv_h, mul_rn(lam2, div_k)));
-    real tzz1 = add_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, Q.gz)), add_rn(P.vz, Q.vz)), pk1);
-    tzz1 = sub_rn(tzz1, fma_rn(mul_rn(two_eta, sub_rn(Q.vz, P.vz)), inv_h, mul_rn(lam2, div_k1)));
-    const real visc_xy = mul_rn(mul_rn(eta, add_rn(sub_rn(vx_yp, P.vx), sub_rn(vy_xp, P.vy))), inv_h);
-    real txy = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gx, gx_yp)), add_rn(P.vy, vy_xp)), visc_xy);
-    real tyx = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gy, gy_xp)), add_rn(P.vx, vx_yp)), visc_xy);
-    const real visc_xz = mul_rn(mul_rn(eta, add_rn(sub_rn(Q.vx, P.vx), sub_rn(vz_xp, P.vz))), inv_h);
-    real txz = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gx, Q.gx)), add_rn(P.vz, vz_xp)), visc_xz);
-    real tzx = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, gz_xp)), add_rn(P.vx, Q.vx)), visc_xz);
-    const real visc_yz = mul_rn(mul_rn(eta, add_rn(sub_rn(Q.vy, P.vy), sub_rn(vz_yp, P.vz))), inv_h);
-    real tyz = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gy, Q.gy)), add_rn(P.vz, vz_yp)), visc_yz);
-    real tzy = sub_rn(mul_rn(mul_rn(quarter, add_rn(P.gz, gz_yp)), add_rn(P.vy, Q.vy)), visc_yz);
+    // the fluxes times 4: products of two-point sums, pressure, minus 4 sigma
+    real txx = add_rn(mul_rn(add_rn(gx_xm, P.gx), add_rn(vx_xm, P.vx)), pk);
+    txx = sub_rn(txx, fma_rn(visc_d, sub_rn(P.vx, vx_xm), bulk_k));
+    real tyy = add_rn(mul_rn(add_rn(gy_ym, P.gy), add_rn(vy_ym, P.vy)), pk);
+    tyy = sub_rn(tyy, fma_rn(visc_d, sub_rn(P.vy, vy_ym), bulk_k));
+    real tzz1 = add_rn(mul_rn(add_rn(P.gz, Q.gz), add_rn(P.vz, Q.vz)), pk1);
+    tzz1 = sub_rn(tzz1, fma_rn(visc_d, sub_rn(Q.vz, P.vz), bulk_k1));
+    const real visc_xy = mul_rn(visc_o, add_rn(sub_rn(vx_yp, P.vx), sub_rn(vy_xp, P.vy)));
+    real txy = sub_rn(mul_rn(add_rn(P.gx, gx_yp), add_rn(P.vy, vy_xp)), visc_xy);
+    real tyx = sub_rn(mul_rn(add_rn(P.gy, gy_xp), add_rn(P.vx, vx_yp)), visc_xy);
+    const real visc_xz = mul_rn(visc_o, add_rn(sub_rn(Q.vx, P.vx), sub_rn(vz_xp, P.vz)));
+    real txz = sub_rn(mul_rn(add_rn(P.gx, Q.gx), add_rn(P.vz, vz_xp)), visc_xz);
+    real tzx = sub_rn(mul_rn(add_rn(P.gz, gz_xp), add_rn(P.vx, Q.vx)), visc_xz);
+    const real visc_yz = mul_rn(visc_o, add_rn(sub_rn(Q.vy, P.vy), sub_rn(vz_yp, P.vz)));
+    real tyz = sub_rn(mul_rn(add_rn(P.gy, Q.gy), add_rn(P.vz, vz_yp)), visc_yz);
+    real tzy = sub_rn(mul_rn(add_rn(P.gz, gz_yp), add_rn(P.vy, Q.vy)), visc_yz);
     if (NOISE) {
       // Sigma_aa = sqrt2 S N_aa + sqrt2 (B - S/3) tr N, Sigma_ab = S N_ab
       const real ntr = mul_rn(nt, add_rn(add_rn(P.nz[0], P.nz[1]), P.nz[2]));
@@ -300,21 +304,18 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     __syncthreads();
 
     if (out_here) {
-      const real neg_inv_h = -inv_h;
-      const real r_rho =
-          mul_rn(add_rn(add_rn(sub_rn(P.gx, gx_xm), sub_rn(P.gy, gy_ym)), sub_rn(P.gz, gz_m)), neg_inv_h);
-      const real r_gx = mul_rn(add_rn(add_rn(sub_rn(T[TXX * EXY + eXp], txx), sub_rn(txy, T[TXY * EXY + eYm])),
-                                      sub_rn(txz, txz_m)),
-                               neg_inv_h);
-      const real r_gy = mul_rn(add_rn(add_rn(sub_rn(T[TYY * EXY + eYp], tyy), sub_rn(tyx, T[TYX * EXY + eXm])),
-                                      sub_rn(tyz, tyz_m)),
-                               neg_inv_h);
-      const real r_gz = mul_rn(add_rn(add_rn(sub_rn(tzz1, tzz_k), sub_rn(tzx, T[TZX * EXY + eXm])),
-                                      sub_rn(tzy, T[TZY * EXY + eYm])),
-                               neg_inv_h);
+      // U_s + dt dU/dt: the mass flux divergence times -dt/h, the summed
+      // differences of the scaled fluxes times -dt/(4h)
+      const real s_rho = add_rn(add_rn(sub_rn(P.gx, gx_xm), sub_rn(P.gy, gy_ym)), sub_rn(P.gz, gz_m));
+      const real s_gx =
+          add_rn(add_rn(sub_rn(T[TXX * EXY + eXp], txx), sub_rn(txy, T[TXY * EXY + eYm])), sub_rn(txz, txz_m));
+      const real s_gy =
+          add_rn(add_rn(sub_rn(T[TYY * EXY + eYp], tyy), sub_rn(tyx, T[TYX * EXY + eXm])), sub_rn(tyz, tyz_m));
+      const real s_gz =
+          add_rn(add_rn(sub_rn(tzz1, tzz_k), sub_rn(tzx, T[TZX * EXY + eXm])), sub_rn(tzy, T[TZY * EXY + eYm]));
       const uint32_t i = i_out;
-      real o0 = fma_rn(dt, r_rho, P.dr), o1 = fma_rn(dt, r_gx, P.gx), o2 = fma_rn(dt, r_gy, P.gy),
-           o3 = fma_rn(dt, r_gz, P.gz);
+      real o0 = fma_rn(s_rho, out_mass, P.dr), o1 = fma_rn(s_gx, out_flux, P.gx),
+           o2 = fma_rn(s_gy, out_flux, P.gy), o3 = fma_rn(s_gz, out_flux, P.gz);
       if (STAGE != 0) {
         o0 = fma_rn(ca, un[0], mul_rn(cb, o0));
         o1 = fma_rn(ca, un[1], mul_rn(cb, o1));
@@ -431,15 +432,15 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
   const auto zwrap = [NZ](int kk) { return kk < 0 ? kk + NZ : (kk >= NZ ? kk - NZ : kk); };
 
   const int64_t step = *a.step;
-  const float drive = c.drive[STAGE];
-  const float2 rho0 = splat2(c.rho0), half = splat2(0.5f), quarter = splat2(0.25f);
-  const float2 inv_h = splat2(c.inv_h), neg_inv_h = splat2(-c.inv_h), c2 = splat2(c.c2);
-  const float2 eta = splat2(c.eta), lam2 = splat2(c.lam2), two_eta = splat2(2.0f * c.eta);
-  const float2 nd = splat2(c.noise_diag), nt = splat2(c.noise_trace), ne = splat2(c.noise_edge);
+  const float drive4 = 4.0f * c.drive[STAGE];
+  const float2 rho0 = splat2(c.rho0), half = splat2(0.5f), four = splat2(4.0f);
+  const float2 c2x4 = splat2(c.c2x4), visc_d = splat2(c.visc_d), visc_o = splat2(c.visc_o);
+  const float2 lam2x4_h = splat2(c.lam2x4_h), out_flux = splat2(c.out_flux), out_mass = splat2(c.out_mass);
+  const float2 nd = splat2(c.noise_d4), nt = splat2(c.noise_t4), ne = splat2(c.noise_e4);
   const float beta = STAGE == 0 ? -1.7320508075688772f : (STAGE == 1 ? 1.7320508075688772f : 0.0f);
   const RngKey key{c.k0, c.k1, c.box};
   const uint32_t ustep = uint32_t(step);
-  const float2 ca = splat2(float(kStageA[STAGE])), cb = splat2(float(kStageB[STAGE])), dt = splat2(c.dt);
+  const float2 ca = splat2(float(kStageA[STAGE])), cb = splat2(float(kStageB[STAGE]));
   const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
   float mode_acc = 0.0f;
 
@@ -523,7 +524,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       P.vx = make_float2(__fdividef(P.gx.x, rfx.x), __fdividef(P.gx.y, rfx.y));
       P.vy = make_float2(__fdividef(P.gy.x, rfy.x), __fdividef(P.gy.y, rfy.y));
       P.vz = make_float2(__fdividef(P.gz.x, rfz.x), __fdividef(P.gz.y, rfz.y));
-      P.pk = add2(fma2(c2, dr, pp), mul2(splat2(drive), make_float2(profile(kk), profile(kk + 1))));
+      // 4 pi = 4 (c^2 delta rho + S Omega + p_ext)
+      P.pk = add2(fma2(c2x4, dr, mul2(four, pp)), mul2(splat2(drive4), make_float2(profile(kk), profile(kk + 1))));
       if (NOISE) {
         float2 w[6];
         if (STAGE == 0) {
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
     Pair2 P = finish2(z0 - 2);
     issue2(z0);
     store_pair(0, P);
-    float gz_m = 0.0f, txz_m = 0.0f, tyz_m = 0.0f, tzz_k = 0.0f, div_k = 0.0f;
+    float gz_m = 0.0f, txz_m = 0.0f, tyz_m = 0.0f, tzz_k = 0.0f, bulk_k = 0.0f;
     int slot = 0;
     for (int k = z0 - 2; k < z1; k += 2, slot ^= 1) {
       // U^n of the output planes
@@ -607,26 +609,28 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       // pairs one plane up: {k+1, k+2}
       const float2 Uvx = up2(P.vx, Q.vx.x), Uvy = up2(P.vy, Q.vy.x), Uvz = up2(P.vz, Q.vz.x);
       const float2 Ugx = up2(P.gx, Q.gx.x), Ugy = up2(P.gy, Q.gy.x), Ugz = up2(P.gz, Q.gz.x);
-      const float2 div_up = mul2(add2(add2(sub2(Uvx, up2(vx_xm, qvx_xm)), sub2(Uvy, up2(vy_ym, qvy_ym))),
-                                      sub2(Uvz, P.vz)),
-                                 inv_h);
-      const float2 div = dn2(div_k, div_up);   // {div(k), div(k+1)}
+      // h div v one plane up, and the bulk-viscous term 4 lam2 div v of both planes
+      const float2 dsum_up = add2(add2(sub2(Uvx, up2(vx_xm, qvx_xm)), sub2(Uvy, up2(vy_ym, qvy_ym))),
+                                  sub2(Uvz, P.vz));
+      const float2 bulk_up = mul2(lam2x4_h, dsum_up);
+      const float2 bulk = dn2(bulk_k, bulk_up);   // {plane k, plane k+1}
 
-      float2 txx = add2(mul2(mul2(quarter, add2(gx_xm, P.gx)), add2(vx_xm, P.vx)), P.pk);
-      txx = sub2(txx, fma2(mul2(two_eta, sub2(P.vx, vx_xm)), inv_h, mul2(lam2, div)));
-      float2 tyy = add2(mul2(mul2(quarter, add2(gy_ym, P.gy)), add2(vy_ym, P.vy)), P.pk);
-      tyy = sub2(tyy, fma2(mul2(two_eta, sub2(P.vy, vy_ym)), inv_h, mul2(lam2, div)));
-      float2 tzz_up = add2(mul2(mul2(quarter, add2(P.gz, Ugz)), add2(P.vz, Uvz)), up2(P.pk, Q.pk.x));
-      tzz_up = sub2(tzz_up, fma2(mul2(two_eta, sub2(Uvz, P.vz)), inv_h, mul2(lam2, div_up)));
-      const float2 visc_xy = mul2(mul2(eta, add2(sub2(vx_yp, P.vx), sub2(vy_xp, P.vy))), inv_h);
-      float2 txy = sub2(mul2(mul2(quarter, add2(P.gx, gx_yp)), add2(P.vy, vy_xp)), visc_xy);
-      float2 tyx = sub2(mul2(mul2(quarter, add2(P.gy, gy_xp)), add2(P.vx, vx_yp)), visc_xy);
-      const float2 visc_xz = mul2(mul2(eta, add2(sub2(Uvx, P.vx), sub2(vz_xp, P.vz))), inv_h);
-      float2 txz = sub2(mul2(mul2(quarter, add2(P.gx, Ugx)), add2(P.vz, vz_xp)), visc_xz);
-      float2 tzx = sub2(mul2(mul2(quarter, add2(P.gz, gz_xp)), add2(P.vx, Uvx)), visc_xz);
-      const float2 visc_yz = mul2(mul2(eta, add2(sub2(Uvy, P.vy), sub2(vz_yp, P.vz))), inv_h);
-      float2 tyz = sub2(mul2(mul2(quarter, add2(P.gy, Ugy)), add2(P.vz, vz_yp)), visc_yz);
-      float2 tzy = sub2(mul2(mul2(quarter, add2(P.gz, gz_yp)), add2(P.vy, Uvy)), visc_yz);
+      // the fluxes times 4: products of two-point sums, pressure, minus 4 sigma
+      float2 txx = add2(mul2(add2(gx_xm, P.gx), add2(vx_xm, P.vx)), P.pk);
+      txx = sub2(txx, fma2(visc_d, sub2(P.vx, vx_xm), bulk));
+      float2 tyy = add2(mul2(add2(gy_ym, P.gy), add2(vy_ym, P.vy)), P.pk);
+      tyy = sub2(tyy, fma2(visc_d, sub2(P.vy, vy_ym), bulk));
+      float2 tzz_up = add2(mul2(add2(P.gz, Ugz), add2(P.vz, Uvz)), up2(P.pk, Q.pk.x));
+      tzz_up = sub2(tzz_up, fma2(visc_d, sub2(Uvz, P.vz), bulk_up));
+      const float2 visc_xy = mul2(visc_o, add2(sub2(vx_yp, P.vx), sub2(vy_xp, P.vy)));
+      float2 txy = sub2(mul2(add2(P.gx, gx_yp), add2(P.vy, vy_xp)), visc_xy);
+      float2 tyx = sub2(mul2(add2(P.gy, gy_xp), add2(P.vx, vx_yp)), visc_xy);
+      const float2 visc_xz = mul2(visc_o, add2(sub2(Uvx, P.vx), sub2(vz_xp, P.vz)));
+      float2 txz = sub2(mul2(add2(P.gx, Ugx), add2(P.vz, vz_xp)), visc_xz);
+      float2 tzx = sub2(mul2(add2(P.gz, gz_xp), add2(P.vx, Uvx)), visc_xz);
+      const float2 visc_yz = mul2(visc_o, add2(sub2(Uvy, P.vy), sub2(vz_yp, P.vz)));
+      float2 tyz = sub2(mul2(add2(P.gy, Ugy), add2(P.vz, vz_yp)), visc_yz);
+      float2 tzy = sub2(mul2(add2(P.gz, gz_yp), add2(P.vy, Uvy)), visc_yz);
       if (NOISE) {
         txx = sub2(txx, P.s[0]);
         tyy = sub2(tyy, P.s[1]);
@@ -647,18 +651,17 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       __syncthreads();
 
       if (out0 || out1) {
-        const float2 r_rho =
-            mul2(add2(add2(sub2(P.gx, gx_xm), sub2(P.gy, gy_ym)), sub2(P.gz, dn2(gz_m, P.gz))), neg_inv_h);
-        const float2 r_gx = mul2(add2(add2(sub2(T[TXX * EXY + eXp], txx), sub2(txy, T[TXY * EXY + eYm])),
-                                      sub2(txz, dn2(txz_m, txz))),
-                                 neg_inv_h);
-        const float2 r_gy = mul2(add2(add2(sub2(T[TYY * EXY + eYp], tyy), sub2(tyx, T[TYX * EXY + eXm])),
-                                      sub2(tyz, dn2(tyz_m, tyz))),
-                                 neg_inv_h);
-        const float2 r_gz = mul2(add2(add2(sub2(tzz_up, dn2(tzz_k, tzz_up)), sub2(tzx, T[TZX * EXY + eXm])),
-                                      sub2(tzy, T[TZY * EXY + eYm])),
-                                 neg_inv_h);
-        float2 o[4] = {fma2(dt, r_rho, P.dr), fma2(dt, r_gx, P.gx), fma2(dt, r_gy, P.gy), fma2(dt, r_gz, P.gz)};
+        // U_s + dt dU/dt: the mass flux divergence times -dt/h, the summed
+        // differences of the scaled fluxes times -dt/(4h)
+        const float2 s_rho = add2(add2(sub2(P.gx, gx_xm), sub2(P.gy, gy_ym)), sub2(P.gz, dn2(gz_m, P.gz)));
+        const float2 s_gx = add2(add2(sub2(T[TXX * EXY + eXp], txx), sub2(txy, T[TXY * EXY + eYm])),
+                                 sub2(txz, dn2(txz_m, txz)));
+        const float2 s_gy = add2(add2(sub2(T[TYY * EXY + eYp], tyy), sub2(tyx, T[TYX * EXY + eXm])),
+                                 sub2(tyz, dn2(tyz_m, tyz)));
+        const float2 s_gz = add2(add2(sub2(tzz_up, dn2(tzz_k, tzz_up)), sub2(tzx, T[TZX * EXY + eXm])),
+                                 sub2(tzy, T[TZY * EXY + eYm]));
+        float2 o[4] = {fma2(s_rho, out_mass, P.dr), fma2(s_gx, out_flux, P.gx), fma2(s_gy, out_flux, P.gy),
+                       fma2(s_gz, out_flux, P.gz)};
         if (STAGE != 0) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) o[j] = fma2(ca, un[j], mul2(cb, o[j]));
@@ -677,7 +680,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       txz_m = txz.y;
       tyz_m = tyz.y;
       tzz_k = tzz_up.y;
-      div_k = div_up.y;
+      bulk_k = bulk_up.y;
       P = Q;
     }
   }
@@ -700,38 +703,10 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
 
 template <typename real>
 FluidConsts<real> fluid_consts(const ic_ctx *ctx) {
-  const ic_grid_params &p = ctx->p;
-  FluidConsts<real> c{};
-  c.nx = p.nx;
-  c.ny = p.ny;
-  c.nz = p.nz;
-  c.rho0 = real(p.rho0);
-  c.c2 = real(p.c * p.c);
-  c.inv_h = real(1.0 / p.h);
-  c.dt = real(p.dt);
-  c.eta = real(p.eta);
-  c.lam2 = real(p.zeta - 2.0 * p.eta / 3.0);
-  const double vol_dt = p.h * p.h * p.h * p.dt;
-  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
-  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
-  c.noise_diag = real(std::sqrt(2.0) * S);
-  c.noise_trace = real(std::sqrt(2.0) * (B - S / 3.0));
-  c.noise_edge = real(S);
-  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
-  c.wave_axis = p.wave_axis;
-  c.plane_index = p.plane_index;
-  if constexpr (sizeof(real) == 4) {
-    c.cos_table = ctx->cos_table_f;
-    c.drive = ctx->drive_f;
-  } else {
-    c.cos_table = ctx->cos_table;
-    c.drive = ctx->drive;
-  }
-  c.k0 = uint32_t(p.seed & 0xffffffffull);
-  c.k1 = uint32_t(p.seed >> 32);
-  c.box = p.box;
-  c.noise = p.kT > 0.0;
-  return c;
+  if constexpr (sizeof(real) == 4)
+    return make_fluid_consts<float>(ctx->p, ctx->cos_table_f, ctx->drive_f);
+  else
+    return make_fluid_consts<double>(ctx->p, ctx->cos_table, ctx->drive);
 }
 
 // Tile shapes of the stage kernel: variant 0 is the wide tile tuned for large

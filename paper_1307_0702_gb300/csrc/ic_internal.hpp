@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <unordered_map>
@@ -25,12 +26,61 @@ struct FluidConsts {
   int nx, ny, nz;
   real rho0, c2, inv_h, dt, eta, lam2;        // lam2 = zeta - 2 eta / 3
   real noise_diag, noise_trace, noise_edge;   // sqrt2 S, sqrt2 (B - S/3), S
+  // The stage kernels carry the momentum fluxes scaled by 4 (so that the
+  // advective products of two-point sums need no factor 1/4) and fold 1/h and
+  // dt into these constants:
+  real c2x4;                                  // 4 c^2
+  real visc_d, visc_o;                        // 8 eta / h (diagonal), 4 eta / h (edges)
+  real lam2x4_h;                              // 4 lam2 / h
+  real noise_d4, noise_t4, noise_e4;          // 4 x the noise coefficients
+  real out_flux, out_mass;                    // -dt / (4 h), -dt / h
   int forcing, wave_axis, plane_index;
   const real *cos_table;                      // cos(k x_i) along the wave axis
   const real *drive;                          // drive amplitude of each RK stage of the current step
   uint32_t k0, k1, box;                       // Philox key and box
   int noise;
 };
+
+// The constants of a grid, derived in FP64 and rounded once to real.
+template <typename real>
+FluidConsts<real> make_fluid_consts(const ic_grid_params &p, const real *cos_table, const real *drive) {
+  FluidConsts<real> c{};
+  c.nx = p.nx;
+  c.ny = p.ny;
+  c.nz = p.nz;
+  c.rho0 = real(p.rho0);
+  c.c2 = real(p.c * p.c);
+  c.inv_h = real(1.0 / p.h);
+  c.dt = real(p.dt);
+  c.eta = real(p.eta);
+  const double lam2 = p.zeta - 2.0 * p.eta / 3.0;
+  c.lam2 = real(lam2);
+  const double vol_dt = p.h * p.h * p.h * p.dt;
+  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
+  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
+  c.noise_diag = real(std::sqrt(2.0) * S);
+  c.noise_trace = real(std::sqrt(2.0) * (B - S / 3.0));
+  c.noise_edge = real(S);
+  c.c2x4 = real(4.0 * p.c * p.c);
+  c.visc_d = real(8.0 * p.eta / p.h);
+  c.visc_o = real(4.0 * p.eta / p.h);
+  c.lam2x4_h = real(4.0 * lam2 / p.h);
+  c.noise_d4 = real(4.0 * std::sqrt(2.0) * S);
+  c.noise_t4 = real(4.0 * std::sqrt(2.0) * (B - S / 3.0));
+  c.noise_e4 = real(4.0 * S);
+  c.out_flux = real(-p.dt / (4.0 * p.h));
+  c.out_mass = real(-p.dt / p.h);
+  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
+  c.wave_axis = p.wave_axis;
+  c.plane_index = p.plane_index;
+  c.cos_table = cos_table;
+  c.drive = drive;
+  c.k0 = uint32_t(p.seed & 0xffffffffull);
+  c.k1 = uint32_t(p.seed >> 32);
+  c.box = p.box;
+  c.noise = p.kT > 0.0;
+  return c;
+}
 
 // Device pointers of the particle arrays; element type of the void* arrays
 // is the context's real type (double or float).

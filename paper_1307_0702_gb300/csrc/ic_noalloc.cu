@@ -59,32 +59,7 @@ __global__ void k_noalloc_tables(int64_t *step_out, int64_t step, real *drive, r
 
 template <typename real>
 ic::FluidConsts<real> consts_from(const ic_grid_params &p, const real *cos_table, const real *drive) {
-  ic::FluidConsts<real> c{};
-  c.nx = p.nx;
-  c.ny = p.ny;
-  c.nz = p.nz;
-  c.rho0 = real(p.rho0);
-  c.c2 = real(p.c * p.c);
-  c.inv_h = real(1.0 / p.h);
-  c.dt = real(p.dt);
-  c.eta = real(p.eta);
-  c.lam2 = real(p.zeta - 2.0 * p.eta / 3.0);
-  const double vol_dt = p.h * p.h * p.h * p.dt;
-  const double S = std::sqrt(2.0 * p.eta * p.kT / vol_dt);
-  const double B = std::sqrt(p.zeta * p.kT / (3.0 * vol_dt));
-  c.noise_diag = real(std::sqrt(2.0) * S);
-  c.noise_trace = real(std::sqrt(2.0) * (B - S / 3.0));
-  c.noise_edge = real(S);
-  c.forcing = (p.wave_amp == 0.0) ? IC_FORCE_NONE : p.forcing;
-  c.wave_axis = p.wave_axis;
-  c.plane_index = p.plane_index;
-  c.cos_table = cos_table;
-  c.drive = drive;
-  c.k0 = uint32_t(p.seed & 0xffffffffull);
-  c.k1 = uint32_t(p.seed >> 32);
-  c.box = p.box;
-  c.noise = p.kT > 0.0;
-  return c;
+  return ic::make_fluid_consts<real>(p, cos_table, drive);
 }
 
 template <typename real>
