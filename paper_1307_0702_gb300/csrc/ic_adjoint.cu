@@ -19,9 +19,10 @@
 // whose derivative is written out in dpeskin3 below.
 //
 // Grid kernels are one thread per cell and gather every term they need, so
-// they write each output once.  Particle kernels are one thread per particle
-// and spread with atomic adds (the adjoint is therefore reproducible to
-// rounding, not bit for bit).  The grid adjoint fields are in the context's
+// they write each output once.  Particle kernels are one warp per particle
+// (lane t < 27 holds stencil point t; sums by warp reduction) and spread
+// with atomic adds (the adjoint is therefore reproducible to rounding, not
+// bit for bit).  The grid adjoint fields are in the context's
 // precision; the particle adjoints and the gradients are FP64.
 #include <cuda_runtime.h>
 
