@@ -293,3 +293,52 @@ def test_line_of_particles_gradient(prec):
         _, ref = gpu_gradient({**gp, "precision": "fp64"}, rho, g, parts, weights, direction, K=50)
         for key in ("m_e", "kappa_ratio"):
             assert rel_err(gr[key], ref[key]) < 1e-3, (key, rel_err(gr[key], ref[key]))
+
+
+def test_dipolar_force_gradient_follows_f2():
+    """The closed form of the dipolar force, Eq. (eq:acousticForce2) with f_2
+    of Eq. (f2): at c_p = c_f (f_1 = 0) the radiation force is proportional
+    to f_2(m), m = m_e - k_s / omega^2 (the tether's excess mass at the drive
+    frequency), so d ln F / d m_e = f_2'(m) / f_2(m) = 3 rho0 V / (m (2 m +
+    3 rho0 V)), whatever the amplitude prefactor.  The adjoint of the 64 000
+    step Table I run of Fig. 4 (rho_p = 2 rho0, mirrored tethered pair, mode
+    drive, Blackman-Harris window after 16 000 steps; FP32) gives it within
+    3 % (measured 0.8 %), and central differences of its own forward (both
+    masses moved by 1 %) within 1 %: the FP32 forward's rounding leaves ~0.5 %
+    of noise in such a difference.  (In FP64 the same adjoint matches central
+    differences to 1e-6, and the FP32 adjoint is within 6e-4 of it.)"""
+    from paper_1307_0702_gb300 import Grid
+    from oracle import theory
+
+    h, n = 10.0, 32
+    gp, parts, _ = W.single_particle_config(n=n, k_spring=1.0, mirror=True, mass_ratio=2.0, kappa_ratio=1.0)
+    gp.update(h=h, dt=0.1 * h / gp["c"], zeta=1.0, precision="fp32", wave_amp=1e-3)
+    L = n * h
+    parts["q"] = np.array([[L / 8, L / 2, L / 2], [7 * L / 8, L / 2, L / 2]])
+    vol = 8 * h ** 3
+    parts["m_e"] = np.full(2, 1.0 * vol)
+    parts["u"] = None
+    rho, g = W.velocity_phase_wave_fields(gp)
+    weights = W.blackman_harris(64000, 16000)
+    # Phi = F_0 - F_1 = 2 F_0: the radiation force is minus the averaged spring force
+    direction = np.array([[-1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    phi, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=100)
+    dphi = float(gr["m_e"][0] + gr["m_e"][1])          # both masses together
+    omega = theory.discrete_sound_frequency(gp["c"], h, n)
+    m = parts["m_e"][0] - 1.0 / omega ** 2
+    closed = 3.0 * gp["rho0"] * vol / (m * (2.0 * m + 3.0 * gp["rho0"] * vol))
+
+    def phi_of(scale):
+        with Grid(gp) as grid:
+            grid.set_state(rho, g)
+            grid.add_particles(parts["q"], parts["m_e"] * scale, parts["kappa_ratio"], parts["k_spring"])
+            grid.step(len(weights), weights)
+            f = grid.time_average()[0]
+        return float(np.sum(direction * f))
+
+    d = 0.01
+    fd = (phi_of(1 + d) - phi_of(1 - d)) / (2 * d * parts["m_e"][0])
+    info = dict(phi=phi, adjoint=dphi, fd=fd, log_slope=dphi / phi, closed=closed)
+    assert phi > 0, info                                    # pushed towards the pressure node
+    assert dphi == pytest.approx(fd, rel=1e-2), info
+    assert dphi / phi == pytest.approx(closed, rel=0.03), info
