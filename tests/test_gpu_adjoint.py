@@ -342,3 +342,68 @@ def test_dipolar_force_gradient_follows_f2():
     assert phi > 0, info                                    # pushed towards the pressure node
     assert dphi == pytest.approx(fd, rel=1e-2), info
     assert dphi / phi == pytest.approx(closed, rel=0.03), info
+
+
+@pytest.mark.parametrize("case_id", range(8))
+def test_adjoint_random_configurations(case_id):
+    """Seeded random cases against the oracle's adjoint: edges 6-20, both
+    precisions, every drive (or none) along any axis, 1-6 particles anywhere
+    (overlapping, on the seam), tethered or free, random objective directions
+    and checkpoint intervals."""
+    rng = np.random.default_rng(500 + case_id)
+    shape = tuple(int(x) for x in rng.integers(6, 21, 3))
+    prec = ["fp64", "fp32"][case_id % 2]
+    forcing = ["none", "mode", "plane"][int(rng.integers(3))]
+    axis = int(rng.integers(3))
+    gp = W.grid_params(shape, kT=0.0, wave_amp=float(rng.uniform(1e-3, 5e-3)), forcing=forcing, wave_axis=axis,
+                       plane_index=int(rng.integers(shape[axis])), zeta=float(rng.uniform(0.0, 1.0)),
+                       precision=prec, wave_phase=float(rng.uniform(0, 6.3)))
+    npart = int(rng.integers(1, 7))
+    L = np.array(shape, dtype=float)
+    q = rng.uniform(0.0, 1.0, (npart, 3)) * L
+    if npart > 1:
+        q[1] = (q[0] + rng.uniform(-1.0, 1.0, 3)) % L
+    if npart > 2:
+        q[2, 1] = L[1] - 0.05
+    parts = dict(q=q, m_e=rng.uniform(-2.0, 8.0, npart), kappa_ratio=rng.uniform(0.3, 2.0, npart),
+                 k_spring=np.where(rng.uniform(size=npart) < 0.7, rng.uniform(0.1, 1.0, npart), 0.0),
+                 u=2e-3 * rng.normal(size=(npart, 3)))
+    parts["k_spring"][0] = 0.5                               # at least one tether: a non-zero objective
+    rho, g = W.random_fields(gp, seed=case_id, amp_rho=3e-3, amp_g=3e-3)
+    nsteps = int(rng.integers(3, 9))
+    weights = rng.uniform(0.2, 1.0, nsteps)
+    direction = rng.normal(size=(npart, 3))
+    K = int(rng.integers(1, nsteps + 1))
+    phi, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=K)
+    ophi, orc = oracle_gradient(gp, rho, g, parts, weights, direction)
+    assert abs(phi - ophi) <= (1e-11 if prec == "fp64" else 1e-4) * abs(ophi)
+    errs = compare(gr, orc) if forcing != "none" else {k: v for k, v in compare(gr, {**orc, "A": 1.0}).items()
+                                                        if k != "A"}
+    bad = {k: v for k, v in errs.items() if not v <= TOL[prec]}
+    assert not bad, (shape, prec, forcing, npart, nsteps, K, errs)
+    if forcing == "none":
+        assert gr["A"] == 0.0
+
+
+def test_rollout_without_particles():
+    """No particles: the objective and every gradient vanish, and the calls
+    run (nothing to spread or gather)."""
+    from paper_1307_0702_gb300 import Grid
+    from paper_1307_0702_gb300.adjoint import Rollout
+
+    gp = W.grid_params((10, 8, 9), kT=0.0, wave_amp=2e-3, forcing="mode", precision="fp64")
+    rho, g = W.random_fields(gp, seed=1)
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.adjoint_enable()
+        grid.adjoint_reset()
+        snap = grid.new_snapshot()
+        grid.snapshot_save(snap)
+        grid.step(2)
+        grid.snapshot_load(snap)
+        grid.step_record()
+        grid.adjoint_step(1.0)
+        out = grid.adjoint_read()
+    assert out["A"] == 0.0
+    assert not np.any(out["rho"]) and not any(np.any(x) for x in out["g"])
+    assert out["m_e"].shape == (0,)
