@@ -22,6 +22,10 @@ ic      : the full IC time step, substeps 1-7 of App. A.2, with the particle
 slabs   : the same step with the box split into z-slabs over ranks (halo
           exchange, owner-computed particle gathers, replicated spreads),
           pinned bit for bit to ``ic`` over gloo ranks.
+adjoint : the reverse-mode derivative (transpose) of the deterministic step,
+          for gradients of the time-averaged tether force (Sec. 6) with
+          respect to m_e, kappa_p/kappa_f, the drive amplitude and the state;
+          pinned by complex-step and central differences of the forward.
 theory  : closed forms used as pins (Eqs. (eq:acousticForce2), (f1), (f2),
           (part_svel), (ke), (eq:densityVariance); discrete dispersion).
 
