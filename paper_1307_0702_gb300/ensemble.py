@@ -1,5 +1,8 @@
 """Ensembles of independent boxes spread over ranks (one box per GPU).
 
+The gradients of a differentiable rollout (one box per rank) are combined
+the same way at the end, by ``ensemble_gradient``.
+
 The IC step of one box needs no communication: every rank advances its own
 box (its own Philox ``box`` id) and the only exchange is at the end, where the
 weighted sums behind the time averages (sum_n w_n F_n, sum_n w_n lambda_n,
@@ -46,3 +49,30 @@ def ensemble_force(ens):
 def ensemble_a2(ens):
     """Ensemble mean of <A^2>_w."""
     return ens["sa2"] / ens["sw"]
+
+
+def ensemble_gradient(phi, grad, group=None):
+    """Combine the rollout gradients of one box per rank (``Rollout.backward``
+    or the oracle's) for the ensemble objective Phi_ens = sum over boxes of
+    each box's Phi.
+
+    phi: this rank's Phi; grad: dict with m_e, kappa_ratio (n,) and A.
+    Returns, identically on every rank, {"phi": sum of Phi, "m_e",
+    "kappa_ratio": per-particle gradients of all boxes stacked in rank order
+    (a particle belongs to one box), "A": summed over boxes (a drive
+    amplitude shared by the ensemble), "boxes": ranks}.
+    """
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    mine = {"phi": float(phi), "A": float(grad["A"]),
+            "m_e": np.ascontiguousarray(grad["m_e"], dtype=np.float64).reshape(-1),
+            "kappa_ratio": np.ascontiguousarray(grad["kappa_ratio"], dtype=np.float64).reshape(-1)}
+    if world > 1:
+        parts = [None] * world
+        dist.all_gather_object(parts, mine, group=group)
+    else:
+        parts = [mine]
+    return {"phi": float(sum(p["phi"] for p in parts)), "A": float(sum(p["A"] for p in parts)),
+            "m_e": np.concatenate([p["m_e"] for p in parts]),
+            "kappa_ratio": np.concatenate([p["kappa_ratio"] for p in parts]), "boxes": world}
