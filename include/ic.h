@@ -189,7 +189,7 @@ void ic_batch_destroy(ic_batch *batch);
 /* Stage-kernel tiling.  The paper has no counterpart: this is a performance
  * setting.  The RK3 stage kernel marches CTAs of tile_x x tile_y cells along
  * z in runs of at least zchunk planes; tile_x is 32 or 16 (tile_y follows:
- * 12 or 8 in FP32, 4 in FP64).  Every field, particle and force is bit
+ * 13 or 8 in FP32, 4 in FP64).  Every field, particle and force is bit
  * for bit the same under every tiling; only the driven-mode amplitude A(t)
  * and <A^2>_w change, by the rounding of their reduction order.
  * ic_set_tile: IC_ERR_ARG for tile_x not 16 or 32, or zchunk < 8 (unless it is

@@ -86,7 +86,7 @@ constexpr double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
 // Tile height of the FP32 (pair) stage kernel and register budget of the
 // scalar one, tuned on GB300.
 #ifndef IC_FP32_TILE_Y
-#define IC_FP32_TILE_Y 12
+#define IC_FP32_TILE_Y 13
 #endif
 #ifndef IC_FP32_MIN_CTAS
 #define IC_FP32_MIN_CTAS 2
