@@ -285,6 +285,21 @@ ic_status ic_adjoint_step(ic_ctx *ctx, double weight);
 ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, double *grad_A, double *rho_bar,
                           double *gx_bar, double *gy_bar, double *gz_bar, double *q_bar, double *u_bar);
 
+/* Step tapes: ic_step_record_tape runs ic_step_record and copies everything
+ * the reverse sweep of that step reads (U^n, the first two RK stages, the
+ * momenta before substep 6, U^{n+1}, and q^n, q^{n+1/2}, u^n, F, dg) into a
+ * caller-owned device buffer of ic_tape_size bytes, 16-byte aligned
+ * (IC_ERR_ARG otherwise); ic_adjoint_step_tape reverses the step of such a
+ * tape, as ic_adjoint_step does for the step recorded last, whatever the
+ * state has done since.  A rollout can so record a whole segment and then
+ * reverse it without recomputing its steps.  A tape recorded by this
+ * context is reversed without synchronising; one from elsewhere has its
+ * header read back and checked (IC_ERR_ARG if it is of another grid,
+ * precision or particle count). */
+ic_status ic_tape_size(const ic_ctx *ctx, size_t *bytes);
+ic_status ic_step_record_tape(ic_ctx *ctx, void *dev_buf);
+ic_status ic_adjoint_step_tape(ic_ctx *ctx, const void *dev_buf, double weight);
+
 /* Device snapshots of the state a rollout needs to restart a step (fields,
  * q, u, step counter): the caller owns dev_buf, device memory of
  * ic_snapshot_size bytes, 16-byte aligned (IC_ERR_ARG otherwise).  Save

@@ -65,6 +65,9 @@ SIGNATURES = {
     "ic_step_record": (c_int, [c_void_p]),
     "ic_adjoint_step": (c_int, [c_void_p, c_double]),
     "ic_adjoint_read": (c_int, [c_void_p, PD, PD, PD, PD, PD, PD, PD, PD, PD]),
+    "ic_tape_size": (c_int, [c_void_p, POINTER(c_size_t)]),
+    "ic_step_record_tape": (c_int, [c_void_p, c_void_p]),
+    "ic_adjoint_step_tape": (c_int, [c_void_p, c_void_p, c_double]),
     "ic_snapshot_size": (c_int, [c_void_p, POINTER(c_size_t)]),
     "ic_snapshot_save": (c_int, [c_void_p, c_void_p]),
     "ic_snapshot_load": (c_int, [c_void_p, c_void_p]),

@@ -10,9 +10,13 @@ square of the wave amplitude.  ``Rollout`` runs N deterministic steps of a
 
 and ``Rollout.backward`` its gradient with respect to every particle's m_e
 and kappa_p/kappa_f, the drive amplitude and the initial state, by the
-library's adjoint kernels (ic_step_record / ic_adjoint_step): states are kept
-on the device every ``checkpoint_every`` steps, and each segment is recomputed
-forward (one snapshot per step) before its steps are reversed, last first.
+library's adjoint kernels: states are kept on the device every
+``checkpoint_every`` steps; each segment is then run forward again from its
+checkpoint, every step recording its tape (ic_step_record_tape), and the
+tapes are reversed last first (ic_adjoint_step_tape).  With ``tapes=False``
+the segment keeps one snapshot per step instead, and each step is recorded
+again just before it is reversed (a third forward pass, K snapshots instead
+of K tapes of ~19 fields).
 
 ``time_averaged_force`` wraps it as a torch.autograd.Function.
 """
@@ -28,7 +32,7 @@ class Rollout:
     particles' kappa_p/kappa_f (n,), for the chain rule from epsilon_pf.
     """
 
-    def __init__(self, grid, kappa_ratio, checkpoint_every=50):
+    def __init__(self, grid, kappa_ratio, checkpoint_every=50, tapes=True):
         if grid.params.get("kT", 0.0) != 0.0:
             raise ValueError("the adjoint covers the deterministic step (kT = 0)")
         self.grid = grid
@@ -36,6 +40,7 @@ class Rollout:
         self.K = int(checkpoint_every)
         if self.K < 1:
             raise ValueError("checkpoint_every must be >= 1")
+        self.tapes = bool(tapes)
         self.checkpoints = []
         self.weights = None
         grid.adjoint_enable()
@@ -72,6 +77,17 @@ class Rollout:
         n = len(self.weights)
         W = float(np.sum(self.weights))
         g.adjoint_reset(self.direction)
+        if self.tapes:
+            tapes = [g.new_tape() for _ in range(min(self.K, n))]
+            for seg in range(len(self.checkpoints) - 1, -1, -1):
+                start = seg * self.K
+                stop = min(start + self.K, n)
+                g.snapshot_load(self.checkpoints[seg])
+                for j in range(stop - start):
+                    g.step_record_tape(tapes[j])
+                for j in range(stop - start - 1, -1, -1):
+                    g.adjoint_step_tape(tapes[j], self.weights[start + j] / W)
+            return self._read()
         pool = [g.new_snapshot() for _ in range(min(self.K, n) - 1)]
         for seg in range(len(self.checkpoints) - 1, -1, -1):
             start = seg * self.K
@@ -86,6 +102,10 @@ class Rollout:
                 g.snapshot_load(states[j])
                 g.step_record()
                 g.adjoint_step(self.weights[start + j] / W)
+        return self._read()
+
+    def _read(self):
+        g = self.grid
         out = g.adjoint_read()
         c2 = float(g.params["c"]) ** 2
         out["kappa_ratio"] = out["eps"] * (-c2 / self.kappa ** 2)

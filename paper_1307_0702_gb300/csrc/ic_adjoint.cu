@@ -397,20 +397,20 @@ struct AdjParticles {
 };
 
 template <typename real>
-AdjParticles<real> adj_particles(const ic_ctx *ctx) {
+AdjParticles<real> adj_particles(const ic_ctx *ctx, const AdjStepTape &t) {
   using T = typename Pos<real>::T;
   const ParticleStore &s = ctx->ps;
   const AdjointStore &A = ctx->adj;
   AdjParticles<real> P;
   P.n = s.n;
-  P.q_half = (const T *)s.q_half;
-  P.q_n = (const T *)A.tq;
-  P.u_n = (const real *)A.tu;
+  P.q_half = (const T *)t.q_half;
+  P.q_n = (const T *)t.q_n;
+  P.u_n = (const real *)t.u_n;
   P.m_e = (const real *)s.m_e;
   P.eps = (const real *)s.eps;
   P.k_s = (const real *)s.k_s;
-  P.force = (const real *)s.force;
-  P.dg = (const real *)s.dg;
+  P.force = (const real *)t.force;
+  P.dg = (const real *)t.dg;
   P.qbar = A.qbar;
   P.ubar = A.ubar;
   P.qhbar = A.qhbar;
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_start(AdjParticle
 
 // ---------------------------------------------------------------- host
 template <typename real>
-cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
+cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
   AdjointStore &A = ctx->adj;
   const ic_grid_params &p = ctx->p;
   const Geo G{p.nx, p.ny, p.nz};
@@ -626,7 +626,7 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
   const int n = ctx->ps.n;
   constexpr int kParticlesPerBlock = kAdjParticleThreads / 32;
   const int pblocks = (n + kParticlesPerBlock - 1) / kParticlesPerBlock;
-  const AdjParticles<real> P = adj_particles<real>(ctx);
+  const AdjParticles<real> P = adj_particles<real>(ctx, t);
   real *bar[4], *acc[4], *gp[3], *rf[3], *vel[3];
   Fields3<real> vb;
   for (int j = 0; j < 4; ++j) {
@@ -641,10 +641,10 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
   }
   real *pibar = static_cast<real *>(A.pibar), *rhox = static_cast<real *>(A.rhox);
   // the recorded step's states
-  void *const *Un = ctx->U[A.rec_cur];
-  void *const *Unew = ctx->U[1 - A.rec_cur];
-  void *const U3v[4] = {Unew[0], A.tG3[0], A.tG3[1], A.tG3[2]};
-  void *const *Ustage[3] = {Un, A.tU1, ctx->U[2]};
+  void *const *Un = t.Un;
+  void *const *Unew = t.Unew;
+  void *const U3v[4] = {Unew[0], t.G3[0], t.G3[1], t.G3[2]};
+  void *const *Ustage[3] = {t.Un, t.U1, t.U2};
   const real rho0 = real(p.rho0);
   auto vt = [&](void *const *U) {
     cudaError_t e = timed_launch(ctx, kClassGrid, [&] {
@@ -688,7 +688,7 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
     k.forcing = p.forcing;
     k.wave_axis = p.wave_axis;
     k.plane_index = p.plane_index;
-    k.dpdA = per_A * std::sin(ctx->omega * (double(A.rec_step) + kStageTimes[s]) * p.dt + p.wave_phase);
+    k.dpdA = per_A * std::sin(ctx->omega * (double(t.step) + kStageTimes[s]) * p.dt + p.wave_phase);
     const State<real> Us = state_of<real>(Ustage[s]);
     StageIn<real> In;
     for (int j = 0; j < 4; ++j) In.lam[j] = bar[j];
@@ -731,9 +731,9 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, double weight) {
 
 }  // namespace
 
-cudaError_t launch_adjoint_step(ic_ctx *ctx, double weight) {
-  if (ctx->p.precision == IC_FP32) return adjoint_step_t<float>(ctx, weight);
-  return adjoint_step_t<double>(ctx, weight);
+cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight) {
+  if (ctx->p.precision == IC_FP32) return adjoint_step_t<float>(ctx, t, weight);
+  return adjoint_step_t<double>(ctx, t, weight);
 }
 
 }  // namespace ic

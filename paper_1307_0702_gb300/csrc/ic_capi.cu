@@ -795,6 +795,93 @@ __global__ void k_snapshot_restart(int64_t *step, int64_t n, int *rebuild, doubl
   drive_f[2] = float(d2);
 }
 
+constexpr uint64_t kTapeMagic = 0x31504154434943ull;   // "ICTAP1"
+
+// Up to kMaxCopies device-to-device copies in one launch (lengths multiples
+// of 4 bytes, addresses 4-byte aligned): block y takes copy y, its threads
+// stride over the 4-byte words, 16 bytes at a time where both ends allow.
+constexpr int kMaxCopies = 32;
+struct CopyList {
+  const char *src[kMaxCopies];
+  char *dst[kMaxCopies];
+  size_t len[kMaxCopies];
+  int n;
+};
+
+__global__ void k_copy_list(CopyList L) {
+  const int c = blockIdx.y;
+  if (c >= L.n) return;
+  const char *src = L.src[c];
+  char *dst = L.dst[c];
+  const size_t len = L.len[c];
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  const size_t t0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  size_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const size_t n16 = len / 16;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (size_t i = t0; i < n16; i += stride) d4[i] = s4[i];
+    done = n16 * 16;
+  }
+  const size_t n4 = (len - done) / 4;
+  const uint32_t *s1 = reinterpret_cast<const uint32_t *>(src + done);
+  uint32_t *d1 = reinterpret_cast<uint32_t *>(dst + done);
+  for (size_t i = t0; i < n4; i += stride) d1[i] = s1[i];
+}
+
+// The context's own buffers as the tape of the step recorded last.
+ic::AdjStepTape context_tape(ic_ctx *ctx) {
+  ic::AdjStepTape t{};
+  const ic::AdjointStore &A = ctx->adj;
+  for (int j = 0; j < 4; ++j) {
+    t.Un[j] = ctx->U[A.rec_cur][j];
+    t.U1[j] = A.tU1[j];
+    t.U2[j] = ctx->U[2][j];
+    t.Unew[j] = ctx->U[1 - A.rec_cur][j];
+  }
+  for (int a = 0; a < 3; ++a) t.G3[a] = A.tG3[a];
+  t.q_n = A.tq;
+  t.q_half = ctx->ps.q_half;
+  t.u_n = A.tu;
+  t.force = ctx->ps.force;
+  t.dg = ctx->ps.dg;
+  t.step = A.rec_step;
+  return t;
+}
+
+// A caller's step tape: a 64-byte header, the 19 fields (U^n, U_1, U_2, g~,
+// U^{n+1}), then q^n, q^{n+1/2}, u^n, F, dg, each 16-byte aligned.
+struct TapeLayout {
+  ic::AdjStepTape t;
+  size_t bytes;
+};
+
+TapeLayout tape_layout(const ic_ctx *ctx, void *base) {
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, fs = (fb + 15) / 16 * 16, n = size_t(ctx->ps.n);
+  const size_t qs = (24 * n + 15) / 16 * 16, vs = (3 * ctx->real_size * n + 15) / 16 * 16;
+  char *p = static_cast<char *>(base);
+  TapeLayout L{};
+  size_t off = sizeof(SnapHeader);
+  auto take = [&](size_t len) {
+    void *at = p ? p + off : nullptr;
+    off += len;
+    return at;
+  };
+  for (int j = 0; j < 4; ++j) L.t.Un[j] = take(fs);
+  for (int j = 0; j < 4; ++j) L.t.U1[j] = take(fs);
+  for (int j = 0; j < 4; ++j) L.t.U2[j] = take(fs);
+  for (int a = 0; a < 3; ++a) L.t.G3[a] = take(fs);
+  for (int j = 0; j < 4; ++j) L.t.Unew[j] = take(fs);
+  L.t.q_n = take(qs);
+  L.t.q_half = take(qs);
+  L.t.u_n = take(vs);
+  L.t.force = take(vs);
+  L.t.dg = take(vs);
+  L.bytes = off;
+  return L;
+}
+
 size_t snapshot_bytes(const ic_ctx *ctx) {
   const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n);
   return sizeof(SnapHeader) + 4 * ((fb + 15) / 16 * 16) + (24 * n + 15) / 16 * 16 + 3 * ctx->real_size * n;
@@ -877,8 +964,77 @@ ic_status ic_adjoint_step(ic_ctx *ctx, double weight) {
   if (ctx->adj.rec_cur < 0) return fail(ctx, IC_ERR_STATE, "no recorded step to reverse (call ic_step_record)");
   if (ctx->adj.rec_cur != 1 - ctx->cur)
     return fail(ctx, IC_ERR_STATE, "the state moved on after ic_step_record; record the step again");
-  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, weight));
+  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, context_tape(ctx), weight));
   ctx->adj.rec_cur = -1;
+  return IC_OK;
+}
+
+ic_status ic_tape_size(const ic_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return IC_ERR_ARG;
+  *bytes = tape_layout(ctx, nullptr).bytes;
+  return IC_OK;
+}
+
+ic_status ic_step_record_tape(ic_ctx *ctx, void *dev_buf) {
+  if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
+  ic_status st = ic_step_record(ctx);
+  if (st) return st;
+  // the recorded step's states and particle arrays, copied out before the next step overwrites them
+  const ic::AdjStepTape src = context_tape(ctx);
+  const TapeLayout L = tape_layout(ctx, dev_buf);
+  const size_t fb = size_t(ctx->cells) * ctx->real_size, n = size_t(ctx->ps.n), r = ctx->real_size;
+  // all 24 copies in one launch (the host issues one call instead of 24)
+  CopyList cl{};
+  auto cp = [&](void *dst, const void *from, size_t len) {
+    if (!len) return;
+    cl.src[cl.n] = static_cast<const char *>(from);
+    cl.dst[cl.n] = static_cast<char *>(dst);
+    cl.len[cl.n] = len;
+    ++cl.n;
+  };
+  for (int j = 0; j < 4; ++j) {
+    cp(L.t.Un[j], src.Un[j], fb);
+    cp(L.t.U1[j], src.U1[j], fb);
+    cp(L.t.U2[j], src.U2[j], fb);
+    cp(L.t.Unew[j], src.Unew[j], fb);
+  }
+  for (int a = 0; a < 3; ++a) cp(L.t.G3[a], src.G3[a], fb);
+  cp(const_cast<void *>(L.t.q_n), src.q_n, 24 * n);
+  cp(const_cast<void *>(L.t.q_half), src.q_half, 24 * n);
+  cp(const_cast<void *>(L.t.u_n), src.u_n, 3 * r * n);
+  cp(const_cast<void *>(L.t.force), src.force, 3 * r * n);
+  cp(const_cast<void *>(L.t.dg), src.dg, 3 * r * n);
+  {
+    const size_t words = (fb + 15) / 16;
+    const unsigned bx = unsigned(std::min<size_t>((words + 255) / 256, 64));
+    k_copy_list<<<dim3(bx, unsigned(cl.n)), 256, 0, ctx->stream>>>(cl);
+    IC_CUDA(ctx, cudaGetLastError());
+  }
+  k_snapshot_header<<<1, 1, 0, ctx->stream>>>(static_cast<SnapHeader *>(dev_buf), kTapeMagic, src.step, ctx->ps.n,
+                                              ctx->p.precision, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+  IC_CUDA(ctx, cudaGetLastError());
+  ctx->tapes[reinterpret_cast<uintptr_t>(dev_buf)] = {src.step, ctx->ps.n};
+  return IC_OK;
+}
+
+ic_status ic_adjoint_step_tape(ic_ctx *ctx, const void *dev_buf, double weight) {
+  if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
+  ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  TapeLayout L = tape_layout(ctx, const_cast<void *>(dev_buf));
+  const auto known = ctx->tapes.find(reinterpret_cast<uintptr_t>(dev_buf));
+  if (known != ctx->tapes.end() && known->second.second == ctx->ps.n) {
+    L.t.step = known->second.first;   // recorded by this context: its header is known
+  } else {
+    SnapHeader hd{};
+    IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    IC_CUDA(ctx, cudaMemcpy(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost));
+    if (hd.magic != kTapeMagic || hd.precision != ctx->p.precision || hd.nx != ctx->p.nx || hd.ny != ctx->p.ny ||
+        hd.nz != ctx->p.nz || hd.np != ctx->ps.n)
+      return fail(ctx, IC_ERR_ARG, "not a step tape of this context's grid and particles");
+    L.t.step = hd.step;
+  }
+  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, L.t, weight));
   return IC_OK;
 }
 

@@ -142,6 +142,7 @@ struct ic_ctx {
   ic::ParticleStore ps{};
   ic::AdjointStore adj{};
   std::unordered_map<uintptr_t, std::pair<int64_t, int>> snapshots;   // device snapshots saved: step, particles
+  std::unordered_map<uintptr_t, std::pair<int64_t, int>> tapes;       // step tapes recorded: step, particles
   void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
   void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
   bool any_spring = false;  // some particle is tethered: the stage force source is launched
@@ -232,8 +233,15 @@ cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]);
 cudaError_t launch_particle_momentum(ic_ctx *ctx, double *dev_out3);
 
-// adjoint (ic_adjoint.cu): reverse sweep of the recorded step
-cudaError_t launch_adjoint_step(ic_ctx *ctx, double weight);
+// adjoint (ic_adjoint.cu): reverse sweep of one recorded step, whose states
+// and particle arrays are read from these buffers (the context's own after
+// ic_step_record, or a caller's tape after ic_step_record_tape)
+struct AdjStepTape {
+  void *Un[4], *U1[4], *U2[4], *G3[3], *Unew[4];   // U^n, U_1, U_2, g~, U^{n+1}
+  const void *q_n, *q_half, *u_n, *force, *dg;
+  int64_t step;
+};
+cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight);
 void positions_to_device(const ic_ctx *ctx, const double *q, size_t n3, void *out);
 void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q);
 }  // namespace ic

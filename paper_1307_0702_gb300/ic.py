@@ -208,6 +208,25 @@ class Grid:
                                               _ptr(g[1]), _ptr(g[2]), _ptr(q), _ptr(u)))
         return dict(m_e=me, eps=eps, A=float(A[0]), rho=rho, g=g, q=q, u=u)
 
+    def tape_size(self):
+        size = ctypes.c_size_t()
+        self._check(self._lib.ic_tape_size(self._ctx, ctypes.byref(size)))
+        return size.value
+
+    def new_tape(self):
+        """A device buffer (torch uint8 tensor) for the tape of one step."""
+        import torch
+
+        return torch.empty(self.tape_size(), dtype=torch.uint8, device=self.device)
+
+    def step_record_tape(self, buf):
+        """One step forward, its reverse-sweep inputs copied into buf."""
+        self._check(self._lib.ic_step_record_tape(self._ctx, ctypes.c_void_p(buf.data_ptr())))
+
+    def adjoint_step_tape(self, buf, weight):
+        """Reverse the step taped in buf, adding weight * sum_p d_p . F_p to the objective."""
+        self._check(self._lib.ic_adjoint_step_tape(self._ctx, ctypes.c_void_p(buf.data_ptr()), float(weight)))
+
     def snapshot_size(self):
         size = ctypes.c_size_t()
         self._check(self._lib.ic_snapshot_size(self._ctx, ctypes.byref(size)))

@@ -37,14 +37,14 @@ def case(prec, shape=(12, 10, 9), forcing="mode", nsteps=10, seed=3, amp=2e-3, u
     return gp, rho, g, parts, weights, direction
 
 
-def gpu_gradient(gp, rho, g, parts, weights, direction, K):
+def gpu_gradient(gp, rho, g, parts, weights, direction, K, tapes=True):
     from paper_1307_0702_gb300 import Grid
     from paper_1307_0702_gb300.adjoint import Rollout
 
     with Grid(gp) as grid:
         grid.set_state(rho, g)
         grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
-        roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K)
+        roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K, tapes=tapes)
         phi = roll.forward(weights, direction)
         return phi, roll.backward()
 
@@ -407,3 +407,33 @@ def test_rollout_without_particles():
     assert out["A"] == 0.0
     assert not np.any(out["rho"]) and not any(np.any(x) for x in out["g"])
     assert out["m_e"].shape == (0,)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_tapes_and_recomputed_steps_give_the_same_gradient(prec):
+    """Reversing recorded tapes (two forward passes per step) and recording
+    each step again before reversing it (three) differentiate the same
+    steps: the gradients agree to the rounding of the atomic spreads."""
+    gp, rho, g, parts, weights, direction = case(prec, nsteps=11)
+    phi_t, gt = gpu_gradient(gp, rho, g, parts, weights, direction, K=4, tapes=True)
+    phi_r, gr = gpu_gradient(gp, rho, g, parts, weights, direction, K=4, tapes=False)
+    assert phi_t == phi_r
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for key in ("m_e", "kappa_ratio", "rho", "q", "u"):
+        assert rel_err(gt[key], gr[key]) < tol, key
+    assert abs(gt["A"] - gr["A"]) <= tol * abs(gr["A"])
+
+
+def test_tape_of_another_grid_is_refused():
+    from paper_1307_0702_gb300 import Grid, ICError
+
+    gp = W.grid_params(8, kT=0.0, precision="fp64")
+    with Grid(gp) as a, Grid(W.grid_params(9, kT=0.0, precision="fp64")) as b:
+        for grid in (a, b):
+            grid.add_particles([[2.0, 3.0, 4.0]], 1.0, 0.5, 0.3)
+            grid.adjoint_enable()
+        tape = a.new_tape()
+        a.step_record_tape(tape)
+        a.adjoint_step_tape(tape, 1.0)
+        with pytest.raises(ICError):
+            b.adjoint_step_tape(tape, 1.0)
