@@ -161,20 +161,44 @@ struct StageIn {
 //   gp = gbar_A(i) + vbar_A(i) / rho^A_i  (the advective momenta, the mass flux and V^T),
 //   rf = -vbar_A(i) v_A(i) / rho^A_i      (for the density part, summed by the next kernel),
 //   T0 = Tbar_A(i)                        (its sum over A is the adjoint of the centre pressure).
+// The 3 x 3 x 3 neighbourhood of a cell: its wrapped x, y, z offsets, so that
+// a neighbour's index is two additions (the grid has fewer than 2^32 cells).
+struct Nbr {
+  uint32_t ox[3], oy[3], oz[3];
+  __device__ __forceinline__ uint32_t at(int dx, int dy, int dz) const { return ox[dx + 1] + oy[dy + 1] + oz[dz + 1]; }
+};
+
+__device__ __forceinline__ Nbr neighbourhood(const Geo &G, int x, int y, int z) {
+  const uint32_t nx = uint32_t(G.nx), nxy = uint32_t(G.nx) * uint32_t(G.ny);
+  Nbr N;
+  N.ox[0] = uint32_t(pw(x - 1, G.nx));
+  N.ox[1] = uint32_t(x);
+  N.ox[2] = uint32_t(pw(x + 1, G.nx));
+  N.oy[0] = uint32_t(pw(y - 1, G.ny)) * nx;
+  N.oy[1] = uint32_t(y) * nx;
+  N.oy[2] = uint32_t(pw(y + 1, G.ny)) * nx;
+  N.oz[0] = uint32_t(pw(z - 1, G.nz)) * nxy;
+  N.oz[1] = uint32_t(z) * nxy;
+  N.oz[2] = uint32_t(pw(z + 1, G.nz)) * nxy;
+  return N;
+}
+
 template <typename real, int A>
-__device__ __forceinline__ void stage_face(const StageIn<real> &In, const Geo &G, real coef, real inv_h, real eta,
+__device__ __forceinline__ void stage_face(const StageIn<real> &In, const Nbr &N, real coef, real inv_h, real eta,
                                            real lam2, real rho0, int x, int y, int z, size_t i, real &gp, real &rf,
                                            real &T0) {
   constexpr int ax = A == 0, ay = A == 1, az = A == 2;
-  const auto L = [&](int a, int xx, int yy, int zz) { return coef * In.lam[1 + a][G.at(xx, yy, zz)]; };
+  // every read lies within one cell of (x, y, z): its index from the neighbourhood
+  const auto at = [&](int xx, int yy, int zz) { return N.at(xx - x, yy - y, zz - z); };
+  const auto L = [&](int a, int xx, int yy, int zz) { return coef * In.lam[1 + a][at(xx, yy, zz)]; };
   const auto Tb = [&](int a, int xx, int yy, int zz) {
     return (L(a, xx, yy, zz) - L(a, xx - (a == 0), yy - (a == 1), zz - (a == 2))) * inv_h;
   };
   const auto Fb = [&](int a, int b, int xx, int yy, int zz) {
     return (L(a, xx + (b == 0), yy + (b == 1), zz + (b == 2)) - L(a, xx, yy, zz)) * inv_h;
   };
-  const auto V = [&](int a, int xx, int yy, int zz) { return In.v[a][G.at(xx, yy, zz)]; };
-  const auto Gm = [&](int a, int xx, int yy, int zz) { return In.U.g[a][G.at(xx, yy, zz)]; };
+  const auto V = [&](int a, int xx, int yy, int zz) { return In.v[a][at(xx, yy, zz)]; };
+  const auto Gm = [&](int a, int xx, int yy, int zz) { return In.U.g[a][at(xx, yy, zz)]; };
   // dvbar_A(c) = -2 eta Tbar_A(c) - lam2 sum_a Tbar_a(c)
   const auto DV = [&](int xx, int yy, int zz) {
     const real t0 = Tb(0, xx, yy, zz), t1 = Tb(1, xx, yy, zz), t2 = Tb(2, xx, yy, zz);
@@ -203,8 +227,9 @@ __device__ __forceinline__ void stage_face(const StageIn<real> &In, const Geo &G
     vb += eta * inv_h * ((Fab0 + Fba0) - (Fab1 + Fba1));
   }
   // mass flux: d rho/dt = -(1/h) sum_a (g_a(i) - g_a(i - a))
-  gb -= coef * (In.lam[0][i] - In.lam[0][G.at(x + ax, y + ay, z + az)]) * inv_h;
-  const real rfv = face_rho(In.U, G, rho0, A, x, y, z);
+  const uint32_t iA = at(x + ax, y + ay, z + az);
+  gb -= coef * (In.lam[0][i] - In.lam[0][iA]) * inv_h;
+  const real rfv = rho0 + real(0.5) * (In.U.d[i] + In.U.d[iA]);
   gp = gb + vb / rfv;
   rf = -vb * v0 / rfv;
 }
@@ -225,9 +250,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(StageIn<real> I
     int x, y, z;
     grid_coords<real>(i, G, x, y, z);
     real g0, r0, t0, g1, r1, t1, g2, r2, t2;
-    stage_face<real, 0>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g0, r0, t0);
-    stage_face<real, 1>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g1, r1, t1);
-    stage_face<real, 2>(In, G, coef, inv_h, eta, lam2, rho0, x, y, z, i, g2, r2, t2);
+    const Nbr N = neighbourhood(G, x, y, z);
+    stage_face<real, 0>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g0, r0, t0);
+    stage_face<real, 1>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g1, r1, t1);
+    stage_face<real, 2>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g2, r2, t2);
     gp0[i] = g0;
     gp1[i] = g1;
     gp2[i] = g2;
