@@ -161,35 +161,14 @@ struct StageIn {
 //   gp = gbar_A(i) + vbar_A(i) / rho^A_i  (the advective momenta, the mass flux and V^T),
 //   rf = -vbar_A(i) v_A(i) / rho^A_i      (for the density part, summed by the next kernel),
 //   T0 = Tbar_A(i)                        (its sum over A is the adjoint of the centre pressure).
-// The 3 x 3 x 3 neighbourhood of a cell: its wrapped x, y, z offsets, so that
-// a neighbour's index is two additions (the grid has fewer than 2^32 cells).
-struct Nbr {
-  uint32_t ox[3], oy[3], oz[3];
-  __device__ __forceinline__ uint32_t at(int dx, int dy, int dz) const { return ox[dx + 1] + oy[dy + 1] + oz[dz + 1]; }
-};
-
-__device__ __forceinline__ Nbr neighbourhood(const Geo &G, int x, int y, int z) {
-  const uint32_t nx = uint32_t(G.nx), nxy = uint32_t(G.nx) * uint32_t(G.ny);
-  Nbr N;
-  N.ox[0] = uint32_t(pw(x - 1, G.nx));
-  N.ox[1] = uint32_t(x);
-  N.ox[2] = uint32_t(pw(x + 1, G.nx));
-  N.oy[0] = uint32_t(pw(y - 1, G.ny)) * nx;
-  N.oy[1] = uint32_t(y) * nx;
-  N.oy[2] = uint32_t(pw(y + 1, G.ny)) * nx;
-  N.oz[0] = uint32_t(pw(z - 1, G.nz)) * nxy;
-  N.oz[1] = uint32_t(z) * nxy;
-  N.oz[2] = uint32_t(pw(z + 1, G.nz)) * nxy;
-  return N;
-}
-
-template <typename real, int A>
-__device__ __forceinline__ void stage_face(const StageIn<real> &In, const Nbr &N, real coef, real inv_h, real eta,
-                                           real lam2, real rho0, int x, int y, int z, size_t i, real &gp, real &rf,
-                                           real &T0) {
+// The arrays of In may be global fields or a block's shared-memory tile;
+// Idx maps an offset (dx, dy, dz) in {-1, 0, 1}^3 from the cell to an index
+// of them, and i is the cell's own index.
+template <typename real, int A, typename Idx>
+__device__ __forceinline__ void stage_face(const StageIn<real> &In, const Idx &at, real coef, real inv_h, real eta,
+                                           real lam2, real rho0, uint32_t i, real &gp, real &rf, real &T0) {
   constexpr int ax = A == 0, ay = A == 1, az = A == 2;
-  // every read lies within one cell of (x, y, z): its index from the neighbourhood
-  const auto at = [&](int xx, int yy, int zz) { return N.at(xx - x, yy - y, zz - z); };
+  constexpr int x = 0, y = 0, z = 0;   // offsets are relative to the cell
   const auto L = [&](int a, int xx, int yy, int zz) { return coef * In.lam[1 + a][at(xx, yy, zz)]; };
   const auto Tb = [&](int a, int xx, int yy, int zz) {
     return (L(a, xx, yy, zz) - L(a, xx - (a == 0), yy - (a == 1), zz - (a == 2))) * inv_h;
@@ -236,24 +215,60 @@ __device__ __forceinline__ void stage_face(const StageIn<real> &In, const Nbr &N
 
 // The stage adjoint's grid part for every cell (stage_face of the three
 // face sets), and dpdA * sum_i pibar(i) profile(i) added to *gA (the drive is
-// linear in A).
+// linear in A).  A block takes an 8 x 8 x 4 box of cells: it stages the 11
+// fields the gathers read (the adjoint of U_{s+1}, the face velocities and
+// momenta, delta rho) on the box and its one-cell periodic halo in shared
+// memory, then each thread gathers its cell's ~100 neighbour values from
+// there.
+constexpr int kTileX = 8, kTileY = 8, kTileZ = 4;
+constexpr int kHaloX = kTileX + 2, kHaloY = kTileY + 2, kHaloZ = kTileZ + 2;
+constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;
+constexpr int kTileFields = 11;
+static_assert(kTileX * kTileY * kTileZ == kAdjThreads, "one thread per cell of the box");
+
 template <typename real>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(StageIn<real> In, Geo G, StageAdjConsts k,
                                                                   const real *__restrict__ cos_table, real *gp0,
                                                                   real *gp1, real *gp2, real *rf0, real *rf1,
                                                                   real *rf2, real *pibar, double *gA) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *tile = reinterpret_cast<real *>(smem_raw);   // [kTileFields][kHaloCells]
   const real coef = real(k.coef), inv_h = real(k.inv_h), eta = real(k.eta), lam2 = real(k.lam2),
              rho0 = real(k.rho0);
-  const size_t cells = size_t(G.nx) * G.ny * G.nz;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY, z0 = blockIdx.z * kTileZ;
+  for (int h = threadIdx.x; h < kHaloCells; h += blockDim.x) {
+    const int hx = h % kHaloX, hy = (h / kHaloX) % kHaloY, hz = h / (kHaloX * kHaloY);
+    const size_t gi = G.at(x0 + hx - 1, y0 + hy - 1, z0 + hz - 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tile[j * kHaloCells + h] = In.lam[j][gi];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      tile[(4 + a) * kHaloCells + h] = In.v[a][gi];
+      tile[(7 + a) * kHaloCells + h] = In.U.g[a][gi];
+    }
+    tile[10 * kHaloCells + h] = In.U.d[gi];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kTileX, ty = (threadIdx.x / kTileX) % kTileY, tz = threadIdx.x / (kTileX * kTileY);
+  const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
   double acc_A = 0.0;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cells; i += size_t(gridDim.x) * blockDim.x) {
-    int x, y, z;
-    grid_coords<real>(i, G, x, y, z);
+  if (x < G.nx && y < G.ny && z < G.nz) {
+    StageIn<real> T;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) T.lam[j] = tile + j * kHaloCells;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T.v[a] = tile + (4 + a) * kHaloCells;
+      T.U.g[a] = tile + (7 + a) * kHaloCells;
+    }
+    T.U.d = tile + 10 * kHaloCells;
+    const int c = (tx + 1) + kHaloX * ((ty + 1) + kHaloY * (tz + 1));
+    const auto at = [c](int dx, int dy, int dz) { return uint32_t(c + dx + kHaloX * (dy + kHaloY * dz)); };
     real g0, r0, t0, g1, r1, t1, g2, r2, t2;
-    const Nbr N = neighbourhood(G, x, y, z);
-    stage_face<real, 0>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g0, r0, t0);
-    stage_face<real, 1>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g1, r1, t1);
-    stage_face<real, 2>(In, N, coef, inv_h, eta, lam2, rho0, x, y, z, i, g2, r2, t2);
+    stage_face<real, 0>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g0, r0, t0);
+    stage_face<real, 1>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g1, r1, t1);
+    stage_face<real, 2>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g2, r2, t2);
+    const size_t i = size_t(x) + size_t(G.nx) * (size_t(y) + size_t(G.ny) * size_t(z));
     gp0[i] = g0;
     gp1[i] = g1;
     gp2[i] = g2;
@@ -262,11 +277,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(StageIn<real> I
     rf2[i] = r2;
     const real pb = t0 + t1 + t2;
     pibar[i] = pb;
-    const int c = k.wave_axis == 0 ? x : (k.wave_axis == 1 ? y : z);
+    const int cw = k.wave_axis == 0 ? x : (k.wave_axis == 1 ? y : z);
     if (k.forcing == IC_FORCE_MODE)
-      acc_A += double(pb) * double(cos_table[c]);
-    else if (k.forcing == IC_FORCE_PLANE && c == k.plane_index)
-      acc_A += double(pb);
+      acc_A = double(pb) * double(cos_table[cw]);
+    else if (k.forcing == IC_FORCE_PLANE && cw == k.plane_index)
+      acc_A = double(pb);
   }
   if (k.forcing != IC_FORCE_NONE) {
     acc_A = warp_sum(acc_A);
@@ -725,8 +740,12 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
       return cudaGetLastError();
     }));
     IC_ADJ_TRY(timed_launch(ctx, kClassStage, [&] {
-      k_adj_stage_rates<real><<<gblocks, kAdjThreads, 0, st>>>(In, G, k, cos_table, gp[0], gp[1], gp[2], rf[0],
-                                                               rf[1], rf[2], pibar, A.gA);
+      constexpr size_t smem = size_t(kTileFields) * kHaloCells * sizeof(real);
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_adj_stage_rates<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem));
+      const dim3 tiles((p.nx + kTileX - 1) / kTileX, (p.ny + kTileY - 1) / kTileY, (p.nz + kTileZ - 1) / kTileZ);
+      k_adj_stage_rates<real><<<tiles, kAdjThreads, smem, st>>>(In, G, k, cos_table, gp[0], gp[1], gp[2], rf[0],
+                                                                rf[1], rf[2], pibar, A.gA);
       return cudaGetLastError();
     }));
     if (n > 0) {
