@@ -406,6 +406,9 @@ def main():
     ap.add_argument("--boxes", type=int, default=256)
     ap.add_argument("--tile", type=int, nargs=2, metavar=("TILE_X", "ZCHUNK"), default=None,
                     help="fixed stage-kernel tiling instead of the autotuner's (e.g. for profiling)")
+    ap.add_argument("--stage-copy", default="auto", choices=["auto", "thread", "bulk", "rows16"],
+                    help="loads of the FP32 wide stage tile: the autotuner's choice, per-thread copies, "
+                         "TMA bulk row copies or 16-byte row copies")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -452,6 +455,9 @@ def main():
         tiling = grid.tile()
     else:
         tiling = grid.autotune(reps=3)
+    if args.stage_copy != "auto":
+        grid.set_stage_copy(args.stage_copy)
+    stage_copy = grid.stage_copy()
     grid.step(args.warmup)
     grid.sync()
 
@@ -512,7 +518,8 @@ def main():
             tj = json.load(f)
         # ncu DRAM bytes of the same kernel (same precision, size and tile width)
         if (tj.get("precision") == args.precision and tj.get("cells") == cells
-                and tj.get("tile_x") == tiling[0] and tj.get("kernel_rev") == STAGE_KERNEL_REV):
+                and tj.get("tile_x") == tiling[0] and tj.get("kernel_rev") == STAGE_KERNEL_REV
+                and tj.get("stage_copy", "thread") == stage_copy):
             traffic = tj.get("bytes_per_launch")
 
     # end-to-end through the public API with host buffers: one step per call,
@@ -567,7 +574,7 @@ def main():
             "config": {"workload": WORKLOAD, "cells": cells, "particles": npart, "precision": args.precision,
                        "parallelism": f"{world} independent boxes (one per GPU)",
                        "l2": "flushed between timed steps (512 MB write, outside the step events)",
-                       "stage_tiling": list(tiling), "particle_steps_per_s": pvalue},
+                       "stage_tiling": list(tiling), "stage_copy": stage_copy, "particle_steps_per_s": pvalue},
             "particle_steps_per_s": pvalue,
             "roofline": roofline,
             "gpu_launches": int(round(launches_per_step * args.steps)),

@@ -195,16 +195,38 @@ void ic_batch_destroy(ic_batch *batch);
  * ic_set_tile: IC_ERR_ARG for tile_x not 16 or 32, or zchunk < 8 (unless it is
  * at least nz).  ic_get_tile: the current tiling (each pointer may be NULL).
  * ic_autotune synchronises the stream, times the three stage kernels of every
- * candidate (tile_x 32 and 16; zchunk 32, 16 and 8, clipped to nz), reps
+ * candidate (tile_x 32 with each staging mode of ic_set_stage_copy that the
+ * grid allows, and 16; zchunk 32, 16 and 8, clipped to nz), reps
  * repetitions each, on the context's scratch buffers (U^n is left untouched:
  * the state is unchanged) and keeps the fastest; choice[3] (or NULL) receives
- * tile_x, tile_y, zchunk.  ic_batch_autotune tunes one context of each
- * distinct grid shape and precision of the batch and gives the choice to the
- * others. */
+ * tile_x, tile_y, zchunk (the staging mode is kept in the context).
+ * ic_batch_autotune tunes one context of each distinct grid shape and
+ * precision of the batch and gives the choice to the others. */
 ic_status ic_set_tile(ic_ctx *ctx, int tile_x, int zchunk);
 ic_status ic_get_tile(const ic_ctx *ctx, int *tile_x, int *tile_y, int *zchunk);
 ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice);
 ic_status ic_batch_autotune(ic_batch *batch, int reps);
+
+/* Loads of the FP32 wide-tile stage kernel (tile_x 32).  The paper has no
+ * counterpart: this is a performance setting; every mode gives the same bits.
+ *   IC_STAGE_COPY_THREAD: each thread copies its own values into shared
+ *     memory (4-byte cp.async).  Works on every grid.
+ *   IC_STAGE_COPY_BULK: each plane pair's tile rows (40 floats, x0 - 4 to
+ *     x0 + 36) are copied by TMA bulk copies (cp.async.bulk, one or two per
+ *     row), their completion tracked by an mbarrier.
+ *   IC_STAGE_COPY_ROWS16: the same rows by 16-byte cp.async, one thread per
+ *     row, signalling the same mbarrier.
+ * The row modes need nx a multiple of 4 and at least 40, and 16-byte aligned
+ * fields (always so for the context's own buffers unless a custom allocator
+ * returns others); elsewhere the kernel falls back to IC_STAGE_COPY_THREAD.
+ * ic_set_stage_copy: IC_ERR_ARG for an unknown mode.  ic_get_stage_copy:
+ * the mode the next step's stage kernels use (after that fallback).  A row
+ * copy that has not landed after about a second stops the kernel; the next
+ * call that reads the device status returns IC_ERR_TIMEOUT.  ic_autotune
+ * times every mode of the wide tile. */
+enum { IC_STAGE_COPY_THREAD = 0, IC_STAGE_COPY_BULK = 1, IC_STAGE_COPY_ROWS16 = 2 };
+ic_status ic_set_stage_copy(ic_ctx *ctx, int mode);
+ic_status ic_get_stage_copy(const ic_ctx *ctx, int *mode);
 
 /* Kernel timing for measurement.  While enabled, ic_step launches without
  * CUDA graphs and brackets every kernel (and ic_adjoint_step every adjoint

@@ -55,6 +55,8 @@ SIGNATURES = {
     "ic_batch_destroy": (None, [c_void_p]),
     "ic_set_tile": (c_int, [c_void_p, c_int, c_int]),
     "ic_get_tile": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ic_set_stage_copy": (c_int, [c_void_p, c_int]),
+    "ic_get_stage_copy": (c_int, [c_void_p, POINTER(c_int)]),
     "ic_autotune": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "ic_batch_autotune": (c_int, [c_void_p, c_int]),
     "ic_profile": (c_int, [c_void_p, c_int]),

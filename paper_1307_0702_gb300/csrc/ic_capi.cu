@@ -199,6 +199,8 @@ ic_status status_error(ic_ctx *ctx, int st) {
   IC_CUDA(ctx, cudaMemset(ctx->d.status, 0, sizeof(int)));
   if (st & ic::kStatusNonfinite)
     return fail(ctx, IC_ERR_NONFINITE, "state became non-finite (check the CFL numbers c dt/h and c_p dt/h)");
+  if (st & ic::kStatusStaging)
+    return fail(ctx, IC_ERR_TIMEOUT, "a bulk copy into a stage kernel's shared memory did not complete");
   if (st & ic::kStatusNbrOverflow)
     return fail(ctx, IC_ERR_CAPACITY, "more than %d particles within the neighbour cutoff of one particle",
                 ic::kMaxNeighbours);
@@ -1250,6 +1252,20 @@ ic_status ic_set_tile(ic_ctx *ctx, int tile_x, int zchunk) {
   return IC_OK;
 }
 
+ic_status ic_set_stage_copy(ic_ctx *ctx, int mode) {
+  if (!ctx || mode < IC_STAGE_COPY_THREAD || mode > IC_STAGE_COPY_ROWS16) return IC_ERR_ARG;
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->stage_copy = mode;
+  invalidate_graphs(ctx);
+  return IC_OK;
+}
+
+ic_status ic_get_stage_copy(const ic_ctx *ctx, int *mode) {
+  if (!ctx || !mode) return IC_ERR_ARG;
+  *mode = ic::stage_copy_active(ctx);
+  return IC_OK;
+}
+
 ic_status ic_get_tile(const ic_ctx *ctx, int *tile_x, int *tile_y, int *zchunk) {
   if (!ctx) return IC_ERR_ARG;
   int t[3];
@@ -1282,10 +1298,21 @@ ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
     cudaEventDestroy(e0);
     return fail(ctx, IC_ERR_CUDA, "cudaEventCreate");
   }
-  int best_v = ctx->tile_variant, best_z = ctx->zchunk;
+  int best_v = ctx->tile_variant, best_z = ctx->zchunk, best_copy = ctx->stage_copy;
   float best_ms = -1.0f;
   cudaError_t err = cudaSuccess;
-  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+  // candidates: the wide tile with each staging mode (the row modes where the
+  // grid allows them), the narrow tile; zchunk 32, 16, 8 each
+  const int v_in = ctx->tile_variant, copy_in = ctx->stage_copy;
+  ctx->tile_variant = 0;
+  ctx->stage_copy = IC_STAGE_COPY_ROWS16;
+  const bool rows_ok = ic::stage_copy_active(ctx) != IC_STAGE_COPY_THREAD;
+  ctx->tile_variant = v_in;
+  ctx->stage_copy = copy_in;
+  for (int cand = 0; cand < 4 && err == cudaSuccess; ++cand) {
+    const int v = cand == 3 ? 1 : 0, copy = cand == 3 ? IC_STAGE_COPY_THREAD : cand;
+    if (copy != IC_STAGE_COPY_THREAD && !rows_ok) continue;
+    ctx->stage_copy = copy;
     int last = -1;
     for (int z : {32, 16, 8}) {
       const int zc = std::min(z, ctx->p.nz);
@@ -1303,11 +1330,13 @@ ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
         best_ms = ms;
         best_v = v;
         best_z = zc;
+        best_copy = copy;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  ctx->stage_copy = best_copy;
   ic::set_stage_tile(ctx, best_v, best_z);
   invalidate_graphs(ctx);
   if (err != cudaSuccess) return cuda_fail(ctx, err, "autotune");
@@ -1331,6 +1360,7 @@ ic_status ic_batch_autotune(ic_batch *b, int reps) {
       tuned.push_back(c);
     } else {
       IC_CUDA(c, cudaStreamSynchronize(c->stream));
+      c->stage_copy = tuned[j]->stage_copy;
       ic::set_stage_tile(c, tuned[j]->tile_variant, tuned[j]->zchunk);
       invalidate_graphs(c);
     }

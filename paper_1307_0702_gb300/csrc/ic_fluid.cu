@@ -54,6 +54,7 @@ struct StageArgs {
   FluidConsts<real> c;
   const int64_t *step;
   double *partials;                // stage 3: per-CTA sum of delta rho cos(k x)
+  int *status;                     // error bits (bulk staging timeout), or null
   int ncols_x, ncols_y;            // tile columns along x and y
 };
 
@@ -390,11 +391,98 @@ __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk (TMA) copies of whole tile rows, tracked by one mbarrier per CTA.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// 16-byte asynchronous copy (L2 only), and an mbarrier arrival that fires
+// when all of this thread's earlier asynchronous copies have landed
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t v;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(v));
+  return v;
+}
+// Waits for the phase of the given parity to complete; gives up (false)
+// after about a second, so that a copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+
 // staging slot of one plane pair: the thread's own values, [field][EXY]
 enum StageField {
   SF_DR0, SF_DR1, SF_DR2, SF_DRX0, SF_DRX1, SF_DRY0, SF_DRY1, SF_GX0, SF_GX1, SF_GY0, SF_GY1, SF_GZ0, SF_GZ1,
   SF_PP0, SF_PP1, SF_NZ, kStageFields = SF_NZ + 12
 };
+
+// Row staging: per plane pair, each staged field-plane is copied as tile
+// rows of TX + 8 floats (x from x0 - 4 to x0 + TX + 4, 16-byte aligned; a row
+// that crosses the periodic seam is copied in two pieces), one thread per
+// row, either by one or two TMA bulk copies (kStageBulk) or by 16-byte
+// asynchronous copies (kStageRows16); an mbarrier tracks the pair.  Field-planes:
+// delta rho at k, k+1, k+2 (TY + 3 rows: the thread rows and one above, for
+// the y neighbour), then g_x, g_y, g_z, S Omega and the six stored normals at
+// k, k+1 (TY + 2 rows each).
+enum BulkField { BF_DR0, BF_DR1, BF_DR2, BF_GX0, BF_PP0 = BF_GX0 + 6, BF_NZ = BF_PP0 + 2, kBulkFields = BF_NZ + 12 };
+
+template <int EY>
+__host__ __device__ constexpr int bulk_row0(int fp) { return fp < 3 ? fp * (EY + 1) : 3 * (EY + 1) + (fp - 3) * EY; }
+template <int TX, int TY>
+__host__ __device__ constexpr int bulk_rows_max() { return bulk_row0<TY + 2>(kBulkFields); }
+
+// Offset, from this thread's own element of the first row block, of the
+// staged value that the per-thread staging slot keeps as field f.
+template <int EY, int RP>
+__device__ __forceinline__ constexpr int bulk_offset(int f) {
+  return f == SF_DR0    ? 0
+         : f == SF_DR1  ? bulk_row0<EY>(BF_DR1) * RP
+         : f == SF_DR2  ? bulk_row0<EY>(BF_DR2) * RP
+         : f == SF_DRX0 ? 1
+         : f == SF_DRX1 ? bulk_row0<EY>(BF_DR1) * RP + 1
+         : f == SF_DRY0 ? RP
+         : f == SF_DRY1 ? (bulk_row0<EY>(BF_DR1) + 1) * RP
+         : f <= SF_GZ1  ? bulk_row0<EY>(BF_GX0 + (f - SF_GX0)) * RP
+         : f <= SF_PP1  ? bulk_row0<EY>(BF_PP0 + (f - SF_PP0)) * RP
+                        : bulk_row0<EY>(BF_NZ + (f - SF_NZ)) * RP;
+}
+
+template <int TX, int TY, bool BULK>
+constexpr size_t z2_smem_bytes() {
+  constexpr int EXY = (TX + 2) * (TY + 2);
+  return 18 * EXY * sizeof(float2) +
+         (BULK ? size_t(bulk_rows_max<TX, TY>()) * (TX + 8) * sizeof(float) : kStageFields * EXY * sizeof(float));
+}
 
 // the finished values of a plane pair
 struct Pair2 {
@@ -412,16 +500,21 @@ constexpr int z2_min_ctas() {
 #endif
 }
 
-template <int TX, int TY, int STAGE, bool NOISE>
+// staging of the pair kernel's loads
+enum { kStageThread = 0, kStageBulk = 1, kStageRows16 = 2 };
+
+template <int TX, int TY, int STAGE, bool NOISE, int STG>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (TY + 2)>())
     k_rk3_stage_z2(const StageArgs<float> a) {
-  constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
+  constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY, RP = TX + 8;
+  constexpr bool BULK = STG != kStageThread;   // row layout, mbarrier
+  static_assert(bulk_rows_max<TX, TY>() <= EXY, "one staged row per thread");
   enum { GX = 0, GY, GZ, VX, VY, VZ };
   enum { TXX = 0, TYY, TXY, TYX, TZX, TZY };
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);   // [2 slots][6 fields][EXY]
   float2 *T = sm + 12 * EXY;                            // [6 fluxes][EXY]
-  float *stg = reinterpret_cast<float *>(T + 6 * EXY);  // [kStageFields][EXY]
+  float *stg = reinterpret_cast<float *>(T + 6 * EXY);  // [kStageFields][EXY], or the bulk rows
   const FluidConsts<float> &c = a.c;
   const int NX = c.nx, NY = c.ny, NZ = c.nz;
   const int t = threadIdx.x;
@@ -443,6 +536,47 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
   const float2 ca = splat2(float(kStageA[STAGE])), cb = splat2(float(kStageB[STAGE]));
   const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
   float mode_acc = 0.0f;
+
+  // Bulk staging: thread t < nrows copies one row of one field-plane per pair
+  __shared__ __align__(8) unsigned long long s_bar;
+  const uint32_t bar = smem_u32(&s_bar);
+  uint32_t phase = 0;
+  bool bad = false;
+  int my_fp = -1, my_ry = 0;
+  if (BULK) {
+    const bool has_pp = a.pp != nullptr, has_nz = NOISE && STAGE != 0;
+    const int nrows = 3 * (EY + 1) + EY * (6 + (has_pp ? 2 : 0) + (has_nz ? 12 : 0));
+    if (t < 3 * (EY + 1)) {
+      my_fp = t / (EY + 1);
+      my_ry = t - my_fp * (EY + 1);
+    } else if (t < nrows) {
+      const int r = t - 3 * (EY + 1);
+      my_fp = r / EY;
+      my_ry = r - my_fp * EY;
+      my_fp += BF_GX0;
+      if (!has_pp && my_fp >= BF_PP0) my_fp += 2;
+    }
+    if (t == 0) mbar_init(bar, uint32_t(nrows));
+    __syncthreads();
+  }
+  const float *my_field = nullptr;
+  int my_dz = 0;
+  uint32_t my_dst = 0;
+  if (BULK && my_fp >= 0) {
+    my_field = my_fp < BF_GX0   ? a.s[0]
+               : my_fp < BF_PP0 ? a.s[1 + (my_fp - BF_GX0) / 2]
+               : my_fp < BF_NZ  ? a.pp
+                                : a.noise_in[(my_fp - BF_NZ) / 2];
+    my_dz = my_fp < BF_GX0 ? my_fp : ((my_fp - BF_GX0) & 1);
+    my_dst = smem_u32(stg + (bulk_row0<EY>(my_fp) + my_ry) * RP);
+  }
+  // a bulk copy that did not land in time: flag it, give the copies in
+  // flight another bounded wait, and leave the CTA (the decision is uniform)
+  const auto staging_abort = [&]() {
+    if (bad && a.status) atomicOr(a.status, kStatusStaging);
+    if (STG == kStageRows16) cp_async_wait_all();
+    (void)mbar_wait(bar, phase ^ 1);
+  };
 
   const int units = a.ncols_x * a.ncols_y * NZ;
   const int u_end = int((long long)units * (blockIdx.x + 1) / gridDim.x);
@@ -472,8 +606,40 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
     };
     const auto stored = [&](int kk) { return interior && kk >= z0 && kk < z1; };
 
+    // this thread's staged row in the run: its global row and the x pieces
+    // (x0 - 4 .. x0 + TX + 4 wrapped; the second piece, if any, starts at x = 0)
+    const float *row_src = nullptr;
+    int seg_a_x = 0, seg_a_len = 0;
+    if (BULK && my_fp >= 0) {
+      row_src = my_field + size_t(wrap((col / a.ncols_x) * TY - 1 + my_ry, NY)) * size_t(NX);
+      const int xs = (col % a.ncols_x) * TX - 4;
+      seg_a_x = xs < 0 ? NX - 4 : xs;
+      seg_a_len = xs < 0 ? 4 : min(RP, NX - xs);
+    }
+
     // asynchronous loads of the planes kk, kk + 1 into this thread's staging slot
     auto issue2 = [&](int kk) {
+      if constexpr (BULK) {
+        if (row_src) {
+          const float *src = row_src + size_t(zwrap(kk + my_dz)) * plane_n;
+          if constexpr (STG == kStageBulk) {
+            mbar_arrive_expect_tx(bar, RP * sizeof(float));
+            bulk_g2s(my_dst, src + seg_a_x, uint32_t(seg_a_len) * sizeof(float), bar);
+            if (seg_a_len < RP)
+              bulk_g2s(my_dst + uint32_t(seg_a_len) * sizeof(float), src, uint32_t(RP - seg_a_len) * sizeof(float),
+                       bar);
+          } else {
+#pragma unroll
+            for (int j = 0; j < RP / 4; ++j) {
+              const int xo = 4 * j;
+              cp_async16(my_dst + 16u * j, xo < seg_a_len ? src + seg_a_x + xo : src + (xo - seg_a_len));
+            }
+            cp_async_commit();
+            cp_async_mbar_arrive(bar);
+          }
+        }
+        return;
+      }
       const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n,
                      b2 = uint32_t(zwrap(kk + 2)) * plane_n;
       const float *S0 = a.s[0];
@@ -506,8 +672,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
     // finished values of the planes kk, kk + 1 from the staged loads
     auto finish2 = [&](int kk) -> Pair2 {
       const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n;
-      cp_async_wait_all();
-      auto ld = [&](int f) { return stg[f * EXY + t]; };
+      const float *R = stg + ey * RP + ex + 3;   // bulk: own element of the first row block
+      if constexpr (BULK) {
+        if (!mbar_wait(bar, phase)) bad = true;
+        phase ^= 1;
+      } else {
+        cp_async_wait_all();
+      }
+      auto ld = [&](int f) { return BULK ? R[bulk_offset<EY, RP>(f)] : stg[f * EXY + t]; };
       const float2 dr = make_float2(ld(SF_DR0), ld(SF_DR1));
       const float2 drx = make_float2(ld(SF_DRX0), ld(SF_DRX1));
       const float2 dry = make_float2(ld(SF_DRY0), ld(SF_DRY1));
@@ -575,6 +747,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
     // one pair below the run supplies the values carried into its first plane
     issue2(z0 - 2);
     Pair2 P = finish2(z0 - 2);
+    // bulk rows are read by neighbours: all reads done before the slot is refilled
+    if (BULK && __syncthreads_or(bad)) return staging_abort();
     issue2(z0);
     store_pair(0, P);
     float gz_m = 0.0f, txz_m = 0.0f, tyz_m = 0.0f, tzz_k = 0.0f, bulk_k = 0.0f;
@@ -593,9 +767,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
         }
       }
       const Pair2 Q = finish2(k + 2);
-      if (k + 2 < z1) issue2(k + 4);   // the next iteration's pair; overlaps this flux work
+      if (!BULK && k + 2 < z1) issue2(k + 4);   // the next iteration's pair; overlaps this flux work
       store_pair(slot ^ 1, Q);
-      __syncthreads();
+      if (BULK) {
+        if (__syncthreads_or(bad)) return staging_abort();
+        if (k + 2 < z1) issue2(k + 4);
+      } else {
+        __syncthreads();
+      }
       const float2 *Ps = sm + slot * 6 * EXY;
       const float2 *Qs = sm + (slot ^ 1) * 6 * EXY;
       const float2 gx_xm = Ps[GX * EXY + eXm], vx_xm = Ps[VX * EXY + eXm];
@@ -758,12 +937,31 @@ constexpr int stage_min_ctas() {
   return min_ctas<real, (TX + 2) * (TY + 2)>();
 }
 
+// Bulk row staging needs 16-byte aligned rows: x extents a multiple of 4 of
+// at least TX + 8 cells (so a row crosses the periodic seam at most once) and
+// 16-byte aligned fields.
+template <int TX, int STAGE, bool NOISE>
+bool bulk_staging_ok(const StageArgs<float> &a) {
+  const auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (a.c.nx % 4 != 0 || a.c.nx < TX + 8) return false;
+  for (int j = 0; j < 4; ++j)
+    if (!al(a.s[j])) return false;
+  if (a.pp && !al(a.pp)) return false;
+  if (NOISE && STAGE != 0)
+    for (int j = 0; j < 6; ++j)
+      if (!al(a.noise_in[j])) return false;
+  return true;
+}
+
 template <int TX, int TY, int STAGE, bool NOISE, typename real>
-void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream) {
+void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream, int stage_copy) {
   constexpr int EXY = (TX + 2) * (TY + 2);
   if constexpr (use_pair_kernel<real, TX>()) {
-    const size_t smem = 18 * EXY * sizeof(float2) + kStageFields * EXY * sizeof(float);
-    auto kern = k_rk3_stage_z2<TX, TY, STAGE, NOISE>;
+    const int stg = stage_copy != kStageThread && bulk_staging_ok<TX, STAGE, NOISE>(a) ? stage_copy : kStageThread;
+    const size_t smem = stg != kStageThread ? z2_smem_bytes<TX, TY, true>() : z2_smem_bytes<TX, TY, false>();
+    auto kern = stg == kStageBulk     ? k_rk3_stage_z2<TX, TY, STAGE, NOISE, kStageBulk>
+                : stg == kStageRows16 ? k_rk3_stage_z2<TX, TY, STAGE, NOISE, kStageRows16>
+                                      : k_rk3_stage_z2<TX, TY, STAGE, NOISE, kStageThread>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     kern<<<ctas, EXY, smem, stream>>>(a);
   } else {
@@ -809,10 +1007,11 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   a.c = fluid_consts<real>(ctx);
   a.step = ctx->d.step;
   a.partials = ctx->d.partials;
+  a.status = ctx->d.status;
   const StageLayout l = stage_layout_v<real, V>(ctx->p, zchunk_for(ctx), ctx->sm_count);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
-  launch_stage_kernel<TX, TY, STAGE, NOISE>(a, l.ctas, ctx->stream);
+  launch_stage_kernel<TX, TY, STAGE, NOISE>(a, l.ctas, ctx->stream, ctx->stage_copy);
   return cudaGetLastError();
 }
 
@@ -997,6 +1196,19 @@ bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk) {
   return true;
 }
 
+int stage_copy_active(const ic_ctx *ctx) {
+  if (ctx->p.precision != IC_FP32 || ctx->tile_variant != 0 || !ctx->stage_copy) return 0;
+  if (ctx->p.nx % 4 != 0 || ctx->p.nx < TileShape<float, 0>::TX + 8) return 0;
+  const auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  for (int b = 0; b < 3; ++b)
+    for (int j = 0; j < 4; ++j)
+      if (!al(ctx->U[b][j])) return 0;
+  if (!al(ctx->pp)) return 0;
+  for (int j = 0; j < 12; ++j)
+    if (ctx->noise[j] && !al(ctx->noise[j])) return 0;
+  return ctx->stage_copy;
+}
+
 void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk) {
   const bool f = ctx->p.precision == IC_FP32, v1 = ctx->tile_variant == 1;
   *tx = v1 ? 16 : 32;
@@ -1030,17 +1242,18 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
   a.c = c;
   a.step = step;
   a.partials = partials;
+  a.status = nullptr;
   const StageLayout l = stage_layout_v<real, 0>(p, std::min<int>(p.nz, IC_ZCHUNK), 1 << 20);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
   const bool noise_on = p.kT > 0.0;
   switch (stage * 2 + (noise_on ? 1 : 0)) {
-    case 0: launch_stage_kernel<TX, TY, 0, false>(a, l.ctas, stream); break;
-    case 1: launch_stage_kernel<TX, TY, 0, true>(a, l.ctas, stream); break;
-    case 2: launch_stage_kernel<TX, TY, 1, false>(a, l.ctas, stream); break;
-    case 3: launch_stage_kernel<TX, TY, 1, true>(a, l.ctas, stream); break;
-    case 4: launch_stage_kernel<TX, TY, 2, false>(a, l.ctas, stream); break;
-    default: launch_stage_kernel<TX, TY, 2, true>(a, l.ctas, stream); break;
+    case 0: launch_stage_kernel<TX, TY, 0, false>(a, l.ctas, stream, kDefaultStageCopy); break;
+    case 1: launch_stage_kernel<TX, TY, 0, true>(a, l.ctas, stream, kDefaultStageCopy); break;
+    case 2: launch_stage_kernel<TX, TY, 1, false>(a, l.ctas, stream, kDefaultStageCopy); break;
+    case 3: launch_stage_kernel<TX, TY, 1, true>(a, l.ctas, stream, kDefaultStageCopy); break;
+    case 4: launch_stage_kernel<TX, TY, 2, false>(a, l.ctas, stream, kDefaultStageCopy); break;
+    default: launch_stage_kernel<TX, TY, 2, true>(a, l.ctas, stream, kDefaultStageCopy); break;
   }
   return cudaGetLastError();
 }

@@ -18,6 +18,9 @@ constexpr double kSkin = 1.0;          // neighbour-list skin in units of h
 constexpr int kStatusNonfinite = 1;    // device status bits
 constexpr int kStatusNbrOverflow = 2;
 constexpr int kStatusSkin = 4;
+constexpr int kStatusStaging = 8;     // a bulk copy into shared memory did not land in time
+// loads of the FP32 wide-tile stage kernel (IC_STAGE_COPY_THREAD / _BULK / _ROWS16)
+constexpr int kDefaultStageCopy = 0;
 
 // Per-stage constants of the fluid kernel, derived on the host in FP64 and
 // handed to the kernel in its working precision.
@@ -162,6 +165,7 @@ struct ic_ctx {
   uint64_t generation = 0;                          // bumped whenever the captured step changes
   int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)
   int zchunk = 0;          // fewest z planes a stage-kernel CTA marches (0 = default)
+  int stage_copy = ic::kDefaultStageCopy;   // FP32 wide-tile loads (IC_STAGE_COPY_*), where the grid allows
   int sm_count = 1;        // SMs of the context's device
   std::string err;
   double omega = 0, force_amp = 0, kwave = 0;
@@ -224,6 +228,7 @@ size_t stage_ctas_raw(const ic_grid_params &p);
 // stage-kernel tiling: variant 0 (32-wide) or 1 (16-wide) and the z chunk
 constexpr int kMinZChunk = 8;
 bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk);
+int stage_copy_active(const ic_ctx *ctx);   // the staging mode the next FP32 wide-tile launch uses
 void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk);
 
 // particles (ic_particles.cu)

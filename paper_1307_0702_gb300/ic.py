@@ -256,6 +256,20 @@ class Grid:
         self._check(self._lib.ic_get_tile(self._ctx, *[ctypes.byref(x) for x in t]))
         return tuple(x.value for x in t)
 
+    STAGE_COPY = ("thread", "bulk", "rows16")
+
+    def set_stage_copy(self, mode):
+        """FP32 wide-tile stage loads: "thread" (per-thread 4-byte copies),
+        "bulk" (TMA bulk row copies) or "rows16" (16-byte row copies); the row
+        modes apply where the grid allows.  Results are unchanged."""
+        self._check(self._lib.ic_set_stage_copy(self._ctx, self.STAGE_COPY.index(mode)))
+
+    def stage_copy(self):
+        """The staging mode the next step's stage kernels use."""
+        v = ctypes.c_int()
+        self._check(self._lib.ic_get_stage_copy(self._ctx, ctypes.byref(v)))
+        return self.STAGE_COPY[v.value]
+
     def autotune(self, reps=5):
         """Time every stage-kernel tiling on scratch buffers, keep the fastest; returns it."""
         out = (ctypes.c_int * 3)()

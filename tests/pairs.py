@@ -12,13 +12,17 @@ def oracle_params(gp, **over):
     return oic.GridParams(**d)
 
 
-def run_gpu(gp, rho, g, parts=None, nsteps=1, weights=None, thermal_seed=None, chunks=None, tile=None):
+def run_gpu(gp, rho, g, parts=None, nsteps=1, weights=None, thermal_seed=None, chunks=None, tile=None,
+            stage_copy=None):
     from paper_1307_0702_gb300 import Grid
 
     out = {}
     with Grid(gp) as grid:
         if tile is not None:
             grid.set_tile(*tile)
+        if stage_copy is not None:
+            grid.set_stage_copy(stage_copy)
+        out["stage_copy"] = grid.stage_copy()
         grid.set_state(rho, g)
         if thermal_seed is not None:
             grid.init_thermal(thermal_seed, add=True)

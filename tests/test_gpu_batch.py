@@ -88,13 +88,17 @@ def test_tiling_leaves_results_unchanged(prec):
     from paper_1307_0702_gb300 import Grid
 
     runs = []
-    for tile in [(32, 32), (16, 8), (32, 8), (16, 16)]:
+    # (tile_x, zchunk, staging of the wide tile): x edge 40 admits the row modes in FP32
+    for tile_x, zchunk, copy in [(32, 32, "rows16"), (16, 8, "rows16"), (32, 8, "bulk"), (16, 16, "thread"),
+                                 (32, 16, "thread")]:
         gp, parts = W.many_particle_config((40, 20, 18), 9, kT=1e-3, wave_amp=2e-3, seed=5, precision=prec,
                                            k_spring=0.3)
         rho, g = W.standing_wave_fields(gp)
         with Grid(gp) as grid:
-            grid.set_tile(*tile)
-            assert grid.tile()[0] == tile[0] and grid.tile()[2] == min(tile[1], 18)
+            grid.set_tile(tile_x, zchunk)
+            grid.set_stage_copy(copy)
+            assert grid.tile()[0] == tile_x and grid.tile()[2] == min(zchunk, 18)
+            assert grid.stage_copy() == (copy if prec == "fp32" and tile_x == 32 else "thread")
             grid.set_state(rho, g)
             grid.init_thermal(4)
             grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])

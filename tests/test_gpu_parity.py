@@ -79,6 +79,32 @@ def test_particles_full_step(prec):
     check(errs, TOL[prec])
 
 
+def test_fp32_wide_tile_staging_modes():
+    """FP32 on a box whose x edge admits the row staging of the wide tile
+    (72 = two tiles + 8 cells, so rows cross the periodic seam at both ends;
+    30 rows = two tiles + 4), with noise, the mode drive and particles on the
+    seam: every staging mode against the oracle, and all alike bit for bit."""
+    gp = W.grid_params((72, 30, 14), kT=1e-3, wave_amp=2e-3, forcing="mode", zeta=0.3, seed=13, precision="fp32")
+    rho, g = W.random_fields(gp, seed=5)
+    parts = particles(6, (14, 30, 72), seed=4)
+    parts["q"][0, 0] = 0.2     # on the x seam
+    parts["q"][1, 0] = 71.9
+    w = np.linspace(0.5, 1.5, 4)
+    sim = run_oracle(gp, rho, g, parts, nsteps=4, weights=w, thermal_seed=3)
+    runs = []
+    for mode in ("thread", "bulk", "rows16"):
+        out = run_gpu(gp, rho, g, parts, nsteps=4, weights=w, thermal_seed=3, stage_copy=mode)
+        assert out["stage_copy"] == mode
+        check(compare(out, sim, gp, q0=parts["q"]), TOL["fp32"])
+        runs.append(out)
+    for other in runs[1:]:
+        assert np.array_equal(runs[0]["rho"], other["rho"])
+        for k in range(3):
+            assert np.array_equal(runs[0]["g"][k], other["g"][k])
+        for k in ("u", "q", "lam", "f_avg", "lam_avg"):
+            assert np.array_equal(runs[0][k], other[k]), k
+
+
 def test_particles_deterministic_single():
     """The single-particle standing wave in FP64 for 200 steps."""
     gp, parts, _ = W.single_particle_config(n=32, k_spring=0.25, mirror=True)
