@@ -524,18 +524,24 @@ def main():
 
     # end-to-end through the public API with host buffers: one step per call,
     # its averaging weight uploaded from pinned memory, the step's result -- the
-    # constraint force lambda on every particle -- read back every step
+    # constraint force lambda on every particle, and the device status word --
+    # copied back every step (ic_forces_async into one of two pinned slots) and
+    # read on the host while the next step runs (ic_forces_collect)
     e2e = None
     if not args.no_e2e:
         pinned_w = torch.ones(1, dtype=torch.float64).pin_memory().numpy()
-        outs = (torch.empty((npart, 3), dtype=torch.float64).pin_memory().numpy(), None, None)
+        lam = np.empty((npart, 3))
         grid.step(1, pinned_w)
-        grid.forces(outs)
+        grid.forces_async(0)
+        grid.forces_collect(0, lam)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for i in range(args.steps):
             grid.step(1, pinned_w)
-            grid.forces(outs)
+            grid.forces_async(i & 1)
+            if i:
+                grid.forces_collect((i - 1) & 1, lam)
+        grid.forces_collect((args.steps - 1) & 1, lam)
         barrier()
         el = time.perf_counter() - t0
         tt = torch.tensor([el], dtype=torch.float64, device="cuda")

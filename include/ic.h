@@ -138,6 +138,18 @@ ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w);
  * fluid force on each particle (substep 4: dg = dt (lambda + F)); u; q. */
 ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q);
 
+/* Pipelined read-back of lambda.  ic_forces_async queues on the stream a
+ * copy of the latest step's lambda and of the device status word into the
+ * context's pinned host slot (0 or 1) and returns without synchronising.
+ * ic_forces_collect waits for that slot's copy alone (not for work queued
+ * after it), writes lambda (n*3 doubles) to the host array (NULL skips) and
+ * returns the device error the status word carried, as ic_forces does.
+ * With both slots a caller reads every step's forces while the next step
+ * runs.  IC_ERR_ARG for a slot other than 0 or 1; IC_ERR_STATE when the slot
+ * holds no queued copy (each queued copy is collected once). */
+ic_status ic_forces_async(ic_ctx *ctx, int slot);
+ic_status ic_forces_collect(ic_ctx *ctx, int slot, double *lambda);
+
 /* Kernel-averaged fluid density J rho^{n+1} at q^{n+1/2} of the latest step
  * (n values; m_f = V J rho, App. A.2 substep 4), to a host array.  Its
  * equilibrium variance is rho0 kT / (c_p^2 V) (Eq. (eq:densityVariance)). */

@@ -56,6 +56,8 @@ SIGNATURES = {
     "ic_set_tile": (c_int, [c_void_p, c_int, c_int]),
     "ic_get_tile": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ic_set_stage_copy": (c_int, [c_void_p, c_int]),
+    "ic_forces_async": (c_int, [c_void_p, c_int]),
+    "ic_forces_collect": (c_int, [c_void_p, c_int, PD]),
     "ic_get_stage_copy": (c_int, [c_void_p, POINTER(c_int)]),
     "ic_autotune": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "ic_batch_autotune": (c_int, [c_void_p, c_int]),

@@ -559,6 +559,43 @@ ic_status ic_forces(ic_ctx *ctx, double *lambda, double *u, double *q) {
   return status_error(ctx, st);
 }
 
+ic_status ic_forces_async(ic_ctx *ctx, int slot) {
+  if (!ctx || slot < 0 || slot > 1) return IC_ERR_ARG;
+  const size_t n3 = 3 * size_t(ctx->ps.n), rb = n3 * ctx->real_size, need = rb + sizeof(int);
+  if (!ctx->fetch_done[slot]) IC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fetch_done[slot], cudaEventDisableTiming));
+  if (need > ctx->fetch_cap[slot]) {
+    IC_CUDA(ctx, cudaEventSynchronize(ctx->fetch_done[slot]));   // an earlier copy into the old buffer
+    if (ctx->fetch[slot]) cudaFreeHost(ctx->fetch[slot]);
+    ctx->fetch[slot] = nullptr;
+    ctx->fetch_cap[slot] = 0;
+    IC_CUDA(ctx, cudaMallocHost(&ctx->fetch[slot], need));
+    ctx->fetch_cap[slot] = need;
+  }
+  if (n3) IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot], ctx->ps.lam, rb, cudaMemcpyDeviceToHost, ctx->stream));
+  IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot] + rb, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  IC_CUDA(ctx, cudaEventRecord(ctx->fetch_done[slot], ctx->stream));
+  ctx->fetch_n[slot] = ctx->ps.n;
+  return IC_OK;
+}
+
+ic_status ic_forces_collect(ic_ctx *ctx, int slot, double *lambda) {
+  if (!ctx || slot < 0 || slot > 1) return IC_ERR_ARG;
+  if (ctx->fetch_n[slot] < 0) return fail(ctx, IC_ERR_STATE, "no read-back queued in slot %d", slot);
+  IC_CUDA(ctx, cudaEventSynchronize(ctx->fetch_done[slot]));
+  const size_t n3 = 3 * size_t(ctx->fetch_n[slot]), rb = n3 * ctx->real_size;
+  ctx->fetch_n[slot] = -1;
+  if (lambda && n3) {
+    if (ctx->p.precision == IC_FP32)
+      from_real<float>(ctx->fetch[slot], 0.0, lambda, n3);
+    else
+      from_real<double>(ctx->fetch[slot], 0.0, lambda, n3);
+  }
+  int st = 0;
+  std::memcpy(&st, ctx->fetch[slot] + rb, sizeof(int));
+  return status_error(ctx, st);
+}
+
 ic_status ic_particle_density(ic_ctx *ctx, double *jrho) {
   if (!ctx || !jrho) return IC_ERR_ARG;
   if (ctx->ps.n > 0) {
@@ -1432,6 +1469,10 @@ void ic_destroy(ic_ctx *ctx) {
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->download) cudaFreeHost(ctx->download);
+  for (int j = 0; j < 2; ++j) {
+    if (ctx->fetch_done[j]) cudaEventDestroy(ctx->fetch_done[j]);
+    if (ctx->fetch[j]) cudaFreeHost(ctx->fetch[j]);
+  }
   while (ctx->n_allocs > 0) dev_free(ctx, ctx->allocs[ctx->n_allocs - 1]);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

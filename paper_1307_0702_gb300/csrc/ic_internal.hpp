@@ -161,6 +161,11 @@ struct ic_ctx {
   cudaEvent_t staging_done = nullptr;
   unsigned char *download = nullptr;  // pinned host staging for per-step particle read-back
   size_t download_cap = 0;
+  // pipelined read-back slots (ic_forces_async / ic_forces_collect)
+  unsigned char *fetch[2] = {nullptr, nullptr};
+  size_t fetch_cap[2] = {0, 0};
+  cudaEvent_t fetch_done[2] = {nullptr, nullptr};
+  int fetch_n[2] = {-1, -1};            // particles of the queued copy, -1: none
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
   uint64_t generation = 0;                          // bumped whenever the captured step changes
   int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)

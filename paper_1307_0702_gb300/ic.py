@@ -146,6 +146,16 @@ class Grid:
         self._check(self._lib.ic_forces(self._ctx, _ptr(lam), _ptr(u), _ptr(q)))
         return lam, u, q
 
+    def forces_async(self, slot):
+        """Queue the read-back of this step's lambda into pinned slot 0 or 1 (no synchronisation)."""
+        self._check(self._lib.ic_forces_async(self._ctx, int(slot)))
+
+    def forces_collect(self, slot, out=None):
+        """Wait for the slot's queued read-back alone; lambda (n, 3) (into ``out`` if given)."""
+        lam = out if out is not None else np.empty((self.n_particles, 3))
+        self._check(self._lib.ic_forces_collect(self._ctx, int(slot), _ptr(lam)))
+        return lam
+
     def particle_density(self):
         """J rho^{n+1} per particle (n,)."""
         out = np.empty(self.n_particles)

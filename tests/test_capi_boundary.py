@@ -86,6 +86,9 @@ def test_invalid_parameters_rejected_without_cuda(lib):
     gp.plane_index = 40
     assert lib.ic_create_grid(ctypes.byref(gp), ctypes.byref(ctx)) == _lib.IC_ERR_ARG
     assert lib.ic_step(None, 1, None) == _lib.IC_ERR_ARG
+    assert lib.ic_forces_async(None, 0) == _lib.IC_ERR_ARG
+    assert lib.ic_forces_collect(None, 0, None) == _lib.IC_ERR_ARG
+    assert lib.ic_set_stage_copy(None, 0) == _lib.IC_ERR_ARG
     assert lib.ic_last_error(None) == b"null context"
 
 
