@@ -240,6 +240,16 @@ enum { IC_STAGE_COPY_THREAD = 0, IC_STAGE_COPY_BULK = 1, IC_STAGE_COPY_ROWS16 = 
 ic_status ic_set_stage_copy(ic_ctx *ctx, int mode);
 ic_status ic_get_stage_copy(const ic_ctx *ctx, int *mode);
 
+/* Verification entry point: the library's counter-based generator,
+ * Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11), which draws the
+ * stochastic stress (Sec. 4.2) and the thermal initial state, evaluated by
+ * the same device code for n counter/key pairs.  in: n*6 host words (ctr0,
+ * ctr1, ctr2, ctr3, key0, key1 per pair); out: n*4 host words.  Needs no
+ * context: runs on the current device with its own temporary buffers and
+ * synchronises it.  IC_ERR_ARG for n < 0, or a NULL array with n > 0;
+ * IC_ERR_OOM, IC_ERR_CUDA on failure. */
+ic_status ic_philox4x32_10(int n, const uint32_t *in, uint32_t *out);
+
 /* Kernel timing for measurement.  While enabled, ic_step launches without
  * CUDA graphs and brackets every kernel (and ic_adjoint_step every adjoint
  * kernel) with CUDA events on the context's stream.  ic_profile_read

@@ -13,6 +13,7 @@
 #include <array>
 #include <vector>
 
+#include "ic_device.cuh"
 #include "ic_internal.hpp"
 
 namespace ic {
@@ -313,6 +314,20 @@ ic_status launch_one_step(ic_ctx *ctx) {
   return IC_OK;
 }
 
+// Philox4x32-10 of n counter/key pairs (ic_philox4x32_10): the device code of
+// the noise and thermal draws, evaluated on given inputs.
+__global__ void k_philox_eval(int n, const uint32_t *in, uint32_t *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t *w = in + 6 * size_t(i);
+  const uint4 r = ic::philox4x32_10(make_uint4(w[0], w[1], w[2], w[3]), w[4], w[5]);
+  uint32_t *o = out + 4 * size_t(i);
+  o[0] = r.x;
+  o[1] = r.y;
+  o[2] = r.z;
+  o[3] = r.w;
+}
+
 }  // namespace
 
 extern "C" {
@@ -594,6 +609,27 @@ ic_status ic_forces_collect(ic_ctx *ctx, int slot, double *lambda) {
   int st = 0;
   std::memcpy(&st, ctx->fetch[slot] + rb, sizeof(int));
   return status_error(ctx, st);
+}
+
+ic_status ic_philox4x32_10(int n, const uint32_t *in, uint32_t *out) {
+  if (n < 0 || (n > 0 && (!in || !out))) return IC_ERR_ARG;
+  if (n == 0) return IC_OK;
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  if (cudaMalloc(&d_in, size_t(n) * 6 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&d_out, size_t(n) * 4 * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_in);
+    return IC_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpy(d_in, in, size_t(n) * 6 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_philox_eval<<<(n + 127) / 128, 128>>>(n, d_in, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, size_t(n) * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  return e == cudaSuccess ? IC_OK : IC_ERR_CUDA;
 }
 
 ic_status ic_particle_density(ic_ctx *ctx, double *jrho) {

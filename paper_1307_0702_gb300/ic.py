@@ -32,6 +32,19 @@ def _f64(a, shape=None):
     return a if shape is None else a.reshape(shape)
 
 
+def philox4x32_10(ctr_key):
+    """The library's Philox4x32-10 evaluated on the current device:
+    ctr_key (n, 6) uint32 rows (ctr0..ctr3, key0, key1) -> (n, 4) uint32."""
+    lib = _lib.load()
+    a = np.ascontiguousarray(np.asarray(ctr_key, dtype=np.uint32).reshape(-1, 6))
+    out = np.empty((a.shape[0], 4), dtype=np.uint32)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    st = lib.ic_philox4x32_10(a.shape[0], a.ctypes.data_as(u32), out.ctypes.data_as(u32))
+    if st != 0:
+        raise ICError(st, "ic_philox4x32_10 failed")
+    return out
+
+
 class Grid:
     """One simulation box (an ic_ctx).
 

@@ -26,7 +26,7 @@ def lib():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ic_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ic_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_calls():
@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
     from paper_1307_0702_gb300 import _lib
 
     out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (ic_[a-z_]+)", out))
+    exported = set(re.findall(r"\bT (ic_[a-z0-9_]+)", out))
     names = declared_functions()
     assert set(names) <= exported, set(names) - exported
     assert set(names) == set(_lib.SIGNATURES), "ctypes signatures must mirror the header"
@@ -89,6 +89,9 @@ def test_invalid_parameters_rejected_without_cuda(lib):
     assert lib.ic_forces_async(None, 0) == _lib.IC_ERR_ARG
     assert lib.ic_forces_collect(None, 0, None) == _lib.IC_ERR_ARG
     assert lib.ic_set_stage_copy(None, 0) == _lib.IC_ERR_ARG
+    assert lib.ic_philox4x32_10(-1, None, None) == _lib.IC_ERR_ARG
+    assert lib.ic_philox4x32_10(3, None, None) == _lib.IC_ERR_ARG
+    assert lib.ic_philox4x32_10(0, None, None) == _lib.IC_OK
     assert lib.ic_last_error(None) == b"null context"
 
 
