@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "ic_device.cuh"
 #include "ic_internal.hpp"
@@ -654,8 +655,28 @@ __global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_start(AdjParticle
 }
 
 // ---------------------------------------------------------------- host
+// d (drive amplitude of RK stage s of the given step) / d A
+double stage_dpdA(const ic_ctx *ctx, int64_t step, int s) {
+  const ic_grid_params &p = ctx->p;
+  const double gamma = (4.0 * p.eta / 3.0 + p.zeta) / (2.0 * p.rho0);
+  const int n_ax = p.wave_axis == 0 ? p.nx : (p.wave_axis == 1 ? p.ny : p.nz);
+  const double per_A = p.forcing == IC_FORCE_MODE ? 2.0 * gamma * ctx->omega : double(n_ax) * gamma * ctx->omega;
+  return per_A * std::sin(ctx->omega * (double(step) + kStageTimes[s]) * p.dt + p.wave_phase);
+}
+
+// The node a capturing stream added last (its single dependency), or null.
+cudaGraphNode_t captured_node(cudaStream_t st) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive || nd != 1)
+    return nullptr;
+  return deps[0];
+}
+
 template <typename real>
-cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
+cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight, AdjGraph *cap) {
   AdjointStore &A = ctx->adj;
   const ic_grid_params &p = ctx->p;
   const Geo G{p.nx, p.ny, p.nz};
@@ -715,9 +736,6 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
     }));
     IC_ADJ_TRY(vt(U3v));
   }
-  const double gamma = (4.0 * p.eta / 3.0 + p.zeta) / (2.0 * p.rho0);
-  const int n_ax = p.wave_axis == 0 ? p.nx : (p.wave_axis == 1 ? p.ny : p.nz);
-  const double per_A = p.forcing == IC_FORCE_MODE ? 2.0 * gamma * ctx->omega : double(n_ax) * gamma * ctx->omega;
   const real *cos_table = sizeof(real) == 4 ? (const real *)ctx->cos_table_f : (const real *)ctx->cos_table;
   for (int s = 2; s >= 0; --s) {
     StageAdjConsts k;
@@ -729,7 +747,7 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
     k.forcing = p.forcing;
     k.wave_axis = p.wave_axis;
     k.plane_index = p.plane_index;
-    k.dpdA = per_A * std::sin(ctx->omega * (double(t.step) + kStageTimes[s]) * p.dt + p.wave_phase);
+    k.dpdA = stage_dpdA(ctx, t.step, s);
     const State<real> Us = state_of<real>(Ustage[s]);
     StageIn<real> In;
     for (int j = 0; j < 4; ++j) In.lam[j] = bar[j];
@@ -739,15 +757,21 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
       k_adj_face_velocity<real><<<gblocks, kAdjThreads, 0, st>>>(Us, G, rho0, vel[0], vel[1], vel[2]);
       return cudaGetLastError();
     }));
+    constexpr size_t smem = size_t(kTileFields) * kHaloCells * sizeof(real);
+    const dim3 tiles((p.nx + kTileX - 1) / kTileX, (p.ny + kTileY - 1) / kTileY, (p.nz + kTileZ - 1) / kTileZ);
     IC_ADJ_TRY(timed_launch(ctx, kClassStage, [&] {
-      constexpr size_t smem = size_t(kTileFields) * kHaloCells * sizeof(real);
       if (smem > 48 * 1024) cudaFuncSetAttribute(k_adj_stage_rates<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(smem));
-      const dim3 tiles((p.nx + kTileX - 1) / kTileX, (p.ny + kTileY - 1) / kTileY, (p.nz + kTileZ - 1) / kTileZ);
       k_adj_stage_rates<real><<<tiles, kAdjThreads, smem, st>>>(In, G, k, cos_table, gp[0], gp[1], gp[2], rf[0],
                                                                 rf[1], rf[2], pibar, A.gA);
       return cudaGetLastError();
     }));
+    if (cap) {   // the drive derivative changes with the step: keep the node
+      const cudaGraphNode_t nd = captured_node(st);
+      if (!nd) return cudaErrorStreamCaptureUnsupported;
+      cap->rates[s].keep(nd, reinterpret_cast<const void *>(k_adj_stage_rates<real>), tiles, dim3(kAdjThreads), smem, In,
+                         G, k, cos_table, gp[0], gp[1], gp[2], rf[0], rf[1], rf[2], pibar, A.gA);
+    }
     if (n > 0) {
       IC_ADJ_TRY(timed_launch(ctx, kClassParticles, [&] {
         k_adj_p_stage<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, Us, G, pc, pibar, bar[1], bar[2], bar[3],
@@ -768,6 +792,12 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
       k_adj_p_start<real><<<pblocks, kAdjParticleThreads, 0, st>>>(P, state_of<real>(Un), G, pc, vb, weight);
       return cudaGetLastError();
     }));
+    if (cap) {   // the weight changes with the step: keep the node
+      const cudaGraphNode_t nd = captured_node(st);
+      if (!nd) return cudaErrorStreamCaptureUnsupported;
+      cap->start.keep(nd, reinterpret_cast<const void *>(k_adj_p_start<real>), dim3(pblocks), dim3(kAdjParticleThreads),
+                      0, P, state_of<real>(Un), G, pc, vb, weight);
+    }
     IC_ADJ_TRY(vt(Un));
   }
 #undef IC_ADJ_TRY
@@ -776,9 +806,29 @@ cudaError_t adjoint_step_t(ic_ctx *ctx, const AdjStepTape &t, double weight) {
 
 }  // namespace
 
-cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight) {
-  if (ctx->p.precision == IC_FP32) return adjoint_step_t<float>(ctx, t, weight);
-  return adjoint_step_t<double>(ctx, t, weight);
+cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight, AdjGraph *cap) {
+  if (ctx->p.precision == IC_FP32) return adjoint_step_t<float>(ctx, t, weight, cap);
+  return adjoint_step_t<double>(ctx, t, weight, cap);
+}
+
+cudaError_t update_adjoint_graph(const ic_ctx *ctx, AdjGraph &g, const AdjStepTape &t, double weight) {
+  for (int s = 0; s < 3; ++s) {
+    KeptNode &n = g.rates[s];
+    if (!n.node) continue;
+    if (n.arg.size() != 12 || n.arg[2].size() != sizeof(StageAdjConsts)) return cudaErrorInvalidValue;
+    StageAdjConsts k;
+    std::memcpy(&k, n.arg[2].data(), sizeof(k));
+    k.dpdA = stage_dpdA(ctx, t.step, s);
+    std::memcpy(n.arg[2].data(), &k, sizeof(k));
+    const cudaError_t e = cudaGraphExecKernelNodeSetParams(g.exec, n.node, &n.p);
+    if (e != cudaSuccess) return e;
+  }
+  if (g.start.node) {
+    if (g.start.arg.size() != 6 || g.start.arg[5].size() != sizeof(double)) return cudaErrorInvalidValue;
+    std::memcpy(g.start.arg[5].data(), &weight, sizeof(weight));
+    return cudaGraphExecKernelNodeSetParams(g.exec, g.start.node, &g.start.p);
+  }
+  return cudaSuccess;
 }
 
 }  // namespace ic

@@ -79,6 +79,14 @@ ic_status cuda_fail(ic_ctx *ctx, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+void drop_adj_graphs(ic_ctx *ctx) {
+  for (auto &kv : ctx->adj_graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  ctx->adj_graphs.clear();
+}
+
 void invalidate_graphs(ic_ctx *ctx) {
   ++ctx->generation;
   for (int i = 0; i < 2; ++i)
@@ -86,6 +94,7 @@ void invalidate_graphs(ic_ctx *ctx) {
       cudaGraphExecDestroy(ctx->graph[i]);
       ctx->graph[i] = nullptr;
     }
+  drop_adj_graphs(ctx);
 }
 
 using ic::timed_launch;
@@ -147,6 +156,39 @@ cudaError_t enqueue_step(ic_ctx *ctx, int cur, bool record = false) {
 bool graphs_enabled() {
   const char *v = std::getenv("IC_NO_GRAPH");
   return !(v && v[0] == '1');
+}
+
+constexpr size_t kMaxAdjGraphs = 256;
+
+// The reverse sweep of one recorded step: its CUDA graph for this tape
+// (captured on first use, its per-step arguments updated after that), or
+// the kernels one by one while profiling.
+cudaError_t run_adjoint_step(ic_ctx *ctx, const ic::AdjStepTape &t, double weight) {
+  if (!graphs_enabled() || ctx->profiling) return ic::launch_adjoint_step(ctx, t, weight);
+  const void *key = t.Un[0];
+  auto it = ctx->adj_graphs.find(key);
+  cudaError_t e = cudaSuccess;
+  if (it == ctx->adj_graphs.end()) {
+    if (ctx->adj_graphs.size() >= kMaxAdjGraphs) drop_adj_graphs(ctx);   // tapes at ever new addresses
+    ic::AdjGraph g;
+    e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = ic::launch_adjoint_step(ctx, t, weight, &g);
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g.graph);
+    e = le != cudaSuccess ? le : ce;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      cudaGetLastError();
+      return e;
+    }
+    it = ctx->adj_graphs.emplace(key, std::move(g)).first;
+  } else {
+    e = ic::update_adjoint_graph(ctx, it->second, t, weight);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGraphLaunch(it->second.exec, ctx->stream);
 }
 
 template <typename real>
@@ -971,6 +1013,7 @@ ic_status ic_adjoint_enable(ic_ctx *ctx) {
   if (ctx->p.kT != 0.0) return fail(ctx, IC_ERR_STATE, "the adjoint covers the deterministic step (kT = 0)");
   ic::AdjointStore &A = ctx->adj;
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  invalidate_graphs(ctx);   // the reverse-step graphs point at the buffers freed here
   dev_free(ctx, A.grid_block);
   dev_free(ctx, A.part_block);
   A = ic::AdjointStore{};
@@ -1039,7 +1082,7 @@ ic_status ic_adjoint_step(ic_ctx *ctx, double weight) {
   if (ctx->adj.rec_cur < 0) return fail(ctx, IC_ERR_STATE, "no recorded step to reverse (call ic_step_record)");
   if (ctx->adj.rec_cur != 1 - ctx->cur)
     return fail(ctx, IC_ERR_STATE, "the state moved on after ic_step_record; record the step again");
-  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, context_tape(ctx), weight));
+  IC_CUDA(ctx, run_adjoint_step(ctx, context_tape(ctx), weight));
   ctx->adj.rec_cur = -1;
   return IC_OK;
 }
@@ -1109,7 +1152,7 @@ ic_status ic_adjoint_step_tape(ic_ctx *ctx, const void *dev_buf, double weight) 
       return fail(ctx, IC_ERR_ARG, "not a step tape of this context's grid and particles");
     L.t.step = hd.step;
   }
-  IC_CUDA(ctx, ic::launch_adjoint_step(ctx, L.t, weight));
+  IC_CUDA(ctx, run_adjoint_step(ctx, L.t, weight));
   return IC_OK;
 }
 

@@ -131,6 +131,43 @@ struct AdjointStore {
   void *grid_block = nullptr, *part_block = nullptr;
 };
 
+
+// A captured kernel node whose scalar arguments change between launches of
+// its graph: the node, its launch configuration and byte copies of its
+// arguments (kernelParams points into them).
+struct KeptNode {
+  cudaGraphNode_t node = nullptr;
+  cudaKernelNodeParams p{};
+  std::vector<std::vector<unsigned char>> arg;
+  std::vector<void *> ptr;
+  template <typename... A>
+  void keep(cudaGraphNode_t n, const void *func, dim3 grid, dim3 block, size_t smem, const A &...a) {
+    node = n;
+    arg.clear();
+    (arg.emplace_back(reinterpret_cast<const unsigned char *>(&a), reinterpret_cast<const unsigned char *>(&a) + sizeof(A)),
+     ...);
+    ptr.resize(arg.size());
+    for (size_t i = 0; i < arg.size(); ++i) ptr[i] = arg[i].data();
+    p.func = const_cast<void *>(func);
+    p.gridDim = grid;
+    p.blockDim = block;
+    p.sharedMemBytes = static_cast<unsigned int>(smem);
+    p.kernelParams = ptr.data();
+    p.extra = nullptr;
+  }
+};
+
+// The reverse sweep of one recorded step as a CUDA graph (one per tape, keyed
+// by its U^n buffer): the stage transposes (whose drive derivative depends on
+// the step) and the particles' start (the objective's weight) are updated
+// before each launch.
+struct AdjGraph {
+  cudaGraph_t graph = nullptr;   // kept: the updated nodes belong to it
+  cudaGraphExec_t exec = nullptr;
+  KeptNode rates[3];   // by RK stage
+  KeptNode start;
+};
+
 }  // namespace ic
 
 struct ic_ctx {
@@ -146,6 +183,7 @@ struct ic_ctx {
   ic::AdjointStore adj{};
   std::unordered_map<uintptr_t, std::pair<int64_t, int>> snapshots;   // device snapshots saved: step, particles
   std::unordered_map<uintptr_t, std::pair<int64_t, int>> tapes;       // step tapes recorded: step, particles
+  std::unordered_map<const void *, ic::AdjGraph> adj_graphs;           // reverse-step graphs by tape
   void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
   void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
   bool any_spring = false;  // some particle is tethered: the stage force source is launched
@@ -251,7 +289,10 @@ struct AdjStepTape {
   const void *q_n, *q_half, *u_n, *force, *dg;
   int64_t step;
 };
-cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight);
+// cap: while capturing, the graph whose per-launch nodes are recorded
+cudaError_t launch_adjoint_step(ic_ctx *ctx, const AdjStepTape &t, double weight, AdjGraph *cap = nullptr);
+// rewrites the per-launch arguments of a captured reverse step for tape t
+cudaError_t update_adjoint_graph(const ic_ctx *ctx, AdjGraph &g, const AdjStepTape &t, double weight);
 void positions_to_device(const ic_ctx *ctx, const double *q, size_t n3, void *out);
 void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q);
 }  // namespace ic
