@@ -321,7 +321,11 @@ ic_status ic_step_record(ic_ctx *ctx);
 /* Reverses the step recorded last: the adjoint held by the context goes from
  * the state after that step to the state before it, and the gradients gain
  * the step's terms, weight * sum_p d_p . F_p included.  IC_ERR_STATE if no
- * step is recorded or the state has moved on since. */
+ * step is recorded or the state has moved on since.  Enqueues work only: the
+ * reverse step runs as a CUDA graph per set of recorded buffers (captured on
+ * first use; the step's drive derivative and weight are rewritten in it
+ * before each launch), or kernel by kernel while profiling or with the
+ * environment variable IC_NO_GRAPH=1. */
 ic_status ic_adjoint_step(ic_ctx *ctx, double weight);
 /* Reads (each pointer may be NULL): grad_m_e[n], grad_eps[n], *grad_A, the
  * adjoint of delta rho and g (nx*ny*nz doubles each, [z][y][x]) and of q and u
