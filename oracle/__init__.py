@@ -33,8 +33,10 @@ Parity status
 -------------
 Every function here is pinned by a ``-m "not gpu"`` test against something
 other than itself (closed forms, invariants, published known answers, brute
-force), except the rounding order of the nonlinear advection flux, whose
-discretisation the paper leaves to a reference that is not available: the
-advective flux form is a reading, "parity unpinned" beyond the invariants it
-must satisfy (mass and momentum conservation, Galilean-free linear limit).
+force).  The nonlinear advection flux, whose discretisation the paper leaves
+to a reference that is not available, is pinned to the paper's continuum
+term -div(g v) (Eq. (eq:consvMom)): on a smooth flow its error falls at
+second order in h, against exact spectral derivatives.  Which second-order
+form (here products of two-point averages) is a reading; its rounding order
+is checked against the GPU only by self-consistency.
 """
