@@ -240,10 +240,10 @@ ic_status check_device_status(ic_ctx *ctx) {
 ic_status status_error(ic_ctx *ctx, int st) {
   if (st == 0) return IC_OK;
   IC_CUDA(ctx, cudaMemset(ctx->d.status, 0, sizeof(int)));
+  if (st & ic::kStatusStaging)   // first: the stages it stopped leave the rest of the step undefined
+    return fail(ctx, IC_ERR_TIMEOUT, "a bulk copy into a stage kernel's shared memory did not complete");
   if (st & ic::kStatusNonfinite)
     return fail(ctx, IC_ERR_NONFINITE, "state became non-finite (check the CFL numbers c dt/h and c_p dt/h)");
-  if (st & ic::kStatusStaging)
-    return fail(ctx, IC_ERR_TIMEOUT, "a bulk copy into a stage kernel's shared memory did not complete");
   if (st & ic::kStatusNbrOverflow)
     return fail(ctx, IC_ERR_CAPACITY, "more than %d particles within the neighbour cutoff of one particle",
                 ic::kMaxNeighbours);

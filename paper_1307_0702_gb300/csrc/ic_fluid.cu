@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ic_device.cuh"
 #include "ic_internal.hpp"
@@ -55,6 +56,8 @@ struct StageArgs {
   const int64_t *step;
   double *partials;                // stage 3: per-CTA sum of delta rho cos(k x)
   int *status;                     // error bits (bulk staging timeout), or null
+  int stall;                       // row staging: arrivals expected beyond the row threads' (0;
+                                   // 1 only to test the bounded wait: nothing makes it)
   int ncols_x, ncols_y;            // tile columns along x and y
 };
 
@@ -431,13 +434,16 @@ __device__ __forceinline__ uint64_t global_ns() {
   return v;
 }
 // Waits for the phase of the given parity to complete; gives up (false)
-// after about a second, so that a copy that never lands cannot hang the GPU.
+// after about a second (or 2^24 tries, should the timer not advance), so that
+// a copy that never lands cannot hang the GPU.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  while (!mbar_test(bar, parity))
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_test(bar, parity)) return true;
     if (global_ns() - t0 > 1000000000ull) return false;
-  return true;
+  }
+  return false;
 }
 
 // staging slot of one plane pair: the thread's own values, [field][EXY]
@@ -556,7 +562,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       my_fp += BF_GX0;
       if (!has_pp && my_fp >= BF_PP0) my_fp += 2;
     }
-    if (t == 0) mbar_init(bar, uint32_t(nrows));
+    if (t == 0) mbar_init(bar, uint32_t(nrows + a.stall));
     __syncthreads();
   }
   const float *my_field = nullptr;
@@ -937,6 +943,14 @@ constexpr int stage_min_ctas() {
   return min_ctas<real, (TX + 2) * (TY + 2)>();
 }
 
+// The bounded wait of the row staging under test: IC_STAGE_STALL_TEST=1 makes
+// each CTA's mbarrier expect one arrival that no thread makes, so every wait
+// runs out (about a second) and the launch reports IC_ERR_TIMEOUT.
+int stage_stall_test() {
+  const char *v = std::getenv("IC_STAGE_STALL_TEST");
+  return v && v[0] == '1' ? 1 : 0;
+}
+
 // Bulk row staging needs 16-byte aligned rows: x extents a multiple of 4 of
 // at least TX + 8 cells (so a row crosses the periodic seam at most once) and
 // 16-byte aligned fields.
@@ -1008,6 +1022,7 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   a.step = ctx->d.step;
   a.partials = ctx->d.partials;
   a.status = ctx->d.status;
+  a.stall = stage_stall_test();
   const StageLayout l = stage_layout_v<real, V>(ctx->p, zchunk_for(ctx), ctx->sm_count);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
@@ -1243,6 +1258,7 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
   a.step = step;
   a.partials = partials;
   a.status = nullptr;
+  a.stall = 0;
   const StageLayout l = stage_layout_v<real, 0>(p, std::min<int>(p.nz, IC_ZCHUNK), 1 << 20);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
