@@ -115,10 +115,21 @@ cudaError_t enqueue_step(ic_ctx *ctx, int cur, bool record = false) {
       te = cudaMemcpyAsync(dst[j], src[j], fb, cudaMemcpyDeviceToDevice, ctx->stream);
     return te;
   };
+  // trace names of the substeps (App. A.2)
+  static const char *const kStageName[3] = {"IC RK3 stage 1", "IC RK3 stage 2", "IC RK3 stage 3"};
+  static const char *const kPhaseName[6][3] = {
+      {"IC substeps 1-2: half step, tether force, stencils", "", ""},
+      {"IC particle pressure, stage 1", "IC particle pressure, stage 2", "IC particle pressure, stage 3"},
+      {"IC tether source, stage 1", "IC tether source, stage 2", "IC tether source, stage 3"},
+      {"IC substeps 4-5: impulse", "", ""},
+      {"IC substep 6: momentum correction", "", ""},
+      {"IC substep 7: positions, force sums", "", ""}};
   auto fluid = [&](int stage, void *const *s, void *const *n, void *const *o) {
+    const ic::TraceRange tr(kStageName[stage]);
     return timed_launch(ctx, 0, [&] { return ic::launch_stage(ctx, stage, s, n, o); });
   };
   auto part = [&](ic::ParticlePhase ph, int stage, void *const *tgt) {
+    const ic::TraceRange tr(kPhaseName[ph][stage]);
     return timed_launch(ctx, 1, [&] { return ic::launch_particles(ctx, ph, stage, U0, tgt); });
   };
 #define IC_TRY(x)                           \
@@ -563,6 +574,7 @@ ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u,
 ic_status ic_step(ic_ctx *ctx, int nsteps, const double *w) {
   if (!ctx || nsteps < 0) return IC_ERR_ARG;
   if (nsteps == 0) return IC_OK;
+  const ic::TraceRange tr("ic_step");
   {
     const ic_status st = upload_weights(ctx, nsteps, w);
     if (st) return st;
@@ -1061,6 +1073,7 @@ ic_status ic_adjoint_reset(ic_ctx *ctx, const double *direction) {
 }
 
 ic_status ic_step_record(ic_ctx *ctx) {
+  const ic::TraceRange tr("ic_step_record");
   if (!ctx) return IC_ERR_ARG;
   ic_status st = adjoint_ready(ctx);
   if (st) return st;
@@ -1076,6 +1089,7 @@ ic_status ic_step_record(ic_ctx *ctx) {
 }
 
 ic_status ic_adjoint_step(ic_ctx *ctx, double weight) {
+  const ic::TraceRange tr("ic_adjoint_step");
   if (!ctx) return IC_ERR_ARG;
   const ic_status st = adjoint_ready(ctx);
   if (st) return st;
@@ -1094,6 +1108,7 @@ ic_status ic_tape_size(const ic_ctx *ctx, size_t *bytes) {
 }
 
 ic_status ic_step_record_tape(ic_ctx *ctx, void *dev_buf) {
+  const ic::TraceRange tr("ic_step_record_tape");
   if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
   ic_status st = ic_step_record(ctx);
   if (st) return st;
@@ -1136,6 +1151,7 @@ ic_status ic_step_record_tape(ic_ctx *ctx, void *dev_buf) {
 }
 
 ic_status ic_adjoint_step_tape(ic_ctx *ctx, const void *dev_buf, double weight) {
+  const ic::TraceRange tr("ic_adjoint_step_tape");
   if (!ctx || !dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return IC_ERR_ARG;
   ic_status st = adjoint_ready(ctx);
   if (st) return st;
@@ -1296,6 +1312,7 @@ ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out) {
 }
 
 ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
+  const ic::TraceRange tr("ic_batch_step");
   if (!b || nsteps < 0) return IC_ERR_ARG;
   if (nsteps == 0) return IC_OK;
   const int parity = b->ctxs[0]->cur;
@@ -1393,6 +1410,7 @@ ic_status ic_get_tile(const ic_ctx *ctx, int *tile_x, int *tile_y, int *zchunk) 
 }
 
 ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
+  const ic::TraceRange tr("ic_autotune");
   if (!ctx || reps <= 0) return IC_ERR_ARG;
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   // the stage kernels of one step, U^n (buffer cur) only read: stage 1 writes

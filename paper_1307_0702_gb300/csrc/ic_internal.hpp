@@ -9,6 +9,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ic.h"
 
 namespace ic {
@@ -131,6 +133,15 @@ struct AdjointStore {
   void *grid_block = nullptr, *part_block = nullptr;
 };
 
+
+// A named NVTX range for the lifetime of the object (host-side tracing; a
+// no-op unless a profiler is attached).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // A captured kernel node whose scalar arguments change between launches of
 // its graph: the node, its launch configuration and byte copies of its
