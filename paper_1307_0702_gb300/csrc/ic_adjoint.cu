@@ -501,16 +501,20 @@ __global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_final(AdjParticle
   if (p >= P.n) return;
   Sten<real> S;
   stencil_at<real>(P.q_half + 3 * p, pc, S);
-  double qh[3] = {0, 0, 0};
-#pragma unroll 1
+  // every gather before any spread, so that the loads are not held behind
+  // the atomics (the arithmetic is the same, in the same order)
+  double J[3], dJ[3][3], jb[3];
   for (int a = 0; a < 3; ++a) {
-    const double jb = 0.5 * double(pc.dt) * P.qbar[3 * p + a];
-    double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Unew, G, pc.rho0, a}, J, dJ);
-    for (int c = 0; c < 3; ++c) qh[c] += jb * dJ[c];
-    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb);
+    jb[a] = 0.5 * double(pc.dt) * P.qbar[3 * p + a];
+    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Unew, G, pc.rho0, a}, J[a], dJ[a]);
+  }
+  double qh[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) qh[c] += jb[a] * dJ[a][c];
+  for (int a = 0; a < 3; ++a) {
+    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb[a]);
     if (lane == 0) {
-      P.jvnh[3 * p + a] = jb;
+      P.jvnh[3 * p + a] = jb[a];
       P.fbar[3 * p + a] = 0.0;
     }
   }
@@ -591,20 +595,20 @@ __global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_stage(AdjParticle
   stencil_at<real>(P.q_half + 3 * p, pc, S);
   const double inv_h3 = double(pc.inv_h3), vol = double(pc.vol), eps = double(P.eps[p]);
   double qh[3] = {P.qhbar[3 * p], P.qhbar[3 * p + 1], P.qhbar[3 * p + 2]};
-  double Jp, dJp[3], Jr, dJr[3];
+  // every gather before the spread (the arithmetic is the same, in the same order)
+  double Jp, dJp[3], Jr, dJr[3], Jf[3], dJf[3][3];
   interp_grad<real>(S, 0, G, lane, FieldV<real>{pibar, real(1)}, Jp, dJp);
   interp_grad<real>(S, 0, G, lane, FieldV<real>{Us.d, real(1)}, Jr, dJr);
+  for (int a = 0; a < 3; ++a) interp_grad<real>(S, 1 + a, G, lane, FieldV<real>{gb[a], coef}, Jf[a], dJf[a]);
   const double ob = Jp * inv_h3, om = eps * vol * Jr;
-  spread_T<real>(S, 0, G, lane, rhox, eps * vol * ob);
   for (int c = 0; c < 3; ++c) qh[c] += om * inv_h3 * dJp[c] + eps * vol * ob * dJr[c];
   double fb[3];
   for (int a = 0; a < 3; ++a) {
-    double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, lane, FieldV<real>{gb[a], coef}, J, dJ);
-    fb[a] = J * inv_h3;
+    fb[a] = Jf[a] * inv_h3;
     const double Fa = double(P.force[3 * p + a]);
-    for (int c = 0; c < 3; ++c) qh[c] += Fa * inv_h3 * dJ[c];
+    for (int c = 0; c < 3; ++c) qh[c] += Fa * inv_h3 * dJf[a][c];
   }
+  spread_T<real>(S, 0, G, lane, rhox, eps * vol * ob);
   if (lane == 0) {
     P.geps[p] += vol * Jr * ob;
     for (int c = 0; c < 3; ++c) {
@@ -632,24 +636,27 @@ __global__ void __launch_bounds__(kAdjParticleThreads) k_adj_p_start(AdjParticle
     const double fbar = P.fbar[3 * p + c] + weight * P.dir[3 * p + c];
     qh[c] = P.qhbar[3 * p + c] - double(P.k_s[p]) * fbar;
   }
-  for (int a = 0; a < 3; ++a) {
-    const double jb = P.jvnh[3 * p + a];
-    double J, dJ[3];
-    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
-    for (int c = 0; c < 3; ++c) qh[c] += jb * dJ[c];
-    spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb);
-  }
+  // every gather (at q^{n+1/2} and at q^n) before any spread, so that the
+  // loads are not held behind the atomics; the arithmetic is the same, in
+  // the same order
   Sten<real> S0;
   stencil_at<real>(P.q_n + 3 * p, pc, S0);
+  double J1[3], dJ1[3][3], J0[3], dJ0[3][3], jb1[3], jb0[3];
+  for (int a = 0; a < 3; ++a) {
+    jb1[a] = P.jvnh[3 * p + a];
+    interp_grad<real>(S, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J1[a], dJ1[a]);
+    interp_grad<real>(S0, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J0[a], dJ0[a]);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) qh[c] += jb1[a] * dJ1[a][c];
   double qb[3];
   for (int c = 0; c < 3; ++c) qb[c] = P.qbar[3 * p + c] + qh[c];
   for (int a = 0; a < 3; ++a) {
-    const double jb = 0.5 * double(pc.dt) * qh[a];
-    double J, dJ[3];
-    interp_grad<real>(S0, 1 + a, G, lane, FaceV<real>{Un, G, pc.rho0, a}, J, dJ);
-    for (int c = 0; c < 3; ++c) qb[c] += jb * dJ[c];
-    spread_T<real>(S0, 1 + a, G, lane, vb.f[a], jb);
+    jb0[a] = 0.5 * double(pc.dt) * qh[a];
+    for (int c = 0; c < 3; ++c) qb[c] += jb0[a] * dJ0[a][c];
   }
+  for (int a = 0; a < 3; ++a) spread_T<real>(S, 1 + a, G, lane, vb.f[a], jb1[a]);
+  for (int a = 0; a < 3; ++a) spread_T<real>(S0, 1 + a, G, lane, vb.f[a], jb0[a]);
   if (lane == 0)
     for (int c = 0; c < 3; ++c) P.qbar[3 * p + c] = qb[c];
 }
