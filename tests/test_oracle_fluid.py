@@ -250,3 +250,54 @@ def test_viscous_and_mass_rates_converge_to_the_continuum_at_second_order():
     assert g64 < 1e-2 and r64 < 1e-2, (g64, r64)
     assert 3.6 < g16 / g32 < 4.4 and 3.8 < g32 / g64 < 4.2, (g16, g32, g64)
     assert 3.6 < r16 / r32 < 4.4 and 3.8 < r32 / r64 < 4.2, (r16, r32, r64)
+
+
+def _rk3_mode_error(dt, T=4.0, amp=1e-9):
+    """Relative error at time T of the oracle's step against the exact
+    solution of the semi-discrete linear dynamics in the invariant subspace of
+    one x-mode: delta rho in span{cos k x_i, sin k x_i}, g_x in span{cos k
+    x_(i+1/2), sin k x_(i+1/2)} (k = 2 pi / 16).  The 4 x 4 generator comes
+    from central differences of the rates, its exponential from scipy."""
+    from scipy.linalg import expm
+
+    n = 16
+    p = ic.GridParams(nx=n, ny=6, nz=6, h=1.0, rho0=1.0, c=4.0, eta=0.5, zeta=0.3, kT=0.0, dt=dt)
+    shape = p.shape
+    kx = 2 * np.pi / n
+    xc = np.broadcast_to(np.arange(n, dtype=float), shape)
+    xf = xc + 0.5
+    basis = [np.cos(kx * xc), np.sin(kx * xc), np.cos(kx * xf), np.sin(kx * xf)]   # drho, drho, g_x, g_x
+    zero = np.zeros(shape)
+
+    def fields(y):
+        return y[0] * basis[0] + y[1] * basis[1], [y[2] * basis[2] + y[3] * basis[3], zero, zero]
+
+    def coords(drho, gx):   # orthogonal projection onto the basis
+        return np.array([np.sum(drho * basis[0]), np.sum(drho * basis[1]), np.sum(gx * basis[2]),
+                         np.sum(gx * basis[3])]) / (0.5 * basis[0].size)
+
+    fp, eps = p.fluid(), 1e-6
+    M = np.zeros((4, 4))
+    for j in range(4):
+        e = np.zeros(4)
+        e[j] = eps
+        rp, gp = fluid.rates(*fields(e), fp)
+        rm, gm = fluid.rates(*fields(-e), fp)
+        M[:, j] = coords((rp - rm) / (2 * eps), (gp[0] - gm[0]) / (2 * eps))
+    y0 = amp * np.array([1.0, 0.3, 0.5, -0.2])
+    exact = expm(M * T) @ y0
+    drho, g = fields(y0)
+    sim = ic.Simulation(p, g=g, drho=drho)
+    for _ in range(int(round(T / dt))):
+        sim.step()
+    return np.linalg.norm(coords(sim.drho, sim.g[0]) - exact) / np.linalg.norm(exact)
+
+
+def test_ssp_rk3_is_third_order_in_time():
+    """The three stages with the weights (1, 0), (3/4, 1/4), (1/3, 2/3) of
+    App. A.2 integrate the semi-discrete equations to third order: on a
+    damped sound mode (viscous and bulk terms included) the error at a fixed
+    time falls 8x per halving of dt.  A wrong stage weight or stage input
+    lowers the order."""
+    e1, e2, e3 = (_rk3_mode_error(dt) for dt in (0.05, 0.025, 0.0125))
+    assert 7.0 < e1 / e2 < 9.0 and 7.0 < e2 / e3 < 9.0, (e1, e2, e3)
