@@ -41,3 +41,37 @@ def test_reference_arm_other_ranks_exit_quietly():
             LOCAL_RANK="1")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+class _FakeSmi:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_summary_keeps_the_timed_window_and_its_throttle_reasons():
+    """The nvidia-smi samples inside the timed window give the median SM
+    clock, the maximum and every throttle reason seen active; malformed lines
+    are skipped; with no sample inside the window all samples are used."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s = bench.ClockSampler(0)
+    s.proc = _FakeSmi()
+    s.lines = [(0.0, "1400, 2070, Not Active, Not Active, Not Active, Not Active"),   # before the window
+               (1.0, "2070, 2070, Not Active, Not Active, Not Active, Active"),
+               (1.2, "[N/A], 2070, Not Active, Not Active, Not Active, Not Active"),  # malformed
+               (1.5, "2055, 2070, Not Active, Not Active, Not Active, Not Active"),
+               (2.0, "2070, 2070, Active, Not Active, Not Active, Not Active"),
+               (3.0, "1000, 2070, Not Active, Not Active, Active, Not Active")]     # after it
+    out = s.stop(window=(0.5, 2.5))
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert out["samples"] == 3 and out["samples_in_timed_region"] == 4
+    s2 = bench.ClockSampler(0)
+    s2.proc = _FakeSmi()
+    s2.lines = [(0.0, "1980, 2070, Not Active, Not Active, Not Active, Not Active")]
+    out2 = s2.stop(window=(5.0, 6.0))
+    assert out2["sm_mhz"] == 1980.0 and out2["samples_in_timed_region"] == 0
