@@ -569,7 +569,8 @@ def main():
                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal (FP64 units)",
                     "alg_flops_per_step": ALG_FP64_FLOPS_PER_CELL_STEP * cells,
                     "hbm_frac_for_reference": achieved / peak}
-    roofline.update({"kernel": "k_rk3_stage (3 launches per step)", "stage_ms_per_step": stage_ms_per_step,
+    kname = "k_stage_rows" if tiling[0] == gp["nx"] and args.precision == "fp32" else "k_rk3_stage"
+    roofline.update({"kernel": f"{kname} (3 launches per step)", "stage_ms_per_step": stage_ms_per_step,
                      "particle_ms_per_step": part_ms / args.steps, "end_ms_per_step": end_ms / args.steps})
     if rank == 0:
         line = {

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libic.so")
-SOURCES = ["ic_capi.cu", "ic_fluid.cu", "ic_particles.cu", "ic_noalloc.cu", "ic_adjoint.cu"]
+SOURCES = ["ic_capi.cu", "ic_fluid.cu", "ic_stage_rows.cu", "ic_particles.cu", "ic_noalloc.cu", "ic_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

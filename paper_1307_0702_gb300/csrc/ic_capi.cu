@@ -477,6 +477,9 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
       cudaMemcpyAsync(ctx->d.status, zero_rebuild, sizeof(zero_rebuild), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaStreamSynchronize(ctx->stream))
     return bail(IC_ERR_CUDA);
+  // Deterministic FP32 boxes whose rows the whole-row stage kernel takes start
+  // on it; with noise the column-tile kernels are the default
+  if (p.kT == 0.0 && ic::rows_eligible(p) && ic::rows_buffers_aligned(ctx)) ctx->tile_variant = ic::kTileRows;
   // a state of rho = rho0 is delta rho = 0: the buffers are already zero
   *out = ctx;
   return IC_OK;
@@ -1378,9 +1381,12 @@ ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
 }
 
 ic_status ic_set_tile(ic_ctx *ctx, int tile_x, int zchunk) {
-  if (!ctx || (tile_x != 16 && tile_x != 32)) return IC_ERR_ARG;
+  if (!ctx || (tile_x != 0 && tile_x != 16 && tile_x != 32)) return IC_ERR_ARG;
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (!ic::set_stage_tile(ctx, tile_x == 16 ? 1 : 0, zchunk)) return fail(ctx, IC_ERR_ARG, "zchunk below 8");
+  const int variant = tile_x == 0 ? ic::kTileRows : (tile_x == 16 ? 1 : 0);
+  if (variant == ic::kTileRows && !(ic::rows_eligible(ctx->p) && ic::rows_buffers_aligned(ctx)))
+    return fail(ctx, IC_ERR_ARG, "the whole-row stage kernel needs FP32, nx a multiple of 4 and at most 128");
+  if (!ic::set_stage_tile(ctx, variant, zchunk)) return fail(ctx, IC_ERR_ARG, "zchunk below 8");
   invalidate_graphs(ctx);
   return IC_OK;
 }
@@ -1443,9 +1449,14 @@ ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
   const bool rows_ok = ic::stage_copy_active(ctx) != IC_STAGE_COPY_THREAD;
   ctx->tile_variant = v_in;
   ctx->stage_copy = copy_in;
-  for (int cand = 0; cand < 4 && err == cudaSuccess; ++cand) {
-    const int v = cand == 3 ? 1 : 0, copy = cand == 3 ? IC_STAGE_COPY_THREAD : cand;
+  // A context on the whole-row kernel is tuned among its z chunks only, one on
+  // the column-tile kernels among those: with noise the two families round the
+  // stress divergence differently, and tuning must not change a run's results.
+  const bool whole_rows = ic::rows_active(ctx);
+  for (int cand = 0; cand < 5 && err == cudaSuccess; ++cand) {
+    const int v = cand == 4 ? ic::kTileRows : (cand == 3 ? 1 : 0), copy = cand >= 3 ? IC_STAGE_COPY_THREAD : cand;
     if (copy != IC_STAGE_COPY_THREAD && !rows_ok) continue;
+    if ((v == ic::kTileRows) != whole_rows) continue;
     ctx->stage_copy = copy;
     int last = -1;
     for (int z : {32, 16, 8}) {

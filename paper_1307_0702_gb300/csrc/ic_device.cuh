@@ -44,6 +44,39 @@ struct RngKey {
   uint32_t k0, k1, box;
 };
 
+// The ten round keys of a Philox4x32-10 key (k0 + r W0, k1 + r W1), computed
+// once on the host: a kernel that draws many blocks with one key reads them
+// as constants instead of stepping the key schedule per block.
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+inline RoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0 + uint32_t(r) * kPhiloxW0;
+    rk.k[2 * r + 1] = k1 + uint32_t(r) * kPhiloxW1;
+  }
+  return rk;
+}
+
+// Philox4x32-10 with precomputed round keys (the same function as philox4x32_10)
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = uint64_t(kPhiloxM0) * c.x;
+    const uint64_t p1 = uint64_t(kPhiloxM1) * c.z;
+    c = make_uint4(uint32_t(p1 >> 32) ^ c.y ^ rk.k[2 * r], uint32_t(p1), uint32_t(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1],
+                   uint32_t(p0));
+  }
+  return c;
+}
+
+// W_A and W_B of one cell and step in FP32 (the normals of stress_normals_ab)
+// from precomputed round keys
+__device__ __forceinline__ void stress_normals_ab_rk(const RoundKeys &rk, uint32_t box, uint32_t cell, uint32_t step,
+                                                     float a[6], float b[6]);
+
 __device__ __forceinline__ uint4 philox_block(const RngKey &key, uint32_t cell, uint32_t step,
                                               uint32_t purpose, uint32_t block) {
   return philox4x32_10(make_uint4(cell, step, (purpose << 16) | block, key.box), key.k0, key.k1);
@@ -147,6 +180,19 @@ __device__ __forceinline__ void stress_normals_ab(const RngKey &key, uint32_t ce
   const uint4 h0 = philox_block(key, cell, step, kPurposeStress, 0);
   const uint4 h1 = philox_block(key, cell, step, kPurposeStress, 1);
   const uint4 h2 = philox_block(key, cell, step, kPurposeStress, 2);
+  box_muller_f32(h0.x, h0.y, a[0], a[1]);
+  box_muller_f32(h0.z, h0.w, a[2], a[3]);
+  box_muller_f32(h1.x, h1.y, a[4], a[5]);
+  box_muller_f32(h1.z, h1.w, b[0], b[1]);
+  box_muller_f32(h2.x, h2.y, b[2], b[3]);
+  box_muller_f32(h2.z, h2.w, b[4], b[5]);
+}
+
+__device__ __forceinline__ void stress_normals_ab_rk(const RoundKeys &rk, uint32_t box, uint32_t cell, uint32_t step,
+                                                     float a[6], float b[6]) {
+  const uint4 h0 = philox4x32_10_rk(make_uint4(cell, step, (kPurposeStress << 16) | 0u, box), rk);
+  const uint4 h1 = philox4x32_10_rk(make_uint4(cell, step, (kPurposeStress << 16) | 1u, box), rk);
+  const uint4 h2 = philox4x32_10_rk(make_uint4(cell, step, (kPurposeStress << 16) | 2u, box), rk);
   box_muller_f32(h0.x, h0.y, a[0], a[1]);
   box_muller_f32(h0.z, h0.w, a[2], a[3]);
   box_muller_f32(h1.x, h1.y, a[4], a[5]);

@@ -38,6 +38,7 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "ic_async.cuh"
 #include "ic_device.cuh"
 #include "ic_internal.hpp"
 
@@ -61,15 +62,6 @@ struct StageArgs {
   int ncols_x, ncols_y;            // tile columns along x and y
 };
 
-// Explicitly rounded scalar arithmetic: the flux formulas are written as the
-// same sequence of rounded operations as the FP32 pair kernel, so that a
-// plane's values do not depend on which kernel, tile or CTA computes them.
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fadd_rn(a, -b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dadd_rn(a, -b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 template <typename real>
 struct PlaneVals {
@@ -393,58 +385,6 @@ __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Bulk (TMA) copies of whole tile rows, tracked by one mbarrier per CTA.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-// global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// 16-byte asynchronous copy (L2 only), and an mbarrier arrival that fires
-// when all of this thread's earlier asynchronous copies have landed
-__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t v;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(v));
-  return v;
-}
-// Waits for the phase of the given parity to complete; gives up (false)
-// after about a second (or 2^24 tries, should the timer not advance), so that
-// a copy that never lands cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_test(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < (1u << 24); ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if (global_ns() - t0 > 1000000000ull) return false;
-  }
-  return false;
-}
 
 // staging slot of one plane pair: the thread's own values, [field][EXY]
 enum StageField {
@@ -1205,7 +1145,8 @@ size_t fluid_num_partials(const ic_ctx *ctx) {
 }
 
 bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk) {
-  if (variant < 0 || variant > 1 || (zchunk < kMinZChunk && zchunk < ctx->p.nz)) return false;
+  if (variant < 0 || variant > 2 || (zchunk < kMinZChunk && zchunk < ctx->p.nz)) return false;
+  if (variant >= kTileRows && !rows_eligible(ctx->p)) return false;
   ctx->tile_variant = variant;
   ctx->zchunk = std::min(zchunk, ctx->p.nz);
   return true;
@@ -1224,7 +1165,17 @@ int stage_copy_active(const ic_ctx *ctx) {
   return ctx->stage_copy;
 }
 
+bool rows_active(const ic_ctx *ctx) {
+  return ctx->tile_variant == kTileRows && rows_eligible(ctx->p) && rows_buffers_aligned(ctx);
+}
+
 void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk) {
+  if (rows_active(ctx)) {
+    *tx = ctx->p.nx;
+    rows_tile(ctx, ty);
+    *zchunk = ctx->zchunk > 0 ? ctx->zchunk : kMinZChunk;
+    return;
+  }
   const bool f = ctx->p.precision == IC_FP32, v1 = ctx->tile_variant == 1;
   *tx = v1 ? 16 : 32;
   *ty = f ? (v1 ? TileShape<float, 1>::TY : TileShape<float, 0>::TY)
@@ -1234,6 +1185,7 @@ void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk) {
 
 cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
                          void *const out[4]) {
+  if (rows_active(ctx)) return launch_stage_rows(ctx, stage, in_s, in_n, out);
   if (ctx->p.precision == IC_FP32) return launch_stage_r<float>(ctx, stage, in_s, in_n, out);
   return launch_stage_r<double>(ctx, stage, in_s, in_n, out);
 }
@@ -1326,7 +1278,9 @@ cudaError_t launch_field_sums(ic_ctx *ctx, void *const U[4], double *dev_out4) {
 }
 
 cudaError_t launch_end_of_step(ic_ctx *ctx) {
-  const int nb = ctx->p.precision == IC_FP32 ? stage_layout<float>(ctx).ctas : stage_layout<double>(ctx).ctas;
+  const int nb = rows_active(ctx)                ? rows_ctas(ctx, 2)
+                 : ctx->p.precision == IC_FP32 ? stage_layout<float>(ctx).ctas
+                                               : stage_layout<double>(ctx).ctas;
   const int has_mode = 1;
   const ic_grid_params &p = ctx->p;
   const double amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;

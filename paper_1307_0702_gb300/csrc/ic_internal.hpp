@@ -217,7 +217,7 @@ struct ic_ctx {
   int fetch_n[2] = {-1, -1};            // particles of the queued copy, -1: none
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per buffer parity
   uint64_t generation = 0;                          // bumped whenever the captured step changes
-  int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY)
+  int tile_variant = 0;    // stage-kernel tile: 0 = wide (32 x TY), 1 = narrow (16 x TY), 2 = whole rows
   int zchunk = 0;          // fewest z planes a stage-kernel CTA marches (0 = default)
   int stage_copy = ic::kDefaultStageCopy;   // FP32 wide-tile loads (IC_STAGE_COPY_*), where the grid allows
   int sm_count = 1;        // SMs of the context's device
@@ -284,6 +284,16 @@ constexpr int kMinZChunk = 8;
 bool set_stage_tile(ic_ctx *ctx, int variant, int zchunk);
 int stage_copy_active(const ic_ctx *ctx);   // the staging mode the next FP32 wide-tile launch uses
 void stage_tile(const ic_ctx *ctx, int *tx, int *ty, int *zchunk);
+bool rows_active(const ic_ctx *ctx);        // the next stage launch is the whole-row kernel
+
+// whole-row FP32 stage kernel (ic_stage_rows.cu): tile variant 2
+constexpr int kTileRows = 2;
+bool rows_eligible(const ic_grid_params &p);
+bool rows_buffers_aligned(const ic_ctx *ctx);
+int rows_ctas(const ic_ctx *ctx, int stage);
+void rows_tile(const ic_ctx *ctx, int *ty);
+cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
+                              void *const out[4]);
 
 // particles (ic_particles.cu)
 enum ParticlePhase { kHalfStep = 0, kPressure = 1, kForce = 2, kImpulse = 3, kSpread = 4, kFinal = 5 };

@@ -72,9 +72,15 @@ struct Pos<float> {
   }
   __device__ static T advance(T q, float dq, const PConsts<float> &pc, int a) {
     const long long span = a == 0 ? pc.span[0] : (a == 1 ? pc.span[1] : pc.span[2]);
-    T r = q + __float2ll_rn(dq * pc.inv_h * 0x1p40f);
-    if (r < 0) r += span;
-    if (r >= span) r -= span;
+    // a non-finite displacement (a state that blew up, which the end-of-step
+    // check reports) leaves the particle in place; any finite one wraps into
+    // [0, span), so that no index derived from q leaves the grid
+    const float d = dq * pc.inv_h * 0x1p40f;
+    T r = q + (isfinite(d) ? __float2ll_rn(d) : 0ll);
+    if (r < 0 || r >= span) {
+      r %= span;
+      if (r < 0) r += span;
+    }
     return r;
   }
   __device__ static float diff(T x, T y, const PConsts<float> &pc, int a) {   // minimum image x - y (length)

@@ -270,7 +270,8 @@ class Grid:
         self._check(self._lib.ic_snapshot_load(self._ctx, ctypes.c_void_p(buf.data_ptr())))
 
     def set_tile(self, tile_x, zchunk):
-        """Stage-kernel tiling (tile_x 32 or 16, zchunk >= 8 planes); results are unchanged."""
+        """Stage-kernel tiling: tile_x 32 or 16 (column tiles) or 0 (bands of whole x
+        rows, FP32 with nx a multiple of 4 up to 128), zchunk >= 8 planes."""
         self._check(self._lib.ic_set_tile(self._ctx, int(tile_x), int(zchunk)))
 
     def tile(self):

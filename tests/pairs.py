@@ -23,6 +23,7 @@ def run_gpu(gp, rho, g, parts=None, nsteps=1, weights=None, thermal_seed=None, c
         if stage_copy is not None:
             grid.set_stage_copy(stage_copy)
         out["stage_copy"] = grid.stage_copy()
+        out["tile"] = grid.tile()
         grid.set_state(rho, g)
         if thermal_seed is not None:
             grid.init_thermal(thermal_seed, add=True)

@@ -93,7 +93,7 @@ def test_fp32_wide_tile_staging_modes():
     sim = run_oracle(gp, rho, g, parts, nsteps=4, weights=w, thermal_seed=3)
     runs = []
     for mode in ("thread", "bulk", "rows16"):
-        out = run_gpu(gp, rho, g, parts, nsteps=4, weights=w, thermal_seed=3, stage_copy=mode)
+        out = run_gpu(gp, rho, g, parts, nsteps=4, weights=w, thermal_seed=3, tile=(32, 16), stage_copy=mode)
         assert out["stage_copy"] == mode
         check(compare(out, sim, gp, q0=parts["q"]), TOL["fp32"])
         runs.append(out)
