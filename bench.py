@@ -143,46 +143,129 @@ def oracle_sample():
     return sim
 
 
-def cpu_baseline(seconds_budget=20.0):
-    """The oracle as it stands on the host cores, timed on the 64^3 sample
-    (cell-updates/s is intensive in the box size)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _slab_worker(rank, world, port, warmup, steps, queue):
+    """One process of the all-core oracle: its z-slab of the 128^3 workload."""
+    import torch.distributed as dist
+
+    from oracle import ic as oic
+    from oracle import slabs
+    from paper_1307_0702_gb300 import workloads as W
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    gp, parts = W.large_box_config()
+    p = oic.GridParams(**{k: v for k, v in gp.items() if k in oic.GridParams.__dataclass_fields__})
+    rho, g = W.standing_wave_fields(gp)
+    th_drho, th_g = oic.thermal_fluctuation(p, 1000)
+    sl = slabs.SlabSimulation(p, slabs.GlooComm(), rho - p.rho0 + th_drho, [g[a] + th_g[a] for a in range(3)])
+    # particles start at rest (the no-slip start J v would need a serial pass)
+    sl.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], np.zeros_like(parts["q"]))
+    sl.run(warmup)
+    dist.barrier()
+    t0 = time.perf_counter()
+    sl.run(steps)
+    dist.barrier()
+    el = time.perf_counter() - t0
+    if rank == 0:
+        queue.put(el)
+    dist.destroy_process_group()
+
+
+def oracle_all_cores(warmup, steps):
+    """The oracle as it stands on every host core: the full 128^3 workload (10^4
+    particles) split into z-slabs, one single-threaded process per core (the
+    oracle's slab form, oracle/slabs.py, halo exchange over gloo).  Processes
+    are spawned, not forked (this process may hold a CUDA context).
+    Returns (seconds for the timed steps, processes)."""
+    import socket
+
+    import torch.multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    world = max(1, min(cores, 128 // 4))          # each slab keeps >= 4 planes beside its ghosts
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        queue = ctx.Queue()
+        procs = [ctx.Process(target=_slab_worker, args=(r, world, port, warmup, steps, queue)) for r in range(world)]
+        for pr in procs:
+            pr.start()
+        el = queue.get(timeout=900)
+        for pr in procs:
+            pr.join(timeout=120)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return el, world
+
+
+def cpu_baseline(steps=10, single_budget=10.0):
+    """The oracle as it stands: the full 128^3 workload on every host core
+    (reported), and one thread on a 64^3 sub-box (beside it)."""
+    el, world = oracle_all_cores(warmup=1, steps=steps)
     sim = oracle_sample()
     sim.step()   # warm-up (page-in, caches)
     t0 = time.perf_counter()
-    steps = 0
+    n1 = 0
     while True:
         sim.step()
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > seconds_budget or steps >= 50:
+        n1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 > single_budget or n1 >= 50:
             break
-    cells = 64 ** 3
-    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"64^3 sub-box, 1250 particles, kT=1e-3, {steps} oracle steps in {el:.1f} s (numpy FP64, 1 thread)",
-            "particle_steps_per_s": 1250 * steps / el}
+    cells = 128 ** 3
+    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": world, "kind": "oracle",
+            "sample": (f"the full 128^3 workload (1e4 particles, kT=1e-3), the oracle split into {world} z-slabs, one "
+                       f"single-threaded numpy FP64 process per core (gloo halo exchange), {steps} steps in {el:.1f} s"),
+            "cpu_model": cpu_model(), "particle_steps_per_s": 10000 * steps / el,
+            "single_thread": {"value": 64 ** 3 * n1 / el1, "unit": "cell-updates/s", "cores": 1,
+                              "sample": f"64^3 sub-box, 1250 particles, {n1} oracle steps in {el1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: each step is one oracle step of the
-    64^3 sample of the workload, on the host (rank 0 only)."""
+    """The oracle as the reference arm: the full 128^3 workload on every host
+    core (rank 0 only; other ranks exit without work)."""
     if rank != 0:
         return
-    sim = oracle_sample()
-    for _ in range(args.warmup):
-        sim.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sim.step()
-    el = time.perf_counter() - t0
-    v = 64 ** 3 * args.steps / el
+    el, procs = oracle_all_cores(warmup=args.warmup, steps=args.steps)
+    v = 128 ** 3 * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "64^3 sub-box with 1250 particles per step (same density)"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v,
-                             "sample": "each step: one oracle step of a 64^3 sub-box, 1250 particles"},
+            "config": {"workload": WORKLOAD, "same_config": True,
+                       "sample": f"the full workload, oracle split into {procs} z-slabs, one process per core"},
+            "particle_steps_per_s": 10000 * args.steps / el,
+            "cpu_baseline": {"kind": "oracle", "cores": procs, "value": v, "cpu_model": cpu_model(),
+                             "sample": f"each step: one oracle step of the full 128^3 workload on {procs} cores"},
             "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
 
 
 ADJOINT_METRIC = ("rollout-gradient steps/s (64^3, 16 tethered particles, 1000 steps, checkpoint every 50; "

@@ -165,6 +165,15 @@ ic_status ic_time_average(ic_ctx *ctx, double *f_spring, double *lambda, double 
 /* Total momentum h^3 sum g + sum m_e u (3 doubles, Eq. (eq:totmom)), current
  * driven-mode amplitude A, and the step counter (each may be NULL). */
 ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step);
+/* The objective whose gradients the adjoint computes (Sec. 6 reads the
+ * acoustic force as the time-averaged tether force):
+ *   *phi = sum_p d_p . <F_p>_w,  <F_p>_w = sum_n w_n F_p^{n+1/2} / sum_n w_n
+ * from the context's weighted sums (those of ic_time_average), summed over
+ * the particles in index order.  direction: n x 3 doubles (host), or NULL for
+ * the x axis of every particle.  reset != 0 zeroes the sums after reading.
+ * Synchronises the stream; IC_ERR_ARG for a NULL phi, IC_ERR_STATE if the
+ * weights sum to zero. */
+ic_status ic_objective(ic_ctx *ctx, const double *direction, double *phi, int reset);
 
 /* Synchronises the stream and reports device-side errors raised since the
  * last check (IC_ERR_NONFINITE, IC_ERR_CAPACITY). */
@@ -344,6 +353,13 @@ ic_status ic_adjoint_step(ic_ctx *ctx, double weight);
  * (n x 3).  Synchronises the stream. */
 ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, double *grad_A, double *rho_bar,
                           double *gx_bar, double *gy_bar, double *gz_bar, double *q_bar, double *u_bar);
+
+/* dPhi / d(kappa_p / kappa_f) of every particle (n doubles, host): the
+ * epsilon gradient of ic_adjoint_read taken through epsilon_pf =
+ * c_f^2 (kappa_f / kappa_p - 1) (Eqs. (part_svel), (ke)), with kappa_p / kappa_f
+ * recovered from the context's epsilon.  Synchronises the stream; IC_ERR_ARG
+ * for a NULL pointer, IC_ERR_STATE as ic_adjoint_read. */
+ic_status ic_adjoint_read_kappa(ic_ctx *ctx, double *grad_kappa_ratio);
 
 /* Step tapes: ic_step_record_tape runs ic_step_record and copies everything
  * the reverse sweep of that step reads (U^n, the first two RK stages, the

@@ -46,6 +46,8 @@ SIGNATURES = {
     "ic_particle_density": (c_int, [c_void_p, PD]),
     "ic_time_average": (c_int, [c_void_p, PD, PD, PD, c_int]),
     "ic_stats": (c_int, [c_void_p, PD, PD, POINTER(c_int64)]),
+    "ic_objective": (c_int, [c_void_p, PD, PD, c_int]),
+    "ic_adjoint_read_kappa": (c_int, [c_void_p, PD]),
     "ic_sync": (c_int, [c_void_p]),
     "ic_checkpoint": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
     "ic_restore": (c_int, [c_void_p, c_void_p, c_size_t]),

@@ -65,9 +65,7 @@ class Rollout:
             self.checkpoints.append(buf)
             stop = min(start + self.K, n)
             g.step(stop - start, weights=self.weights[start:stop])
-        f_avg, _, _ = g.time_average(reset=True)
-        d = self.direction if self.direction is not None else np.tile([1.0, 0.0, 0.0], (f_avg.shape[0], 1))
-        return float(np.sum(d * f_avg))
+        return g.objective(self.direction, reset=True)
 
     def backward(self):
         """Gradients of the last forward's Phi: dict m_e, kappa_ratio, eps (n,),
@@ -107,8 +105,7 @@ class Rollout:
     def _read(self):
         g = self.grid
         out = g.adjoint_read()
-        c2 = float(g.params["c"]) ** 2
-        out["kappa_ratio"] = out["eps"] * (-c2 / self.kappa ** 2)
+        out["kappa_ratio"] = g.adjoint_read_kappa()
         return out
 
 

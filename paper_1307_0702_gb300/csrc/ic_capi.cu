@@ -723,6 +723,20 @@ ic_status ic_time_average(ic_ctx *ctx, double *f_spring, double *lambda, double 
   return IC_OK;
 }
 
+ic_status ic_objective(ic_ctx *ctx, const double *direction, double *phi, int reset) {
+  if (!ctx || !phi) return IC_ERR_ARG;
+  const size_t n = size_t(ctx->ps.n);
+  std::vector<double> f(3 * n);
+  const ic_status st = ic_time_average(ctx, n ? f.data() : nullptr, nullptr, nullptr, reset);
+  if (st) return st;
+  // Phi = sum_p d_p . <F_p>_w, particles in index order, components x, y, z
+  double s = 0.0;
+  for (size_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) s += (direction ? direction[3 * i + a] : (a == 0 ? 1.0 : 0.0)) * f[3 * i + a];
+  *phi = s;
+  return IC_OK;
+}
+
 ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step) {
   if (!ctx) return IC_ERR_ARG;
   double *sums = ctx->d.scalars + 8;
@@ -1194,6 +1208,27 @@ ic_status ic_adjoint_read(ic_ctx *ctx, double *grad_m_e, double *grad_eps, doubl
   if (grad_A) IC_CUDA(ctx, cudaMemcpy(grad_A, A.gA, sizeof(double), cudaMemcpyDeviceToHost));
   if (q_bar && n) IC_CUDA(ctx, cudaMemcpy(q_bar, A.qbar, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
   if (u_bar && n) IC_CUDA(ctx, cudaMemcpy(u_bar, A.ubar, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  return check_device_status(ctx);
+}
+
+ic_status ic_adjoint_read_kappa(ic_ctx *ctx, double *grad_kappa_ratio) {
+  if (!ctx || !grad_kappa_ratio) return IC_ERR_ARG;
+  ic_status st = adjoint_ready(ctx);
+  if (st) return st;
+  const size_t n = size_t(ctx->adj.np);
+  if (!n) return IC_OK;
+  std::vector<double> geps(n), eps(n);
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  IC_CUDA(ctx, cudaMemcpy(geps.data(), ctx->adj.geps, n * sizeof(double), cudaMemcpyDeviceToHost));
+  st = download_real(ctx, eps.data(), ctx->ps.eps, 0.0, n);
+  if (st) return st;
+  // epsilon = c^2 (kappa_f / kappa_p - 1) (Eqs. (part_svel), (ke)), so with
+  // r = kappa_p / kappa_f = c^2 / (epsilon + c^2): d epsilon / d r = -c^2 / r^2
+  const double c2 = ctx->p.c * ctx->p.c;
+  for (size_t i = 0; i < n; ++i) {
+    const double r = c2 / (eps[i] + c2);
+    grad_kappa_ratio[i] = geps[i] * (-c2 / (r * r));
+  }
   return check_device_status(ctx);
 }
 

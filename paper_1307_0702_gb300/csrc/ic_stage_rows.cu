@@ -53,7 +53,9 @@ constexpr double kStageAR[3] = {0.0, 0.75, 1.0 / 3.0};
 constexpr double kStageBR[3] = {1.0, 0.25, 2.0 / 3.0};
 
 __host__ __device__ constexpr int rows_nsg(int stage) { return stage == 0 ? 3 : 4; }   // momentum ring
-__host__ __device__ constexpr int rows_nfn(int stage, bool noise) { return stage == 0 ? 0 : (noise ? 7 : 4); }
+// fields of the U^n ring: U^n (stages 2-3) and the stage's stored noise divergence
+__host__ __device__ constexpr int rows_nun(int stage) { return stage == 0 ? 0 : 4; }
+__host__ __device__ constexpr int rows_nfn(int stage, bool noise) { return rows_nun(stage) + (noise ? 3 : 0); }
 
 // Shared-memory regions of one CTA, in floats (all multiples of 4).
 struct RowLayout {
@@ -68,9 +70,8 @@ __host__ __device__ inline RowLayout row_layout(int nx, int vc, int R, int RD, i
   L.v = L.g + rows_nsg(stage) * 4 * plane;                // [2][3][R][nx] vx, vy, vz by plane parity
   L.t = L.v + 6 * plane;                                  // [3][R][nx] T_yy, T_xy, T_zy
   L.tb = L.t + 3 * plane;                                 // [3][R][nx/vc] edge-cell T_xx, T_yx, T_zx
-  L.s = L.tb + ((3 * R * (nx / vc) + 3) & ~3);            // stage 1: [10][R][nx] in-plane stresses
-  L.n = L.s + ((noise && stage == 0) ? 16 * plane : 0);   // (+ [6][R][nx] own xz, yz of the plane below, zz)
-                                                          // stages 2-3: [NSN][nfn][ty][nx]
+  L.s = L.tb + ((3 * R * (nx / vc) + 3) & ~3);
+  L.n = L.s;                                              // [NSN][nfn][ty][nx] U^n (stages 2-3), D_s
   L.total = L.n + kRowsNSN * rows_nfn(stage, noise) * ty * nx;
   return L;
 }
@@ -80,8 +81,7 @@ struct RowArgs {
   const float *__restrict__ n[4];     // U^n
   float *__restrict__ o[4];           // U_{s+1}
   const float *__restrict__ pp;       // particle pressure S Omega_s at centres, or null
-  const float *__restrict__ d_in[3];  // stages 2-3: stored D_s (x, y, z faces)
-  float *__restrict__ d_out[6];       // stage 1: D_2 and D_3
+  const float *__restrict__ d_in[3];  // kT > 0: the stage's stress divergence D_s (x, y, z faces)
   FluidConsts<float> c;
   const int64_t *step;
   double *partials;                   // stage 3: per-CTA sum of delta rho cos(k x)
@@ -91,7 +91,6 @@ struct RowArgs {
   int wrapy;   // 1: one tile holds every row (y periodic inside the CTA, no ring rows)
   int ncols;   // tiles along y
   int stall;   // 1 only to test the bounded waits: every mbarrier expects an arrival nothing makes
-  RoundKeys rk;   // Philox round keys of the noise key
 };
 
 // the VC x-adjacent cells of one thread: one 8- or 16-byte vector per field
@@ -155,8 +154,7 @@ __device__ __forceinline__ bool cbar_or(int T, bool pred) {
 template <int VC, int STAGE, bool NOISE, bool PROD>
 __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(const RowArgs a) {
   constexpr int NSD = kRowsNSD, NSG = rows_nsg(STAGE), NSN = kRowsNSN;
-  constexpr bool GEN = NOISE && STAGE == 0;
-  constexpr int NFN = rows_nfn(STAGE, NOISE);
+  constexpr int NUN = rows_nun(STAGE), NFN = rows_nfn(STAGE, NOISE);
   extern __shared__ __align__(16) float sm[];
   __shared__ __align__(8) unsigned long long bars[kRowsMaxBars + 1];   // + the copy warp's go signal
   __shared__ float s_acc[rows_max_threads<VC>()];
@@ -178,19 +176,14 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
   const int rp = wrapy ? (r == R - 1 ? 0 : r + 1) : min(r + 1, R - 1);
   const int rpd = wrapy ? rp : r + 1;        // density row one y up
   const int ur = wrapy ? r : r - 1;          // row of the U^n ring
-  float *sd = sm + L.d, *sg = sm + L.g, *sv = sm + L.v, *st = sm + L.t, *stb = sm + L.tb, *ss = sm + L.s,
-        *sn = sm + L.n;
+  float *sd = sm + L.d, *sg = sm + L.g, *sv = sm + L.v, *st = sm + L.t, *stb = sm + L.tb, *sn = sm + L.n;
   const int RQ = R * QX;
   const auto zw = [NZ](int p) { return p < 0 ? p + NZ : (p >= NZ ? p - NZ : p); };
 
-  const int64_t step = *a.step;
-  const uint32_t ustep = uint32_t(step);
   const float drive4 = 4.0f * c.drive[STAGE];
   const float rho0 = c.rho0, c2x4 = c.c2x4, visc_d = c.visc_d, visc_o = c.visc_o, lam2x4_h = c.lam2x4_h;
   const float out_flux = c.out_flux, out_mass = c.out_mass;
-  const float nd = c.noise_d4, nt = c.noise_t4, ne = c.noise_e4;
   const float ca = float(kStageAR[STAGE]), cb = float(kStageBR[STAGE]);
-  const RngKey key{c.k0, c.k1, c.box};
   float cosx[VC];
 #pragma unroll
   for (int e = 0; e < VC; ++e) cosx[e] = (c.wave_axis == 0 && c.cos_table) ? c.cos_table[xq + e] : 0.0f;
@@ -261,8 +254,8 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
         if (cnt <= 0) continue;
         const float *src = which == 0   ? a.s[0]
                            : which == 1 ? (f == 0 ? a.s[1] : f == 1 ? a.s[2] : f == 2 ? a.s[3] : a.pp)
-                                        : (f < 4 ? (f == 0 ? a.n[0] : f == 1 ? a.n[1] : f == 2 ? a.n[2] : a.n[3])
-                                                 : (f == 4 ? a.d_in[0] : f == 5 ? a.d_in[1] : a.d_in[2]));
+                                        : (f < NUN ? (f == 0 ? a.n[0] : f == 1 ? a.n[1] : f == 2 ? a.n[2] : a.n[3])
+                                                   : (f == NUN ? a.d_in[0] : f == NUN + 1 ? a.d_in[1] : a.d_in[2]));
         bulk_g2s(smem_u32(dst + f * fstride + rr * NX), src + (size_t(z) * NY + yy) * NX, uint32_t(cnt * NX * 4), bar);
       }
     };
@@ -285,7 +278,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
         if (issuer) issue_d(next_d);
       for (; next_g <= gmax; ++next_g)
         if (issuer) issue_g(next_g);
-      if (STAGE != 0)
+      if (NFN > 0)
         for (; next_n <= nmax; ++next_n)
           if (issuer) issue_n(next_n);
     };
@@ -327,7 +320,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
         if (a.status) atomicOr(a.status, kStatusStaging);
         for (; wd < next_d; ++wd) wait_bar((wd - pbase) % NSD);
         for (; wg < next_g; ++wg) wait_bar(NSD + (wg - pbase) % NSG);
-        if (STAGE != 0)
+        if (NFN > 0)
           for (; wn < next_n; ++wn) wait_bar(NSD + NSG + (wn - z0) % NSN);
       }
     };
@@ -363,29 +356,6 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
       stc<VC>(V + 2 * plane, Q.vz);
     };
 
-    // stage 1: this thread's stresses of the plane below the run (for the z
-    // differences of the first plane), kept in its own shared-memory words
-    // [xz_A, yz_A, xz_B, yz_B, zz_A, zz_B] of the plane below
-    float *own_s = ss + 10 * plane + r * NX + xq;
-    if (GEN) {
-      float v[4][VC];
-#pragma unroll
-      for (int e = 0; e < VC; ++e) {
-        const uint32_t cell = uint32_t(xq + e) + uint32_t(NX) * (uint32_t(y) + uint32_t(NY) * uint32_t(zw(pbase)));
-        const uint4 h1 = philox4x32_10_rk(make_uint4(cell, ustep, (kPurposeStress << 16) | 1u, key.box), a.rk);
-        const uint4 h2 = philox4x32_10_rk(make_uint4(cell, ustep, (kPurposeStress << 16) | 2u, key.box), a.rk);
-        float w4, w5, u4, u5;
-        box_muller_f32(h1.x, h1.y, w4, w5);   // W_A: xz, yz
-        box_muller_f32(h2.z, h2.w, u4, u5);   // W_B: xz, yz
-        v[0][e] = mul_rn(ne, w4);
-        v[1][e] = mul_rn(ne, w5);
-        v[2][e] = mul_rn(ne, u4);
-        v[3][e] = mul_rn(ne, u5);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) stc<VC>(own_s + j * plane, v[j]);
-    }
-
     PlaneQ<VC> P;
     finish(pbase, P);
     float gz_m[VC], txz_m[VC], tyz_m[VC], tzz_k[VC], bulk_k[VC];
@@ -412,52 +382,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
       const float *VXk = sv + (k & 1) * 3 * plane, *VYk = VXk + plane, *VZk = VXk + 2 * plane;
       const float *VXq = sv + ((k + 1) & 1) * 3 * plane, *VYq = VXq + plane;
       const int row = r * NX;
-      // stage 1: the in-plane parts of the stress divergence of both streams;
-      // D_2 and D_3 of the x and y faces are stored here, D_1 kept for phase C
-      // (before the fluxes, so that its temporaries are dead while they are live)
-      float D1x[VC], D1y[VC], DzA[VC], DzB[VC];
       const size_t gi = (size_t(zw(k)) * NY + y) * NX + xq;
-      if (GEN && body) {
-        float DxA[VC], DyA[VC], DxB[VC], DyB[VC];
-#pragma unroll
-        for (int sI = 0; sI < 2; ++sI) {
-          const float *S = ss + sI * 5 * plane;   // xx, yy, xy, xz, yz
-          const Cells<VC> xx = ldc<VC>(S + row + xq), yy = ldc<VC>(S + plane + row + xq), yy_p = ldc<VC>(S + plane + rp * NX + xq);
-          const Cells<VC> xy = ldc<VC>(S + 2 * plane + row + xq), xy_m = ldc<VC>(S + 2 * plane + rm * NX + xq);
-          const Cells<VC> xz = ldc<VC>(S + 3 * plane + row + xq), yz = ldc<VC>(S + 4 * plane + row + xq);
-          const Cells<VC> yz_m = ldc<VC>(S + 4 * plane + rm * NX + xq);
-          const float xx_r = S[row + ep], xy_l = S[2 * plane + row + em], xz_l = S[3 * plane + row + em];
-          float *xz_own = own_s + (2 * sI) * plane, *yz_own = own_s + (2 * sI + 1) * plane;
-          const Cells<VC> xz_prev = ldc<VC>(xz_own), yz_prev = ldc<VC>(yz_own);
-          float *Dx = sI == 0 ? DxA : DxB, *Dy = sI == 0 ? DyA : DyB, *Dz = sI == 0 ? DzA : DzB;
-#pragma unroll
-          for (int e = 0; e < VC; ++e) {
-            const float xxp = e < VC - 1 ? xx.v[e + 1] : xx_r;
-            const float xyl = e > 0 ? xy.v[e - 1] : xy_l;
-            const float xzl = e > 0 ? xz.v[e - 1] : xz_l;
-            Dx[e] = add_rn(add_rn(sub_rn(xxp, xx.v[e]), sub_rn(xy.v[e], xy_m.v[e])), sub_rn(xz.v[e], xz_prev.v[e]));
-            Dy[e] = add_rn(add_rn(sub_rn(yy_p.v[e], yy.v[e]), sub_rn(xy.v[e], xyl)), sub_rn(yz.v[e], yz_prev.v[e]));
-            Dz[e] = add_rn(sub_rn(xz.v[e], xzl), sub_rn(yz.v[e], yz_m.v[e]));   // in-plane part
-          }
-          stc<VC>(xz_own, xz.v);
-          stc<VC>(yz_own, yz.v);
-        }
-        float d2x[VC], d2y[VC];
-#pragma unroll
-        for (int e = 0; e < VC; ++e) {
-          // D_1 = D(W_A) - sqrt3 D(W_B) now; D_2 = D(W_A) + sqrt3 D(W_B) and D_3 = D(W_A) kept
-          D1x[e] = fma_rn(-1.7320508075688772f, DxB[e], DxA[e]);
-          D1y[e] = fma_rn(-1.7320508075688772f, DyB[e], DyA[e]);
-          d2x[e] = fma_rn(1.7320508075688772f, DxB[e], DxA[e]);
-          d2y[e] = fma_rn(1.7320508075688772f, DyB[e], DyA[e]);
-        }
-        if (own) {
-          stc<VC>(a.d_out[0] + gi, d2x);
-          stc<VC>(a.d_out[1] + gi, d2y);
-          stc<VC>(a.d_out[3] + gi, DxA);
-          stc<VC>(a.d_out[4] + gi, DyA);
-        }
-      }
       const Cells<VC> qvy_ym = ldc<VC>(VYq + rm * NX + xq);
       const float qvx_l = VXq[row + em];
       float bulk_up[VC], tzz_up[VC], txz[VC], tyz[VC];
@@ -512,9 +437,8 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
       cbar<PROD>(T);
 
       // ---- phase C: divergence, noise, RK combination, stores
-      if (STAGE != 0 && body)   // every thread waits on every fill: the parities stay in step
+      if (NFN > 0 && body)   // every thread waits on every fill: the parities stay in step
         for (; wn <= k; ++wn) wait_bar(NSD + NSG + (wn - z0) % NSN);
-      float sgz[VC];   // stage 1: the deterministic z-momentum divergence, finished below
       if (body && own) {
         const Cells<VC> gy_ym = ldc<VC>(GYk + rm * NX + xq);
         const float gx_l = GXk[row + em];
@@ -523,13 +447,13 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
         const float Txx_r = stb[r * QX + qp], Tyx_l = stb[RQ + r * QX + qm], Tzx_l = stb[2 * RQ + r * QX + qm];
         float o[4][VC];
         Cells<VC> un[4], dn[3];
-        if (STAGE != 0) {
+        if (NFN > 0) {
           const float *U = sn + ((k - z0) % NSN) * NFN * TY * NX + ur * NX + xq;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) un[j] = ldc<VC>(U + j * TY * NX);
+          for (int j = 0; j < NUN; ++j) un[j] = ldc<VC>(U + j * TY * NX);
           if (NOISE) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) dn[j] = ldc<VC>(U + (4 + j) * TY * NX);
+            for (int j = 0; j < 3; ++j) dn[j] = ldc<VC>(U + (NUN + j) * TY * NX);
           }
         }
 #pragma unroll
@@ -546,11 +470,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
           float s_gy = add_rn(add_rn(sub_rn(Tyy_p.v[e], tyy[e]), sub_rn(tyx[e], Tyx_xm)), sub_rn(tyz[e], tyz_m[e]));
           float s_gz =
               add_rn(add_rn(sub_rn(tzz_up[e], tzz_k[e]), sub_rn(tzx[e], Tzx_xm)), sub_rn(tzy[e], Tzy_m.v[e]));
-          if (GEN) {
-            s_gx = sub_rn(s_gx, D1x[e]);
-            s_gy = sub_rn(s_gy, D1y[e]);
-            sgz[e] = s_gz;
-          } else if (NOISE) {
+          if (NOISE) {
             s_gx = sub_rn(s_gx, dn[0].v[e]);
             s_gy = sub_rn(s_gy, dn[1].v[e]);
             s_gz = sub_rn(s_gz, dn[2].v[e]);
@@ -569,68 +489,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
           }
         }
 #pragma unroll
-        for (int j = 0; j < (GEN ? 3 : 4); ++j) stc<VC>(a.o[j] + gi, o[j]);
-      }
-      if (GEN) {
-        // the stresses of plane k + 1 of both streams, two cells at a time:
-        // their in-plane components for the next plane's differences (every
-        // row: the ring rows supply neighbours), Sigma_zz for this plane's z
-        // difference, which completes the z-momentum of plane k
-        const Cells<VC> zz_a = ldc<VC>(own_s + 4 * plane), zz_b = ldc<VC>(own_s + 5 * plane);
-        float zn[2][VC];
-#pragma unroll
-        for (int h = 0; h < VC / 2; ++h) {
-          float2 sxx[2], syy[2], sxy[2], sxz[2], syz[2];
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const int e = 2 * h + j;
-            const uint32_t cell =
-                uint32_t(xq + e) + uint32_t(NX) * (uint32_t(y) + uint32_t(NY) * uint32_t(zw(k + 1)));
-            float w[2][6];
-            stress_normals_ab_rk(a.rk, key.box, cell, ustep, w[0], w[1]);
-#pragma unroll
-            for (int sI = 0; sI < 2; ++sI) {
-              const float ntr = mul_rn(nt, add_rn(add_rn(w[sI][0], w[sI][1]), w[sI][2]));
-              const float vxx = fma_rn(nd, w[sI][0], ntr), vyy = fma_rn(nd, w[sI][1], ntr);
-              const float vzz = fma_rn(nd, w[sI][2], ntr);
-              const float vxy = mul_rn(ne, w[sI][3]), vxz = mul_rn(ne, w[sI][4]), vyz = mul_rn(ne, w[sI][5]);
-              (j == 0 ? sxx[sI].x : sxx[sI].y) = vxx;
-              (j == 0 ? syy[sI].x : syy[sI].y) = vyy;
-              (j == 0 ? sxy[sI].x : sxy[sI].y) = vxy;
-              (j == 0 ? sxz[sI].x : sxz[sI].y) = vxz;
-              (j == 0 ? syz[sI].x : syz[sI].y) = vyz;
-              if (body) {
-                float &Dz = sI == 0 ? DzA[e] : DzB[e];
-                Dz = add_rn(sub_rn(vzz, sI == 0 ? zz_a.v[e] : zz_b.v[e]), Dz);
-              }
-              zn[sI][e] = vzz;
-            }
-          }
-#pragma unroll
-          for (int sI = 0; sI < 2; ++sI) {
-            float2 *S = reinterpret_cast<float2 *>(ss + sI * 5 * plane + r * NX + xq + 2 * h);
-            const int pf = plane / 2;
-            S[0] = sxx[sI];
-            S[pf] = syy[sI];
-            S[2 * pf] = sxy[sI];
-            S[3 * pf] = sxz[sI];
-            S[4 * pf] = syz[sI];
-          }
-        }
-        stc<VC>(own_s + 4 * plane, zn[0]);
-        stc<VC>(own_s + 5 * plane, zn[1]);
-        if (body && own) {
-          float o3[VC], d2z[VC];
-#pragma unroll
-          for (int e = 0; e < VC; ++e) {
-            // D_1 = D(W_A) - sqrt3 D(W_B); D_2 = D(W_A) + sqrt3 D(W_B) and D_3 = D(W_A) kept
-            o3[e] = fma_rn(sub_rn(sgz[e], fma_rn(-1.7320508075688772f, DzB[e], DzA[e])), out_flux, P.gz[e]);
-            d2z[e] = fma_rn(1.7320508075688772f, DzB[e], DzA[e]);
-          }
-          stc<VC>(a.o[3] + gi, o3);
-          stc<VC>(a.d_out[2] + gi, d2z);
-          stc<VC>(a.d_out[5] + gi, DzA);
-        }
+        for (int j = 0; j < 4; ++j) stc<VC>(a.o[j] + gi, o[j]);
       }
 #pragma unroll
       for (int e = 0; e < VC; ++e) {
@@ -671,6 +530,168 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
     }
   }
 }
+
+// ------------------------------------------------------------ noise kernel
+// The stochastic stress of one step enters the three stages only through its
+// divergence at the faces, and that is linear in the normals:
+//   D_s = D(W_A) + beta_s D(W_B),  beta = (-sqrt3, +sqrt3, 0)  (App. A.2),
+// with D(W) = div Sigma(W) (times 4, like the stage kernels' fluxes):
+//   D^x = Sigma_xx(i+x) - Sigma_xx + Sigma_xy - Sigma_xy(i-y) + Sigma_xz - Sigma_xz(i-z)
+//   D^y = Sigma_yy(i+y) - Sigma_yy + Sigma_xy - Sigma_xy(i-x) + Sigma_yz - Sigma_yz(i-z)
+//   D^z = Sigma_zz(i+z) - Sigma_zz + Sigma_xz - Sigma_xz(i-x) + Sigma_yz - Sigma_yz(i-y)
+// (the (a,b) edge stress owned by cell i sits at r_i + h/2 (e_a + e_b)).  This
+// kernel draws W_A and W_B of every cell once per step (Philox4x32-10, the FP32
+// normals of ic_device.cuh) over the same bands of whole rows as the stage
+// kernel, exchanges the in-plane stresses through shared memory, marches z
+// with the z neighbours in registers, and stores D_1, D_2, D_3 (nine words per
+// cell) for the three stage launches.  It reads nothing from global memory.
+constexpr int kNoiseMaxThreads = 576;
+
+struct NoiseArgs {
+  float *__restrict__ d[9];   // D_1 (x, y, z faces), D_2, D_3, each [z][y][x]
+  int nx, ny, nz;
+  float nd, nt, ne;           // 4 x (sqrt2 S, sqrt2 (B - S/3), S)
+  RoundKeys rk;               // Philox round keys of the noise key
+  uint32_t box;
+  const int64_t *step;
+  int ty, nrow, wrapy, ncols;
+};
+
+template <int VC>
+__global__ void __launch_bounds__(kNoiseMaxThreads, 1) k_noise_rows(const NoiseArgs a) {
+  extern __shared__ __align__(16) float sm[];   // [plane parity][stream A, B][xx, yy, xy, xz, yz][R][NX]
+  const int NX = a.nx, NY = a.ny, NZ = a.nz, QX = NX / VC;
+  const int R = a.nrow, TY = a.ty, wrapy = a.wrapy;
+  const int plane = R * NX;
+  const int t = threadIdx.x;
+  const int r = t / QX, q = t - r * QX, xq = VC * q;
+  const int em = (q == 0 ? NX : xq) - 1, ep = q == QX - 1 ? 0 : xq + VC;
+  const int rm = wrapy ? (r == 0 ? R - 1 : r - 1) : max(r - 1, 0);
+  const int rp = wrapy ? (r == R - 1 ? 0 : r + 1) : min(r + 1, R - 1);
+  const int row = r * NX;
+  const uint32_t ustep = uint32_t(*a.step);
+  const float nd = a.nd, nt = a.nt, ne = a.ne;
+  const auto zw = [NZ](int p) { return p < 0 ? p + NZ : (p >= NZ ? p - NZ : p); };
+  const auto buf = [&](int p, int sI, int comp) { return sm + (((p & 1) * 2 + sI) * 5 + comp) * plane; };
+
+  const int units = a.ncols * NZ;
+  const int u_end = int((long long)units * (blockIdx.x + 1) / gridDim.x);
+  for (int u = int((long long)units * blockIdx.x / gridDim.x); u < u_end;) {
+    const int col = u / NZ;
+    const int z0 = u - col * NZ;
+    const int z1 = min(NZ, z0 + (u_end - u));
+    u += z1 - z0;
+    const int y0 = wrapy ? 0 : col * TY;
+    const int y = wrap((wrapy ? 0 : y0 - 1) + r, NY);
+    const bool own = wrapy ? true : (r >= 1 && r <= TY && y0 - 1 + r < NY);
+    const auto cell = [&](int p, int e) {
+      return uint32_t(xq + e) + uint32_t(NX) * (uint32_t(y) + uint32_t(NY) * uint32_t(zw(p)));
+    };
+    // the stresses of plane p of both streams at this thread's cells, two at a
+    // time: the in-plane components into the plane's buffer, Sigma_zz returned
+    const auto draw = [&](int p, float zzA[VC], float zzB[VC]) {
+#pragma unroll
+      for (int h = 0; h < VC / 2; ++h) {
+        float2 sxx[2], syy[2], sxy[2], sxz[2], syz[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int e = 2 * h + j;
+          float w[2][6];
+          stress_normals_ab_rk(a.rk, a.box, cell(p, e), ustep, w[0], w[1]);
+#pragma unroll
+          for (int sI = 0; sI < 2; ++sI) {
+            // Sigma_aa = sqrt2 S N_aa + sqrt2 (B - S/3) tr N, Sigma_ab = S N_ab (times 4)
+            const float ntr = mul_rn(nt, add_rn(add_rn(w[sI][0], w[sI][1]), w[sI][2]));
+            (j == 0 ? sxx[sI].x : sxx[sI].y) = fma_rn(nd, w[sI][0], ntr);
+            (j == 0 ? syy[sI].x : syy[sI].y) = fma_rn(nd, w[sI][1], ntr);
+            (j == 0 ? sxy[sI].x : sxy[sI].y) = mul_rn(ne, w[sI][3]);
+            (j == 0 ? sxz[sI].x : sxz[sI].y) = mul_rn(ne, w[sI][4]);
+            (j == 0 ? syz[sI].x : syz[sI].y) = mul_rn(ne, w[sI][5]);
+            (sI == 0 ? zzA : zzB)[e] = fma_rn(nd, w[sI][2], ntr);
+          }
+        }
+#pragma unroll
+        for (int sI = 0; sI < 2; ++sI) {
+          const int o = row + xq + 2 * h;
+          *reinterpret_cast<float2 *>(buf(p, sI, 0) + o) = sxx[sI];
+          *reinterpret_cast<float2 *>(buf(p, sI, 1) + o) = syy[sI];
+          *reinterpret_cast<float2 *>(buf(p, sI, 2) + o) = sxy[sI];
+          *reinterpret_cast<float2 *>(buf(p, sI, 3) + o) = sxz[sI];
+          *reinterpret_cast<float2 *>(buf(p, sI, 4) + o) = syz[sI];
+        }
+      }
+    };
+
+    __syncthreads();   // the previous run's reads of shared memory are done
+    // Sigma_xz, Sigma_yz of the plane below the run (own cells: blocks 1, 2 only)
+    float xzA[VC], yzA[VC], xzB[VC], yzB[VC];
+#pragma unroll
+    for (int e = 0; e < VC; ++e) {
+      const uint4 h1 = philox4x32_10_rk(make_uint4(cell(z0 - 1, e), ustep, (kPurposeStress << 16) | 1u, a.box), a.rk);
+      const uint4 h2 = philox4x32_10_rk(make_uint4(cell(z0 - 1, e), ustep, (kPurposeStress << 16) | 2u, a.box), a.rk);
+      float w4, w5, u4, u5;
+      box_muller_f32(h1.x, h1.y, w4, w5);   // W_A: xz, yz
+      box_muller_f32(h2.z, h2.w, u4, u5);   // W_B: xz, yz
+      xzA[e] = mul_rn(ne, w4);
+      yzA[e] = mul_rn(ne, w5);
+      xzB[e] = mul_rn(ne, u4);
+      yzB[e] = mul_rn(ne, u5);
+    }
+    float zzA[VC], zzB[VC];
+    draw(z0, zzA, zzB);
+    for (int k = z0; k < z1; ++k) {
+      float znA[VC], znB[VC];
+      draw(k + 1, znA, znB);
+      __syncthreads();   // plane k's buffer is complete (and plane k + 1's)
+      if (own) {
+        float D[2][3][VC];
+#pragma unroll
+        for (int sI = 0; sI < 2; ++sI) {
+          const float *XX = buf(k, sI, 0), *YY = buf(k, sI, 1), *XY = buf(k, sI, 2), *XZ = buf(k, sI, 3),
+                      *YZ = buf(k, sI, 4);
+          const Cells<VC> xx = ldc<VC>(XX + row + xq), yy = ldc<VC>(YY + row + xq), yy_p = ldc<VC>(YY + rp * NX + xq);
+          const Cells<VC> xy = ldc<VC>(XY + row + xq), xy_m = ldc<VC>(XY + rm * NX + xq);
+          const Cells<VC> xz = ldc<VC>(XZ + row + xq), yz = ldc<VC>(YZ + row + xq), yz_m = ldc<VC>(YZ + rm * NX + xq);
+          const float xx_r = XX[row + ep], xy_l = XY[row + em], xz_l = XZ[row + em];
+          float *xz_prev = sI == 0 ? xzA : xzB, *yz_prev = sI == 0 ? yzA : yzB;
+          const float *zz = sI == 0 ? zzA : zzB, *zn = sI == 0 ? znA : znB;
+#pragma unroll
+          for (int e = 0; e < VC; ++e) {
+            const float xxp = e < VC - 1 ? xx.v[e + 1] : xx_r;
+            const float xyl = e > 0 ? xy.v[e - 1] : xy_l;
+            const float xzl = e > 0 ? xz.v[e - 1] : xz_l;
+            D[sI][0][e] = add_rn(add_rn(sub_rn(xxp, xx.v[e]), sub_rn(xy.v[e], xy_m.v[e])), sub_rn(xz.v[e], xz_prev[e]));
+            D[sI][1][e] = add_rn(add_rn(sub_rn(yy_p.v[e], yy.v[e]), sub_rn(xy.v[e], xyl)), sub_rn(yz.v[e], yz_prev[e]));
+            D[sI][2][e] = add_rn(sub_rn(zn[e], zz[e]), add_rn(sub_rn(xz.v[e], xzl), sub_rn(yz.v[e], yz_m.v[e])));
+            xz_prev[e] = xz.v[e];
+            yz_prev[e] = yz.v[e];
+          }
+        }
+        const size_t gi = (size_t(zw(k)) * NY + y) * NX + xq;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          float d1[VC], d2[VC];
+#pragma unroll
+          for (int e = 0; e < VC; ++e) {
+            d1[e] = fma_rn(-1.7320508075688772f, D[1][j][e], D[0][j][e]);
+            d2[e] = fma_rn(1.7320508075688772f, D[1][j][e], D[0][j][e]);
+          }
+          stc<VC>(a.d[j] + gi, d1);
+          stc<VC>(a.d[3 + j] + gi, d2);
+          stc<VC>(a.d[6 + j] + gi, D[0][j]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < VC; ++e) {
+        zzA[e] = znA[e];
+        zzB[e] = znB[e];
+      }
+      __syncthreads();   // plane k's buffer is read: the next draw may refill it
+    }
+  }
+}
+
+size_t noise_smem(int nx, int R) { return size_t(20) * R * nx * sizeof(float); }
 
 struct RowsPlan {
   int vc = 4, ty = 0, nrow = 0, wrapy = 0, ncols = 0, threads = 0, ctas = 0;
@@ -756,13 +777,80 @@ cudaError_t launch_rows_v(const RowArgs &a, const RowsPlan &pl, int stage, bool 
 
 int rows_zmin(const ic_ctx *ctx) { return ctx->zchunk > 0 ? ctx->zchunk : kMinZChunk; }
 
+struct NoisePlan {
+  int ty = 0, nrow = 0, wrapy = 0, ncols = 0, threads = 0, ctas = 0;
+  size_t smem = 0;
+};
+
+// Bands of the noise kernel: as rows_plan, with the run's extra planes of
+// noise (the plane above and half of the plane below) in the cost, and CTAs
+// of fewer than 16 warps counted as if they had 16.
+NoisePlan noise_plan(const ic_grid_params &p, int sm_count) {
+  NoisePlan best;
+  const int qx = p.nx / kRowsVC;
+  double best_cost = 1e300;
+  for (int ty = 1; ty <= p.ny; ++ty) {
+    const bool wy = ty == p.ny;
+    const int R = wy ? p.ny : ty + 2;
+    if (qx * R > kNoiseMaxThreads || noise_smem(p.nx, R) > kRowsSmemCap) continue;
+    const int ncols = wy ? 1 : (p.ny + ty - 1) / ty;
+    const long long units = (long long)ncols * p.nz;
+    const long long ctas = std::max<long long>(1, std::min<long long>(sm_count, (units + kMinZChunk - 1) / kMinZChunk));
+    // the draw is issue-bound: fewer than 16 warps leave issue slots idle
+    const double cost = (double(units) / double(ctas) + 1.7) * std::max(qx * R, 512);
+    if (cost < best_cost * (1.0 - 1e-9)) {
+      best_cost = cost;
+      best.ty = ty;
+      best.nrow = R;
+      best.wrapy = wy ? 1 : 0;
+      best.ncols = ncols;
+      best.ctas = int(ctas);
+    }
+  }
+  if (best.ty == 0) return best;
+  best.threads = qx * best.nrow;
+  best.smem = noise_smem(p.nx, best.nrow);
+  return best;
+}
+
+// The step's stress divergences D_1, D_2, D_3 into noise[0..8].
+cudaError_t launch_noise_rows(const ic_ctx *ctx) {
+  const NoisePlan pl = noise_plan(ctx->p, ctx->sm_count);
+  if (pl.ty == 0) return cudaErrorInvalidConfiguration;
+  const FluidConsts<float> c = make_fluid_consts<float>(ctx->p, ctx->cos_table_f, ctx->drive_f);
+  NoiseArgs a{};
+  for (int j = 0; j < 9; ++j) a.d[j] = static_cast<float *>(ctx->noise[j]);
+  a.nx = ctx->p.nx;
+  a.ny = ctx->p.ny;
+  a.nz = ctx->p.nz;
+  a.nd = c.noise_d4;
+  a.nt = c.noise_t4;
+  a.ne = c.noise_e4;
+  a.rk = philox_round_keys(c.k0, c.k1);
+  a.box = c.box;
+  a.step = ctx->d.step;
+  a.ty = pl.ty;
+  a.nrow = pl.nrow;
+  a.wrapy = pl.wrapy;
+  a.ncols = pl.ncols;
+  auto kern = k_noise_rows<kRowsVC>;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kRowsSmemCap));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  kern<<<pl.ctas, pl.threads, pl.smem, ctx->stream>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool rows_eligible(const ic_grid_params &p) {
   if (p.precision != IC_FP32 || p.nx % 4 != 0 || p.nx > kRowsMaxNx) return false;
   for (int s = 0; s < 3; ++s)
     if (rows_plan(p, s, 1, 1, kRowsVC).ty == 0) return false;
-  return true;
+  return p.kT == 0.0 || noise_plan(p, 1).ty != 0;
 }
 
 bool rows_buffers_aligned(const ic_ctx *ctx) {
@@ -771,7 +859,7 @@ bool rows_buffers_aligned(const ic_ctx *ctx) {
     for (int j = 0; j < 4; ++j)
       if (!al(ctx->U[b][j])) return false;
   if (!al(ctx->pp)) return false;
-  for (int j = 0; j < 6; ++j)
+  for (int j = 0; j < 9; ++j)
     if (!al(ctx->noise[j])) return false;
   return true;
 }
@@ -794,13 +882,10 @@ cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4],
   }
   a.pp = ctx->ps.n > 0 ? static_cast<const float *>(ctx->pp) : nullptr;
   const bool noise = ctx->p.kT > 0.0;
-  for (int j = 0; j < 3; ++j) a.d_in[j] = nullptr;
-  for (int j = 0; j < 6; ++j) a.d_out[j] = nullptr;
-  if (noise) {
-    if (stage == 0)
-      for (int j = 0; j < 6; ++j) a.d_out[j] = static_cast<float *>(ctx->noise[j]);
-    else
-      for (int j = 0; j < 3; ++j) a.d_in[j] = static_cast<const float *>(ctx->noise[(stage == 1 ? 0 : 3) + j]);
+  for (int j = 0; j < 3; ++j) a.d_in[j] = noise ? static_cast<const float *>(ctx->noise[3 * stage + j]) : nullptr;
+  if (noise && stage == 0) {   // the step's noise first: D_1, D_2, D_3 for the three stages
+    const cudaError_t e = launch_noise_rows(ctx);
+    if (e != cudaSuccess) return e;
   }
   a.c = make_fluid_consts<float>(ctx->p, ctx->cos_table_f, ctx->drive_f);
   a.step = ctx->d.step;
@@ -810,7 +895,6 @@ cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4],
   a.nrow = pl.nrow;
   a.wrapy = pl.wrapy;
   a.ncols = pl.ncols;
-  a.rk = philox_round_keys(a.c.k0, a.c.k1);
   const char *stall = std::getenv("IC_STAGE_STALL_TEST");
   a.stall = stall && stall[0] == '1' ? 1 : 0;
   return launch_rows_v<kRowsVC>(a, pl, stage, noise, ctx->stream);

@@ -42,7 +42,11 @@ def ensemble_sums(sums, group=None):
 
 
 def ensemble_force(ens):
-    """Mean over the ensemble's particles of the radiation force -<F_spring>_w."""
+    """Mean over the ensemble's particles of the radiation force -<F_spring>_w.
+
+    A statistic of the ensemble, taken on the host over the boxes' results:
+    each box's time averages are the library's (ic_time_average); averaging
+    independent realizations is outside the method's step."""
     return -np.mean(ens["sf"] / ens["sw_p"][:, None], axis=0)
 
 

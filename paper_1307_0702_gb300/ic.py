@@ -182,6 +182,19 @@ class Grid:
         self._check(self._lib.ic_time_average(self._ctx, _ptr(f), _ptr(lam), ctypes.byref(a2), 1 if reset else 0))
         return f, lam, a2.value
 
+    def objective(self, direction=None, reset=False):
+        """Phi = sum_p d_p . <F_p>_w from the context's sums (ic_objective)."""
+        phi = ctypes.c_double()
+        d = None if direction is None else np.ascontiguousarray(direction, dtype=np.float64).reshape(-1, 3)
+        self._check(self._lib.ic_objective(self._ctx, _ptr(d), ctypes.byref(phi), 1 if reset else 0))
+        return phi.value
+
+    def adjoint_read_kappa(self):
+        """dPhi / d(kappa_p / kappa_f) of every particle (ic_adjoint_read_kappa)."""
+        out = np.empty(self.n_particles)
+        self._check(self._lib.ic_adjoint_read_kappa(self._ctx, _ptr(out)))
+        return out
+
     def stats(self):
         """(total momentum (3,), driven-mode amplitude A, step)."""
         p = np.empty(3)

@@ -164,3 +164,43 @@ def test_batch_as_one_graph_equals_individual_steps(monkeypatch):
             assert np.array_equal(u, v)
     for g in a_grids + b_grids:
         g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("fp64", 1e-11)])
+def test_batch_boxes_against_the_oracle(prec, tol):
+    """Every box of a heterogeneous batch (edges 16, 24, 32 and 48, 0 to 20
+    particles, their own Philox seeds and box ids, tethered and free) against
+    the oracle run of the same box, field by field and particle by particle."""
+    from pairs import compare, run_oracle
+
+    from paper_1307_0702_gb300 import Batch, Grid
+
+    specs = [(16, 0, 11), (24, 7, 12), (32, 20, 13), (48, 13, 14)]
+    w = np.linspace(0.5, 1.0, 3)
+    grids, inputs = [], []
+    for n, npart, box in specs:
+        gp, parts = W.many_particle_config(n, max(npart, 1), kT=1e-3, wave_amp=2e-3, seed=box, precision=prec,
+                                           k_spring=0.4 if box % 2 else 0.0)
+        gp["box"] = box
+        rho, g = W.standing_wave_fields(gp)
+        grid = Grid(gp)
+        grid.set_state(rho, g)
+        grid.init_thermal(200 + box, add=True)
+        sub = {k: v[:npart] for k, v in parts.items()} if npart else None
+        if npart:
+            grid.add_particles(sub["q"], sub["m_e"], sub["kappa_ratio"], sub["k_spring"])
+        grids.append(grid)
+        inputs.append((gp, rho, g, sub))
+    with Batch(grids) as batch:
+        batch.step(3, w)
+    for grid, (gp, rho, g, sub) in zip(grids, inputs):
+        out = {}
+        out["rho"], out["g"] = grid.get_state()
+        if sub is not None:
+            out["lam"], out["u"], out["q"] = grid.forces()
+            out["f_avg"], out["lam_avg"], out["a2"] = grid.time_average()
+        sim = run_oracle(gp, rho, g, sub, nsteps=3, weights=w, thermal_seed=200 + gp["box"])
+        errs = compare(out, sim, gp, q0=None if sub is None else sub["q"])
+        bad = {k: v for k, v in errs.items() if not v <= tol}
+        assert not bad, (gp["nx"], errs)
+        grid.close()

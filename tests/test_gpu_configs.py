@@ -1,0 +1,117 @@
+"""The library on the study's configurations, end to end.
+
+* The single tethered particle in the deterministic 32^3 standing-wave box
+  (h = 1, the particle at L/8 with m_p = 1.5 rho0 V and kappa_p = 0.5
+  kappa_f): the time-averaged spring force of FP64 and FP32 runs against the
+  oracle's FP64 value (tests/golden/config1_force.json, written by
+  make_config1_force.py from the oracle alone), at the converged length of
+  8000 steps (Blackman-Harris window from step 3000).  The FP32 state with
+  FP64 accumulators keeps the force within 1e-4 of the FP64 oracle.
+* The paper-regime dipolar case (Table I: 32^3 cells of h = 10, mirrored
+  tethered pair, rho_p = 2 rho0): FP32 against FP64 at the converged length,
+  within 1e-4.
+* The fluctuating many-particle box (64^3, 1000 particles with
+  m_p / (rho0 V) ~ U[0.5, 2] and kappa_p / kappa_f ~ U[0, 2] (clamped at
+  0.04), kT = 1e-3, standing-wave amplitude 5e-3, 5000 steps) in FP64 and
+  FP32: total momentum is conserved (no tethers; the drive's net force is
+  zero), and away from the particles' kernels the fluid keeps equipartition,
+  <v_y^2> = <v_z^2> = kT / (rho0 h^3) (the components across the wave) and
+  <(delta rho - A(t) cos kx)^2> = rho0 kT / (c^2 h^3) (Sec. 4.5).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1307_0702_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_force.json")
+
+
+def config1_force(precision):
+    from paper_1307_0702_gb300 import Grid
+
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    gp, parts, _ = W.single_particle_config()
+    gp["precision"] = precision
+    rho, g = W.velocity_phase_wave_fields(gp)
+    w = W.blackman_harris(gold["nsteps"], gold["skip"])
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])
+        grid.step(len(w), w)
+        f, lam, a2 = grid.time_average()
+    return gold, f[0], a2
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_single_particle_force_against_the_oracle(precision, tol):
+    gold, f, a2 = config1_force(precision)
+    f_ref = gold["f_spring"][0]
+    assert abs(f[0] - f_ref) <= tol * abs(f_ref), (precision, f[0], f_ref, abs(f[0] / f_ref - 1))
+    assert abs(a2 - gold["a2"]) <= tol * gold["a2"]
+    # the transverse components are zero by symmetry up to rounding
+    assert np.all(np.abs(f[1:]) <= 1e-3 * abs(f_ref))
+
+
+def test_paper_regime_force_fp32_against_fp64():
+    from test_gpu_physics import tethered_pair_force
+
+    a = tethered_pair_force(2.0, 1.0, k_s=1.0, zeta=1.0, precision="fp32", nsteps=24000, skip=8000)
+    b = tethered_pair_force(2.0, 1.0, k_s=1.0, zeta=1.0, precision="fp64", nsteps=24000, skip=8000)
+    assert a[0] == pytest.approx(b[0], rel=1e-4), (a, b)
+    assert a[1] == pytest.approx(b[1], rel=1e-4), (a, b)
+
+
+def kernel_mask(shape, q, reach=2):
+    """True at cells more than `reach` cells (per axis) from every particle."""
+    nz, ny, nx = shape
+    near = np.zeros(shape, dtype=bool)
+    for x, y, z in q:
+        ix, iy, iz = int(np.floor(x)), int(np.floor(y)), int(np.floor(z))
+        xs = np.arange(ix - reach, ix + reach + 2) % nx
+        ys = np.arange(iy - reach, iy + reach + 2) % ny
+        zs = np.arange(iz - reach, iz + reach + 2) % nz
+        near[np.ix_(zs, ys, xs)] = True
+    return ~near
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fluctuating_many_particle_box(precision):
+    from paper_1307_0702_gb300 import Grid
+
+    gp, parts = W.many_particle_config(64, 1000, kT=1e-3, wave_amp=5e-3, seed=1, precision=precision)
+    rho, g = W.standing_wave_fields(gp)
+    kT, rho0, c = gp["kT"], gp["rho0"], gp["c"]
+    k = 2 * np.pi / 64.0
+    cosx = np.cos(k * np.arange(64))[None, None, :]
+    vy2, vz2, dr2 = [], [], []
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.init_thermal(1, add=True)
+        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"])
+        p0 = grid.stats()[0]
+        grid.step(4000)
+        for _ in range(10):
+            grid.step(100)
+            r, gg = grid.get_state()
+            q = grid.forces()[2]
+            far = kernel_mask(r.shape, q)
+            dr = r - rho0
+            rf = [rho0 + 0.5 * (dr + np.roll(dr, -1, axis=2 - a)) for a in range(3)]
+            vy2.append(np.mean((gg[1] / rf[1])[far] ** 2))
+            vz2.append(np.mean((gg[2] / rf[2])[far] ** 2))
+            A = grid.stats()[1]
+            dr2.append(np.mean((dr - A * cosx)[far] ** 2))
+        p1, _, nsteps = grid.stats()
+        scale = sum(np.sum(np.abs(x)) for x in gg)
+    assert nsteps == 5000
+    tol_p = 1e-12 if precision == "fp64" else 1e-6
+    assert np.all(np.abs(p1 - p0) <= tol_p * scale), (p1, p0, scale)
+    assert np.mean(vy2) == pytest.approx(kT / rho0, rel=0.03)
+    assert np.mean(vz2) == pytest.approx(kT / rho0, rel=0.03)
+    assert np.mean(dr2) == pytest.approx(rho0 * kT / c ** 2, rel=0.03)
