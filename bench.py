@@ -39,12 +39,13 @@ ALG_BYTES_PER_CELL_STEP = {"fp32": 128, "fp64": 256}
 # The FP64 form is bound by GB300's FP64 units, not HBM: its roofline counts the
 # floating-point operations of the three stages as written (an FMA is 2; a
 # division, logarithm, square root, sine or cosine 1), 580 per cell and step,
-# against the nominal 1.25 TFLOP/s FP64 rate of the part (no measured figure).
+# against the FP64 FMA rate measured on the GPU by the library's FMA-chain
+# kernel (ic_fma64_rate); the nominal 1.25 TFLOP/s only if that fails.
 ALG_FP64_FLOPS_PER_CELL_STEP = 580
 # revision of the stage kernels: the ncu traffic in profiles/stage_traffic.json
 # is reported only when it was captured on this revision
 STAGE_KERNEL_REV = "pair-scaled-fluxes-ty13"
-FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_TFLOPS = 1.25   # nominal, the fallback
 
 
 def load_peaks():
@@ -113,6 +114,130 @@ class ClockSampler:
         n_inside = 0 if window is None else sum(1 for x in self.lines if window[0] <= x[0] <= window[1])
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm), "samples_in_timed_region": n_inside}
+
+
+def fp64_fma_peak(local):
+    """The FP64 FMA rate of this GPU, measured by the library's FMA-chain
+    kernel (ic_fma64_rate, CUDA events) with the SM clock sampled meanwhile."""
+    import ctypes
+
+    from paper_1307_0702_gb300 import _lib
+
+    lib = _lib.load()
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    w0 = time.perf_counter()
+    st = lib.ic_fma64_rate(200000, ctypes.byref(rate), ctypes.byref(sec))
+    clocks = sampler.stop((w0, time.perf_counter()))
+    if st != 0:
+        return None
+    out = {"tflops": rate.value / 1e12, "seconds": sec.value, "clocks": clocks,
+           "how": "ic_fma64_rate: 8 independent FMA chains per thread, 8 CTAs x 256 threads per SM, CUDA events"}
+    if clocks and clocks.get("sm_mhz"):
+        out["tflops_per_ghz"] = out["tflops"] / (clocks["sm_mhz"] / 1e3)   # the rate scaled by the clock it ran at
+    return out
+
+
+def time_steps(grid, steps, warmup, flush, local):
+    """Device time of `steps` single steps (CUDA events on the library's
+    stream, the L2 flushed before each), the per-class kernel times of the
+    same number of steps launched kernel by kernel, and the clocks."""
+    import torch
+
+    stream = grid.stream
+    grid.step(warmup)
+    grid.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    w0 = time.perf_counter()
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+        grid.step(1)
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop((w0, time.perf_counter()))
+    t = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    grid.profile(True)
+    for i in range(steps):
+        if i % 8 == 0:
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(8_000_000)
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        grid.step(1)
+    prof = grid.profile_read()
+    grid.profile(False)
+    return t, prof, clocks
+
+
+def sub_fp64(steps, warmup, local, flush, peak):
+    """The plain FP64 form of the same workload (the precision the oracle
+    matches to 1e-11): its throughput and its FP64-unit roofline."""
+    from paper_1307_0702_gb300 import workloads as W
+
+    gp, parts = W.large_box_config()
+    gp["precision"] = "fp64"
+    grid = setup_box(gp, parts, seed_thermal=1000)
+    tiling = grid.autotune(reps=1)
+    t, prof, clocks = time_steps(grid, steps, warmup, flush, local)
+    grid.close()
+    cells = gp["nx"] * gp["ny"] * gp["nz"]
+    stage_ms = prof["fluid"][0] / steps
+    tflops = ALG_FP64_FLOPS_PER_CELL_STEP * cells / (stage_ms * 1e-3) / 1e12
+    peak_tf, kind = (peak["tflops"], "measured (ic_fma64_rate)") if peak else (FP64_PEAK_TFLOPS, "nominal")
+    return {"value": cells * steps / t, "unit": "cell-updates/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "particle_steps_per_s": parts["q"].shape[0] * steps / t, "stage_tiling": list(tiling),
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": tflops / peak_tf, "peak_kind": kind, "stage_ms_per_step": stage_ms,
+                         "alg_flops_per_step": ALG_FP64_FLOPS_PER_CELL_STEP * cells},
+            "clocks": clocks}
+
+
+def sub_ensemble(steps, warmup, local, flush, boxes=256):
+    """The FP32 batched ensemble (256 boxes of edges 16-48, ic_batch_step)."""
+    import torch
+
+    from paper_1307_0702_gb300 import Batch, workloads as W
+
+    cfg = W.ensemble_config(boxes)
+    grids = [setup_box(gp, parts, seed_thermal=5000 + b) for b, (gp, parts) in enumerate(cfg)]
+    cells = sum(g.shape[0] * g.shape[1] * g.shape[2] for g in grids)
+    npart = sum(g.n_particles for g in grids)
+    s0 = grids[0].stream
+    with Batch(grids) as batch:
+        batch.autotune(reps=1)
+        batch.step(warmup)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        w0 = time.perf_counter()
+        for i in range(steps):
+            with torch.cuda.stream(s0):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(s0)
+            batch.step(1)
+            with torch.cuda.stream(s0):
+                ev[i][1].record(s0)
+        torch.cuda.synchronize()
+        clocks = sampler.stop((w0, time.perf_counter()))
+    t = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    for g in grids:
+        g.close()
+    return {"value": cells * steps / t, "unit": "cell-updates/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "boxes": boxes, "cells": cells, "particles": npart, "particle_steps_per_s": npart * steps / t,
+            "dtype": "f32", "clocks": clocks,
+            "workload": "256 FP32 boxes, edges uniform in {16,24,32,48}, 1-200 particles each, kT=1e-3, Philox seed "
+                        "= box index, one ic_batch_step per step"}
 
 
 def setup_box(gp, parts, seed_thermal):
@@ -482,6 +607,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the FP64 and ensemble records beside the headline")
+    ap.add_argument("--sub-steps", type=int, default=20)
     ap.add_argument("--adj-steps", type=int, default=1000)
     ap.add_argument("--adj-precision", nargs="+", default=["fp32", "fp64"], choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="box", choices=["box", "ensemble", "adjoint"],
@@ -638,6 +765,15 @@ def main():
                "d2h_bytes_per_step": 3 * npart * (4 if args.precision == "fp32" else 8) + 4,
                "particle_steps_per_s": world * npart * args.steps / el}
 
+    # beside the headline: the plain FP64 form of the same box and the FP32
+    # batched ensemble, each timed like the headline (rank 0 of a 1-GPU run)
+    subs = {}
+    if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_sub:
+        peak64 = fp64_fma_peak(local)
+        subs["fp64_fma_peak"] = peak64
+        subs["fp64"] = sub_fp64(args.sub_steps, 3, local, flush, peak64)
+        subs["ensemble"] = sub_ensemble(args.sub_steps, 3, local, flush)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -648,8 +784,10 @@ def main():
                     "alg_bytes_per_launch": alg_bytes / 3, "alg_bytes_per_step": alg_bytes}
     else:
         tflops = ALG_FP64_FLOPS_PER_CELL_STEP * cells / (stage_ms_per_step * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal (FP64 units)",
+        pk = fp64_fma_peak(local)
+        peak_tf, peak_kind64 = (pk["tflops"], "measured (ic_fma64_rate)") if pk else (FP64_PEAK_TFLOPS, "nominal")
+        roofline = {"bound": "alu", "achieved": tflops, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": tflops / peak_tf, "traffic": None, "peak_kind": peak_kind64, "fp64_fma_peak": pk,
                     "alg_flops_per_step": ALG_FP64_FLOPS_PER_CELL_STEP * cells,
                     "hbm_frac_for_reference": achieved / peak}
     kname = "k_stage_rows" if tiling[0] == gp["nx"] and args.precision == "fp32" else "k_rk3_stage"
@@ -673,6 +811,7 @@ def main():
             "cpu_baseline": base,
             "wall_s_timed": wall,
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
     grid.close()
     if world > 1:

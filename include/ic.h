@@ -261,6 +261,16 @@ enum { IC_STAGE_COPY_THREAD = 0, IC_STAGE_COPY_BULK = 1, IC_STAGE_COPY_ROWS16 = 
 ic_status ic_set_stage_copy(ic_ctx *ctx, int mode);
 ic_status ic_get_stage_copy(const ic_ctx *ctx, int *mode);
 
+/* Measurement helper (the paper has no counterpart): the FP64 fused
+ * multiply-add rate of the current device, from one launch of eight
+ * independent FMA chains per thread over 8 CTAs of 256 threads per SM, each
+ * thread running iters iterations, timed by CUDA events on a stream of its
+ * own (after a short warm-up launch).  *flops_per_s = 2 FLOP per FMA over the
+ * measured time; *seconds (may be NULL) that time.  Synchronous; IC_ERR_ARG
+ * for iters <= 0 or a NULL result pointer, IC_ERR_CUDA on a CUDA error.  It
+ * allocates 8 bytes of device memory for the duration of the call. */
+ic_status ic_fma64_rate(int iters, double *flops_per_s, double *seconds);
+
 /* Verification entry point: the library's counter-based generator,
  * Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11), which draws the
  * stochastic stress (Sec. 4.2) and the thermal initial state, evaluated by

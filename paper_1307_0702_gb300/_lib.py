@@ -60,6 +60,7 @@ SIGNATURES = {
     "ic_set_stage_copy": (c_int, [c_void_p, c_int]),
     "ic_forces_async": (c_int, [c_void_p, c_int]),
     "ic_philox4x32_10": (c_int, [c_int, POINTER(c_uint32), POINTER(c_uint32)]),
+    "ic_fma64_rate": (c_int, [c_int, PD, PD]),
     "ic_forces_collect": (c_int, [c_void_p, c_int, PD]),
     "ic_get_stage_copy": (c_int, [c_void_p, POINTER(c_int)]),
     "ic_autotune": (c_int, [c_void_p, c_int, POINTER(c_int)]),

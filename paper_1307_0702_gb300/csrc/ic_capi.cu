@@ -367,6 +367,23 @@ ic_status launch_one_step(ic_ctx *ctx) {
   return IC_OK;
 }
 
+// FP64 fused multiply-add throughput (ic_fma64_rate): eight independent FMA
+// chains per thread, enough warps to fill every SM's FP64 units.
+constexpr int kFmaChains = 8;
+__global__ void k_fma64(double *sink, int iters, double b, double c) {
+  double a[kFmaChains];
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) a[j] = 1e-3 * (threadIdx.x + j);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) s += a[j];
+  if (s == 12345.6789) sink[0] = s;   // never true for these inputs; keeps the chains live
+}
+
 // Philox4x32-10 of n counter/key pairs (ic_philox4x32_10): the device code of
 // the noise and thermal draws, evaluated on given inputs.
 __global__ void k_philox_eval(int n, const uint32_t *in, uint32_t *out) {
@@ -666,6 +683,41 @@ ic_status ic_forces_collect(ic_ctx *ctx, int slot, double *lambda) {
   int st = 0;
   std::memcpy(&st, ctx->fetch[slot] + rb, sizeof(int));
   return status_error(ctx, st);
+}
+
+ic_status ic_fma64_rate(int iters, double *flops_per_s, double *seconds) {
+  if (iters <= 0 || !flops_per_s) return IC_ERR_ARG;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    return IC_ERR_CUDA;
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return IC_ERR_CUDA;
+  double *sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ic_status rc = IC_OK;
+  const int blocks = 8 * sms, threads = 256;
+  float ms = 0.0f;
+  if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = IC_ERR_CUDA;
+  } else {
+    k_fma64<<<blocks, threads, 0, st>>>(sink, iters / 8 + 1, 1.0000001, 1e-9);   // warm-up
+    cudaEventRecord(e0, st);
+    k_fma64<<<blocks, threads, 0, st>>>(sink, iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.0f)
+      rc = IC_ERR_CUDA;
+  }
+  if (rc == IC_OK) {
+    const double flops = 2.0 * kFmaChains * double(iters) * blocks * threads;
+    *flops_per_s = flops / (1e-3 * ms);
+    if (seconds) *seconds = 1e-3 * ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (sink) cudaFree(sink);
+  cudaStreamDestroy(st);
+  return rc;
 }
 
 ic_status ic_philox4x32_10(int n, const uint32_t *in, uint32_t *out) {

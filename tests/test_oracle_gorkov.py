@@ -14,7 +14,7 @@ paper reports agreement within 1.5 % at 32^3.  Here it comes out within
 
 Outside that regime Gor'kov's inviscid force is not the method's limit: in the
 h = 1 box of the single-particle configuration the viscous length is about
-the particle radius, and the converged oracle force is 0.59 of Gor'kov (see
+the particle radius, and the converged oracle force is 0.57 of Gor'kov (see
 tests/golden/config1_force.json and the GPU test that checks the library
 against it).
 """
