@@ -240,6 +240,43 @@ def sub_ensemble(steps, warmup, local, flush, boxes=256):
                         "= box index, one ic_batch_step per step"}
 
 
+def sub_long_run(steps, local):
+    """The headline box over a long run in one ic_step call (its graph
+    replayed per step, no L2 flush): the amortised step time including the
+    neighbour-list rebuilds the particles' motion triggers, and their count."""
+    import torch
+
+    from paper_1307_0702_gb300 import workloads as W
+
+    gp, parts = W.large_box_config()
+    grid = setup_box(gp, parts, seed_thermal=1000)
+    grid.autotune(reps=1)
+    grid.step(3)
+    grid.sync()
+    r0 = grid.neighbour_rebuilds()
+    stream = grid.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    w0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    grid.step(steps)
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop((w0, time.perf_counter()))
+    t = e0.elapsed_time(e1) / 1e3
+    rebuilds = grid.neighbour_rebuilds() - r0
+    grid.close()
+    cells = gp["nx"] * gp["ny"] * gp["nz"]
+    return {"value": cells * steps / t, "unit": "cell-updates/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "rebuilds": rebuilds, "particle_steps_per_s": parts["q"].shape[0] * steps / t, "clocks": clocks,
+            "how": "one ic_step call of all steps after 3 warm-up steps, CUDA events around it, L2 not flushed"}
+
+
 def setup_box(gp, parts, seed_thermal):
     from paper_1307_0702_gb300 import Grid, workloads as W
 
@@ -609,6 +646,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the FP64 and ensemble records beside the headline")
     ap.add_argument("--sub-steps", type=int, default=20)
+    ap.add_argument("--long-steps", type=int, default=2000,
+                    help="steps of the long-run sub-record (amortised rebuilds)")
     ap.add_argument("--adj-steps", type=int, default=1000)
     ap.add_argument("--adj-precision", nargs="+", default=["fp32", "fp64"], choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="box", choices=["box", "ensemble", "adjoint"],
@@ -773,6 +812,7 @@ def main():
         subs["fp64_fma_peak"] = peak64
         subs["fp64"] = sub_fp64(args.sub_steps, 3, local, flush, peak64)
         subs["ensemble"] = sub_ensemble(args.sub_steps, 3, local, flush)
+        subs["long_run"] = sub_long_run(args.long_steps, local)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

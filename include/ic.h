@@ -165,6 +165,28 @@ ic_status ic_time_average(ic_ctx *ctx, double *f_spring, double *lambda, double 
 /* Total momentum h^3 sum g + sum m_e u (3 doubles, Eq. (eq:totmom)), current
  * driven-mode amplitude A, and the step counter (each may be NULL). */
 ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step);
+/* Number of neighbour-list rebuilds the context's steps have made (App. A.1:
+ * a particle's kernel touches the 27 cells around it, so two particles
+ * interact only within 4h + skin on every axis; the lists are rebuilt, by a
+ * counting sort of the particles into bins of whole cells, after a particle
+ * has moved a quarter of the skin).  Synchronises the stream; IC_ERR_ARG for
+ * a NULL count. */
+ic_status ic_neighbour_rebuilds(ic_ctx *ctx, int64_t *count);
+
+/* Index-check build.  libic_bounds.so is this library compiled with
+ * -DIC_BOUNDS_CHECK: every grid, noise, neighbour-bin and particle index the
+ * kernels form is checked against its array; one outside it raises a flag,
+ * the access is redirected to the array's first element, and the next status
+ * check (ic_step, ic_sync, ic_stats ...) returns IC_ERR_ARG naming the kernel
+ * family.  A debug build: the flags are read back with a device
+ * synchronisation.  ic_bounds_check_build returns 1 in that build, 0 in
+ * libic.so.  ic_bounds_selftest launches (on the legacy default stream) a
+ * kernel that passes an index equal to its extent to the check without
+ * touching memory, and waits for it: IC_OK if the flag rose (it is cleared
+ * again), IC_ERR_STATE in a build without the checks, IC_ERR_CUDA if the
+ * launch fails. */
+int ic_bounds_check_build(void);
+ic_status ic_bounds_selftest(void);
 /* The objective whose gradients the adjoint computes (Sec. 6 reads the
  * acoustic force as the time-averaged tether force):
  *   *phi = sum_p d_p . <F_p>_w,  <F_p>_w = sum_n w_n F_p^{n+1/2} / sum_n w_n
@@ -300,14 +322,17 @@ ic_status ic_profile_read(ic_ctx *ctx, double *ms, int64_t *launches, int reset)
  * is all reserved by their own pool, plug-ins that may not allocate after
  * start-up.  params: as for ic_create_grid (stream is used; alloc, free and
  * alloc_ctx are ignored); in / out: device pointers to delta rho, g_x, g_y,
- * g_z of nx*ny*nz values each in the params' precision, out distinct from
- * in; step: the step index n (Philox counter and drive phase).  The same
+ * g_z of nx*ny*nz values each in the params' precision; no out array may
+ * share a byte with an in array or with another out array (IC_ERR_ARG);
+ * step: the step index n (Philox counter and drive phase).  The same
  * kernels as ic_step, without the particle terms.  Scratch lives in one static
  * device array of 5.5 MiB held by every GPU that loads the library, so
  * nx*ny*nz must not exceed IC_NOALLOC_MAX_CELLS (else IC_ERR_CAPACITY).  Its
- * device address is looked up on the first call on each device: make that
- * first call before any stream capture.  Calls share the array (it keeps the
- * last call's contents), so calls that overlap on the GPU race.  Returns
+ * device address is looked up on the first call in each CUDA context and
+ * cached with the context's id, so a device reset (which ends the context)
+ * makes the next call look it up again: make the first call in a context
+ * before any stream capture.  Calls share the array (it keeps the last
+ * call's contents), so calls that overlap on the GPU race.  Returns
  * IC_ERR_ARG on invalid parameters or pointers, IC_ERR_CUDA if the symbol
  * lookup or a launch fails; work is enqueued on params->stream. */
 #define IC_NOALLOC_MAX_CELLS 32768

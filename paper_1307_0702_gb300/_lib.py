@@ -4,7 +4,8 @@ import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_size_t, c_uint32, c_uint64, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libic.so")
+# IC_LIBRARY=bounds selects the index-checking debug build (libic_bounds.so)
+LIB_PATH = os.path.join(HERE, "libic_bounds.so" if os.environ.get("IC_LIBRARY") == "bounds" else "libic.so")
 
 IC_OK, IC_ERR_ARG, IC_ERR_CUDA, IC_ERR_OOM, IC_ERR_NONFINITE, IC_ERR_TIMEOUT, IC_ERR_STATE, IC_ERR_CAPACITY = (
     0, -1, -2, -3, -4, -5, -6, -7)
@@ -46,6 +47,9 @@ SIGNATURES = {
     "ic_particle_density": (c_int, [c_void_p, PD]),
     "ic_time_average": (c_int, [c_void_p, PD, PD, PD, c_int]),
     "ic_stats": (c_int, [c_void_p, PD, PD, POINTER(c_int64)]),
+    "ic_neighbour_rebuilds": (c_int, [c_void_p, POINTER(c_int64)]),
+    "ic_bounds_check_build": (c_int, []),
+    "ic_bounds_selftest": (c_int, []),
     "ic_objective": (c_int, [c_void_p, PD, PD, c_int]),
     "ic_adjoint_read_kappa": (c_int, [c_void_p, PD]),
     "ic_sync": (c_int, [c_void_p]),
@@ -92,8 +96,9 @@ def load():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(
-                f"libic.so is missing at {LIB_PATH}: build it with "
-                "`python -m paper_1307_0702_gb300.build` (needs nvcc for sm_103a)")
+                f"{os.path.basename(LIB_PATH)} is missing at {LIB_PATH}: build it with "
+                "`python -m paper_1307_0702_gb300.build` (add --bounds-check for libic_bounds.so; "
+                "needs nvcc for sm_103a)")
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

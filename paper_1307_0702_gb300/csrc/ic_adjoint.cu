@@ -54,7 +54,8 @@ __device__ __forceinline__ int pw(int v, int n) { return v < 0 ? v + n : (v >= n
 struct Geo {
   int nx, ny, nz;
   __device__ __forceinline__ size_t at(int x, int y, int z) const {
-    return size_t(pw(x, nx)) + size_t(nx) * (size_t(pw(y, ny)) + size_t(ny) * size_t(pw(z, nz)));
+    return size_t(IC_CHK(pw(x, nx), nx)) +
+           size_t(nx) * (size_t(IC_CHK(pw(y, ny), ny)) + size_t(ny) * size_t(IC_CHK(pw(z, nz), nz)));
   }
 };
 
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_stage_rates(StageIn<real> I
     stage_face<real, 0>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g0, r0, t0);
     stage_face<real, 1>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g1, r1, t1);
     stage_face<real, 2>(T, at, coef, inv_h, eta, lam2, rho0, uint32_t(c), g2, r2, t2);
-    const size_t i = size_t(x) + size_t(G.nx) * (size_t(y) + size_t(G.ny) * size_t(z));
+    const size_t i = size_t(IC_CHK(x, G.nx)) + size_t(G.nx) * (size_t(IC_CHK(y, G.ny)) + size_t(G.ny) * size_t(IC_CHK(z, G.nz)));
     gp0[i] = g0;
     gp1[i] = g1;
     gp2[i] = g2;
@@ -837,5 +838,7 @@ cudaError_t update_adjoint_graph(const ic_ctx *ctx, AdjGraph &g, const AdjStepTa
   }
   return cudaSuccess;
 }
+
+IC_BOUNDS_READER(bounds_flag_adjoint)
 
 }  // namespace ic

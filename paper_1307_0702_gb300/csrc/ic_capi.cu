@@ -249,6 +249,15 @@ ic_status check_device_status(ic_ctx *ctx) {
 // The status word as read back with other data: IC_OK, or the error it flags
 // (the flags are cleared).
 ic_status status_error(ic_ctx *ctx, int st) {
+#ifdef IC_BOUNDS_CHECK
+  {  // the debug build's index checks: any index outside its array is an error
+    const unsigned f[4] = {ic::bounds_flag_fluid(), ic::bounds_flag_rows(), ic::bounds_flag_particles(),
+                           ic::bounds_flag_adjoint()};
+    if (f[0] | f[1] | f[2] | f[3])
+      return fail(ctx, IC_ERR_ARG, "index out of bounds in the kernels of (fluid, rows, particles, adjoint) = (%u, %u, %u, %u)",
+                  f[0], f[1], f[2], f[3]);
+  }
+#endif
   if (st == 0) return IC_OK;
   IC_CUDA(ctx, cudaMemset(ctx->d.status, 0, sizeof(int)));
   if (st & ic::kStatusStaging)   // first: the stages it stopped leave the rest of the step undefined
@@ -278,13 +287,20 @@ std::vector<PArray> particle_arrays(ic_ctx *ctx) {
           {&s.jrho, r},
           {(void **)&s.base, 6 * sizeof(int)},
           {(void **)&s.nbr, ic::kMaxNeighbours * sizeof(int)},
-          {(void **)&s.nnbr, sizeof(int)}};
+          {(void **)&s.nnbr, sizeof(int)},
+          {(void **)&s.order, sizeof(int)}};
 }
 
 ic_status grow_particles(ic_ctx *ctx, int need) {
   ic::ParticleStore &s = ctx->ps;
   if (need <= s.cap) return IC_OK;
   const int cap = std::max(need, std::max(16, 2 * s.cap));
+  if (!s.bins) {   // bin starts and fill cursors of the neighbour-list counting sort
+    int nb[3];
+    const size_t bytes = (2 * size_t(ic::neighbour_bins(ctx->p, nb)) + 1) * sizeof(int);
+    s.bins = static_cast<int *>(dev_alloc(ctx, bytes));
+    if (!s.bins) return fail(ctx, IC_ERR_OOM, "neighbour bin table allocation of %zu bytes failed", bytes);
+  }
   for (PArray a : particle_arrays(ctx)) {
     void *fresh = dev_alloc(ctx, a.per * size_t(cap));
     if (!fresh) return fail(ctx, IC_ERR_OOM, "particle buffer allocation of %zu bytes failed", a.per * cap);
@@ -464,32 +480,36 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   ctx->d.partials = (double *)dev_alloc(ctx, ctx->n_partials * sizeof(double));
   ctx->d.step = (int64_t *)dev_alloc(ctx, 4 * sizeof(int64_t));
   ctx->d.scalars = (double *)dev_alloc(ctx, 16 * sizeof(double));
-  ctx->d.status = (int *)dev_alloc(ctx, 2 * sizeof(int));
+  ctx->d.status = (int *)dev_alloc(ctx, 4 * sizeof(int));   // status, rebuild, bin_done, spare
+  ctx->d.rebuilds = (long long *)dev_alloc(ctx, sizeof(long long));
   ctx->cos_table = (double *)dev_alloc(ctx, n_ax * sizeof(double));
   ctx->cos_table_f = (float *)dev_alloc(ctx, n_ax * sizeof(float));
   ctx->drive = (double *)dev_alloc(ctx, 3 * sizeof(double));
   ctx->drive_f = (float *)dev_alloc(ctx, 3 * sizeof(float));
   ctx->weights_cap = 1024;
   ctx->d.weights = (double *)dev_alloc(ctx, ctx->weights_cap * sizeof(double));
-  if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->cos_table || !ctx->d.weights ||
+  if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->d.rebuilds || !ctx->cos_table ||
+      !ctx->d.weights ||
       !ctx->cos_table_f || !ctx->drive || !ctx->drive_f)
     return bail(IC_ERR_OOM);
   if (cudaMallocHost(&ctx->staging, (ctx->weights_cap + 3) * sizeof(double)) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(IC_ERR_OOM);
   ctx->d.rebuild = ctx->d.status + 1;
+  ctx->d.bin_done = ctx->d.status + 2;
   std::vector<double> tab(n_ax);
   std::vector<float> tab_f(n_ax);
   for (int i = 0; i < n_ax; ++i) {
     tab[i] = std::cos(ctx->kwave * i * p.h);
     tab_f[i] = float(tab[i]);
   }
-  const int zero_rebuild[2] = {0, 1};
+  const int zero_rebuild[4] = {0, 1, 0, 0};
   if (upload_drive(ctx, 0) != IC_OK ||
       cudaMemcpyAsync(ctx->cos_table, tab.data(), n_ax * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaMemcpyAsync(ctx->cos_table_f, tab_f.data(), n_ax * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaMemsetAsync(ctx->d.step, 0, 4 * sizeof(int64_t), ctx->stream) ||
       cudaMemsetAsync(ctx->d.scalars, 0, 16 * sizeof(double), ctx->stream) ||
+      cudaMemsetAsync(ctx->d.rebuilds, 0, sizeof(long long), ctx->stream) ||
       cudaMemsetAsync(ctx->d.weights, 0, ctx->weights_cap * sizeof(double), ctx->stream) ||
       cudaMemcpyAsync(ctx->d.status, zero_rebuild, sizeof(zero_rebuild), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaStreamSynchronize(ctx->stream))
@@ -585,6 +605,7 @@ ic_status ic_add_particles(ic_ctx *ctx, int n, const double *q, const double *u,
   }
   const int one = 1;
   IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  IC_CUDA(ctx, ic::launch_particle_bins(ctx));
   IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   invalidate_graphs(ctx);
   if (first_id) *first_id = first;
@@ -789,6 +810,30 @@ ic_status ic_objective(ic_ctx *ctx, const double *direction, double *phi, int re
   return IC_OK;
 }
 
+int ic_bounds_check_build(void) {
+#ifdef IC_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+ic_status ic_bounds_selftest(void) {
+  ic::bounds_flag_fluid();   // clear
+  if (ic::launch_bounds_probe(nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return IC_ERR_CUDA;
+  const unsigned f = ic::bounds_flag_fluid();
+  return ic_bounds_check_build() && f == 1u ? IC_OK : IC_ERR_STATE;
+}
+
+ic_status ic_neighbour_rebuilds(ic_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return IC_ERR_ARG;
+  long long v = 0;
+  IC_CUDA(ctx, cudaMemcpyAsync(&v, ctx->d.rebuilds, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *count = v;
+  return IC_OK;
+}
+
 ic_status ic_stats(ic_ctx *ctx, double *p_total, double *mode_amp, int64_t *step) {
   if (!ctx) return IC_ERR_ARG;
   double *sums = ctx->d.scalars + 8;
@@ -917,6 +962,8 @@ ic_status ic_restore(ic_ctx *ctx, const void *buf, size_t bytes) {
   }
   const int st2[2] = {0, 1};
   IC_CUDA(ctx, cudaMemcpy(ctx->d.status, st2, sizeof(st2), cudaMemcpyHostToDevice));
+  IC_CUDA(ctx, ic::launch_particle_bins(ctx));
+  IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   invalidate_graphs(ctx);
   return IC_OK;
 }
@@ -1341,6 +1388,7 @@ ic_status ic_snapshot_load(ic_ctx *ctx, const void *dev_buf) {
   k_snapshot_restart<<<1, 1, 0, ctx->stream>>>(ctx->d.step, step, ctx->d.rebuild, ctx->drive, ctx->drive_f, d[0],
                                                 d[1], d[2]);
   IC_CUDA(ctx, cudaGetLastError());
+  IC_CUDA(ctx, ic::launch_particle_bins(ctx));
   ctx->host_step = step;
   ctx->host_wcount = 0;
   ctx->adj.rec_cur = -1;

@@ -245,4 +245,34 @@ __device__ __forceinline__ real warp_sum(real v) {
   return v;
 }
 
+// Index checks of the debug build (compiled with -DIC_BOUNDS_CHECK into
+// libic_bounds.so).  IC_CHK(i, n) passes an element index i of an array of n
+// elements; outside [0, n) it sets this translation unit's flag and yields 0,
+// so the access stays inside the array and the host reports IC_ERR_ARG.  The
+// checks sit on every grid, noise and particle index the kernels form and
+// stand in for a memory checker.  Without the macro IC_CHK(i, n) is i.
+#ifdef IC_BOUNDS_CHECK
+static __device__ unsigned int ic_bounds_flag;
+template <typename I>
+__device__ __forceinline__ I ic_checked(I i, unsigned long long n) {
+  if (static_cast<unsigned long long>(static_cast<long long>(i)) < n) return i;
+  atomicOr(&ic_bounds_flag, 1u);
+  return I(0);
+}
+#define IC_CHK(i, n) ::ic::ic_checked((i), (unsigned long long)(n))
+// host: this translation unit's flag, cleared on read
+#define IC_BOUNDS_READER(name)                                            \
+  unsigned name() {                                                       \
+    unsigned v = 0, zero = 0;                                             \
+    if (cudaMemcpyFromSymbol(&v, ic_bounds_flag, sizeof(v)) != cudaSuccess || \
+        cudaMemcpyToSymbol(ic_bounds_flag, &zero, sizeof(zero)) != cudaSuccess) \
+      return 2u;                                                          \
+    return v;                                                             \
+  }
+#else
+#define IC_CHK(i, n) (i)
+#define IC_BOUNDS_READER(name) \
+  unsigned name() { return 0u; }
+#endif
+
 }  // namespace ic

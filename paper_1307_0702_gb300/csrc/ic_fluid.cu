@@ -124,6 +124,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   const uint32_t ustep = uint32_t(step);
   const real ca = real(kStageA[STAGE]), cb = real(kStageB[STAGE]);
   const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
+  [[maybe_unused]] const size_t cells = size_t(plane_n) * size_t(NZ);
   real mode_acc = real(0);
 
   // this CTA's share of the (column, plane) pairs
@@ -159,17 +160,17 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
   const uint32_t o_c = uint32_t(x) + uint32_t(NX) * uint32_t(y);
   const uint32_t o_xp = uint32_t(xp) + uint32_t(NX) * uint32_t(y);
   const uint32_t o_yp = uint32_t(x) + uint32_t(NX) * uint32_t(yp);
-  auto cell_of = [&](int kk) { return o_c + uint32_t(zwrap(kk)) * plane_n; };
+  auto cell_of = [&](int kk) { return IC_CHK(o_c + uint32_t(zwrap(kk)) * plane_n, cells); };
   auto fetch = [&](int kk) {
     PlaneRaw<real> r;
     const int k = zwrap(kk);
     const uint32_t kb = uint32_t(k) * plane_n;
     const uint32_t kpb = (k + 1 == NZ) ? 0u : kb + plane_n;
-    const uint32_t i = o_c + kb;
+    const uint32_t i = IC_CHK(o_c + kb, cells);
     r.dr = a.s[0][i];
-    r.drx = a.s[0][o_xp + kb];
-    r.dry = a.s[0][o_yp + kb];
-    r.drz = a.s[0][o_c + kpb];
+    r.drx = a.s[0][IC_CHK(o_xp + kb, cells)];
+    r.dry = a.s[0][IC_CHK(o_yp + kb, cells)];
+    r.drz = a.s[0][IC_CHK(o_c + kpb, cells)];
     r.gx = a.s[1][i];
     r.gy = a.s[2][i];
     r.gz = a.s[3][i];
@@ -481,6 +482,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
   const uint32_t ustep = uint32_t(step);
   const float2 ca = splat2(float(kStageA[STAGE])), cb = splat2(float(kStageB[STAGE]));
   const uint32_t plane_n = uint32_t(NX) * uint32_t(NY);
+  [[maybe_unused]] const size_t cells = size_t(plane_n) * size_t(NZ);
   float mode_acc = 0.0f;
 
   // Bulk staging: thread t < nrows copies one row of one field-plane per pair
@@ -568,6 +570,16 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       if constexpr (BULK) {
         if (row_src) {
           const float *src = row_src + size_t(zwrap(kk + my_dz)) * plane_n;
+#ifdef IC_BOUNDS_CHECK
+          {  // the row's pieces [x, x + len) and [0, RP - len) lie in the field; else copy from its start
+            const size_t row0 = size_t(src - my_field);
+            if (row0 + size_t(seg_a_x) + size_t(seg_a_len) > cells || row0 + size_t(RP - seg_a_len) > cells) {
+              (void)IC_CHK(cells, cells);
+              src = my_field;
+              seg_a_x = 0;
+            }
+          }
+#endif
           if constexpr (STG == kStageBulk) {
             mbar_arrive_expect_tx(bar, RP * sizeof(float));
             bulk_g2s(my_dst, src + seg_a_x, uint32_t(seg_a_len) * sizeof(float), bar);
@@ -589,28 +601,28 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n,
                      b2 = uint32_t(zwrap(kk + 2)) * plane_n;
       const float *S0 = a.s[0];
-      cp_async4(stg + SF_DR0 * EXY + t, S0 + o_c + b0);
-      cp_async4(stg + SF_DR1 * EXY + t, S0 + o_c + b1);
-      cp_async4(stg + SF_DR2 * EXY + t, S0 + o_c + b2);
-      cp_async4(stg + SF_DRX0 * EXY + t, S0 + o_xp + b0);
-      cp_async4(stg + SF_DRX1 * EXY + t, S0 + o_xp + b1);
-      cp_async4(stg + SF_DRY0 * EXY + t, S0 + o_yp + b0);
-      cp_async4(stg + SF_DRY1 * EXY + t, S0 + o_yp + b1);
-      cp_async4(stg + SF_GX0 * EXY + t, a.s[1] + o_c + b0);
-      cp_async4(stg + SF_GX1 * EXY + t, a.s[1] + o_c + b1);
-      cp_async4(stg + SF_GY0 * EXY + t, a.s[2] + o_c + b0);
-      cp_async4(stg + SF_GY1 * EXY + t, a.s[2] + o_c + b1);
-      cp_async4(stg + SF_GZ0 * EXY + t, a.s[3] + o_c + b0);
-      cp_async4(stg + SF_GZ1 * EXY + t, a.s[3] + o_c + b1);
+      cp_async4(stg + SF_DR0 * EXY + t, S0 + IC_CHK(o_c + b0, cells));
+      cp_async4(stg + SF_DR1 * EXY + t, S0 + IC_CHK(o_c + b1, cells));
+      cp_async4(stg + SF_DR2 * EXY + t, S0 + IC_CHK(o_c + b2, cells));
+      cp_async4(stg + SF_DRX0 * EXY + t, S0 + IC_CHK(o_xp + b0, cells));
+      cp_async4(stg + SF_DRX1 * EXY + t, S0 + IC_CHK(o_xp + b1, cells));
+      cp_async4(stg + SF_DRY0 * EXY + t, S0 + IC_CHK(o_yp + b0, cells));
+      cp_async4(stg + SF_DRY1 * EXY + t, S0 + IC_CHK(o_yp + b1, cells));
+      cp_async4(stg + SF_GX0 * EXY + t, a.s[1] + IC_CHK(o_c + b0, cells));
+      cp_async4(stg + SF_GX1 * EXY + t, a.s[1] + IC_CHK(o_c + b1, cells));
+      cp_async4(stg + SF_GY0 * EXY + t, a.s[2] + IC_CHK(o_c + b0, cells));
+      cp_async4(stg + SF_GY1 * EXY + t, a.s[2] + IC_CHK(o_c + b1, cells));
+      cp_async4(stg + SF_GZ0 * EXY + t, a.s[3] + IC_CHK(o_c + b0, cells));
+      cp_async4(stg + SF_GZ1 * EXY + t, a.s[3] + IC_CHK(o_c + b1, cells));
       if (a.pp) {
-        cp_async4(stg + SF_PP0 * EXY + t, a.pp + o_c + b0);
-        cp_async4(stg + SF_PP1 * EXY + t, a.pp + o_c + b1);
+        cp_async4(stg + SF_PP0 * EXY + t, a.pp + IC_CHK(o_c + b0, cells));
+        cp_async4(stg + SF_PP1 * EXY + t, a.pp + IC_CHK(o_c + b1, cells));
       }
       if (NOISE && STAGE != 0) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          cp_async4(stg + (SF_NZ + 2 * j) * EXY + t, a.noise_in[j] + o_c + b0);
-          cp_async4(stg + (SF_NZ + 2 * j + 1) * EXY + t, a.noise_in[j] + o_c + b1);
+          cp_async4(stg + (SF_NZ + 2 * j) * EXY + t, a.noise_in[j] + IC_CHK(o_c + b0, cells));
+          cp_async4(stg + (SF_NZ + 2 * j + 1) * EXY + t, a.noise_in[j] + IC_CHK(o_c + b1, cells));
         }
       }
       cp_async_commit();
@@ -650,7 +662,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
           // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const uint32_t i = o_c + (e == 0 ? b0 : b1);
+            const uint32_t i = IC_CHK(o_c + (e == 0 ? b0 : b1), cells);
             float wa[6], wb[6];
             stress_normals_ab(key, i, ustep, wa, wb);
             const bool st = stored(kk + e);
@@ -702,7 +714,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
     for (int k = z0 - 2; k < z1; k += 2, slot ^= 1) {
       // U^n of the output planes
       const bool out0 = stored(k), out1 = stored(k + 1);
-      const uint32_t i0 = o_c + uint32_t(zwrap(k)) * plane_n, i1 = o_c + uint32_t(zwrap(k + 1)) * plane_n;
+      const uint32_t i0 = IC_CHK(o_c + uint32_t(zwrap(k)) * plane_n, cells),
+                     i1 = IC_CHK(o_c + uint32_t(zwrap(k + 1)) * plane_n, cells);
       float2 un[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -1289,5 +1302,16 @@ cudaError_t launch_end_of_step(ic_ctx *ctx) {
                                                     amp, ctx->omega, p.dt, p.wave_phase, ctx->drive, ctx->drive_f);
   return cudaGetLastError();
 }
+
+// An index equal to its extent passed to the check, no memory touched: the
+// debug build's flag must rise.
+__global__ void k_bounds_probe(int n) { (void)IC_CHK(n, n); }
+
+cudaError_t launch_bounds_probe(cudaStream_t stream) {
+  k_bounds_probe<<<1, 1, 0, stream>>>(7);
+  return cudaGetLastError();
+}
+
+IC_BOUNDS_READER(bounds_flag_fluid)
 
 }  // namespace ic

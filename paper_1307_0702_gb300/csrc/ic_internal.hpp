@@ -104,7 +104,14 @@ struct ParticleStore {
   int *base = nullptr;       // n*6: centre base (x,y,z), own-axis face base (x,y,z)
   int *nbr = nullptr;        // n*kMaxNeighbours, ascending indices
   int *nnbr = nullptr;       // n
+  int *order = nullptr;      // n: particle indices grouped by neighbour bin
+  int *bins = nullptr;       // 2 nbins + 1: first slot of each bin in order (nbins + 1), fill cursors
 };
+
+// Neighbour bins: the box cut into nb[a] slabs per axis of whole cells, each
+// at least floor(cutoff / h) + 1 cells wide, so that two particles within the
+// cutoff on every axis sit in the same or adjacent bins.  Returns nb[0] nb[1] nb[2].
+int neighbour_bins(const ic_grid_params &p, int nb[3]);
 
 struct Device {
   int64_t *step = nullptr;        // [0] step counter n, [1] step of weights[0], [2] number of weights
@@ -112,6 +119,8 @@ struct Device {
   double *scalars = nullptr;      // [0] sum w, [1] sum w A^2, [2] A of the last step
   int *status = nullptr;          // error bits
   int *rebuild = nullptr;         // neighbour list must be rebuilt
+  long long *rebuilds = nullptr;  // neighbour-list rebuilds so far
+  int *bin_done = nullptr;        // CTAs of the running k_final that have finished (0 between launches)
   double *partials = nullptr;     // per-CTA partial sums
 };
 
@@ -296,7 +305,18 @@ cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4],
                               void *const out[4]);
 
 // particles (ic_particles.cu)
+// Index-check flags of the kernels of each source file, cleared on read
+// (always 0 unless the library is built with -DIC_BOUNDS_CHECK).
+unsigned bounds_flag_fluid();
+unsigned bounds_flag_rows();
+unsigned bounds_flag_particles();
+unsigned bounds_flag_adjoint();
+cudaError_t launch_bounds_probe(cudaStream_t stream);
+
 enum ParticlePhase { kHalfStep = 0, kPressure = 1, kForce = 2, kImpulse = 3, kSpread = 4, kFinal = 5 };
+// the counting sort into the neighbour bins, if a rebuild is flagged (after
+// the host has changed positions outside a step)
+cudaError_t launch_particle_bins(ic_ctx *ctx);
 cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *const cur[4],
                              void *const tgt[4]);
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]);

@@ -14,15 +14,19 @@
 //
 // The array's host-side name is only a stand-in for the device symbol: the
 // device address is looked up with cudaGetSymbolAddress the first time the
-// entry point runs on a device (with that device current) and cached per
-// device.  That first call on each device should therefore come before any
-// stream capture.  Every call shares the one array and it keeps the last
+// entry point runs in a CUDA context and cached with that context's unique id
+// (cuCtxGetId, reached through the runtime's driver entry points so that the
+// library does not link the driver).  A device reset ends the context, the
+// next call sees a new id and looks the address up again.  The first call in
+// each context should therefore come before any stream capture.  Every call shares the one array and it keeps the last
 // call's contents; nothing in it has to start at zero (each buffer is fully
 // written before it is read within a call).  Calls whose work overlaps on the
 // GPU (different streams, or several host threads) race on the array.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "ic_device.cuh"
@@ -39,6 +43,7 @@ static __device__ __align__(256) unsigned char ic_noalloc_scratch[kNoallocScratc
 
 std::mutex g_mutex;
 void *g_scratch[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -103,20 +108,54 @@ ic_status step_noalloc(const ic_grid_params &p, const void *const in[4], void *c
   return IC_OK;
 }
 
-// device address of the scratch array on the current device (looked up once per device)
+// unique id of the current CUDA context (0 if it cannot be had)
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f1);
+      get_id = reinterpret_cast<GetId>(f2);
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// device address of the scratch array in the current context: looked up once
+// per context, again after a device reset has replaced the context
 unsigned char *scratch_for_current_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!g_scratch[dev] || id == 0 || id != g_ctx_id[dev]) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, ic_noalloc_scratch) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
     g_scratch[dev] = ptr;
+    g_ctx_id[dev] = current_context_id();   // the lookup made the context current if it was not
   }
   return static_cast<unsigned char *>(g_scratch[dev]);
+}
+
+// [a, a + bytes) and [b, b + bytes) share a byte
+bool overlap(const void *a, const void *b, uint64_t bytes) {
+  const uint64_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
 }
 
 }  // namespace
@@ -132,10 +171,15 @@ extern "C" ic_status ic_fluid_step_noalloc(const ic_grid_params *params, const v
   if (p.forcing < IC_FORCE_NONE || p.forcing > IC_FORCE_PLANE || p.wave_axis < 0 || p.wave_axis > 2) return IC_ERR_ARG;
   const int n_ax = p.wave_axis == 0 ? p.nx : (p.wave_axis == 1 ? p.ny : p.nz);
   if (p.wave_nlambda < 1 || p.plane_index < 0 || p.plane_index >= n_ax) return IC_ERR_ARG;
+  // no output may share a byte with an input (stage 3 reads U^n while it
+  // writes U^{n+1}) or with another output
+  const uint64_t bytes = uint64_t(p.nx) * uint64_t(p.ny) * uint64_t(p.nz) * (p.precision == IC_FP32 ? 4u : 8u);
   for (int j = 0; j < 4; ++j) {
     if (!in[j] || !out[j]) return IC_ERR_ARG;
-    for (int k = 0; k < 4; ++k)
-      if (in[j] == out[k]) return IC_ERR_ARG;   // stage 3 reads U^n while writing U^{n+1}
+    for (int k = 0; k < 4; ++k) {
+      if (overlap(in[k], out[j], bytes)) return IC_ERR_ARG;
+      if (k < j && overlap(out[k], out[j], bytes)) return IC_ERR_ARG;
+    }
   }
   if (int64_t(p.nx) * p.ny * p.nz > kMaxCells) return IC_ERR_CAPACITY;
   unsigned char *scratch = scratch_for_current_device();

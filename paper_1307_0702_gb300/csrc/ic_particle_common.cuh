@@ -21,6 +21,7 @@ struct PConsts {
   real cutoff;         // neighbour cutoff per axis (length)
   real rebuild_at;     // displacement since build that triggers a rebuild
   real skin_limit;     // displacement at which a list is no longer valid
+  int nb[3], nbins;    // neighbour bins per axis and in all
 };
 
 template <typename real>
@@ -40,6 +41,10 @@ struct Pos<double> {
     const double ff = floor(sf + 0.5);
     rf = sf - ff;
     bf = wrap(int(ff), n);
+  }
+  __device__ static int cell(T q, const PConsts<double> &pc, int a) {   // floor(q / h) in [0, n)
+    const int n = a == 0 ? pc.n[0] : (a == 1 ? pc.n[1] : pc.n[2]);
+    return min(max(int(floor(q / pc.h)), 0), n - 1);
   }
   __device__ static T advance(T q, double dq, const PConsts<double> &pc, int a) {
     const double L = a == 0 ? pc.L[0] : (a == 1 ? pc.L[1] : pc.L[2]);
@@ -70,6 +75,7 @@ struct Pos<float> {
     bf = cell;
     rf = frac - 0.5f;
   }
+  __device__ static int cell(T q, const PConsts<float> &, int) { return int(q >> kFixBits); }   // [0, n)
   __device__ static T advance(T q, float dq, const PConsts<float> &pc, int a) {
     const long long span = a == 0 ? pc.span[0] : (a == 1 ? pc.span[1] : pc.span[2]);
     // a non-finite displacement (a state that blew up, which the end-of-step
@@ -101,7 +107,7 @@ struct PV {
   P *q, *q_eq, *q_build, *q_half;
   double *acc;
   real *u, *m_e, *eps, *k_s, *w, *jv_n, *force, *dg, *lam, *jrho;
-  int *base, *nbr, *nnbr;
+  int *base, *nbr, *nnbr, *order, *bins;
 };
 
 template <typename real>
@@ -127,6 +133,8 @@ PV<real> view(const ParticleStore &s) {
   v.base = s.base;
   v.nbr = s.nbr;
   v.nnbr = s.nnbr;
+  v.order = s.order;
+  v.bins = s.bins;
   return v;
 }
 
@@ -154,6 +162,7 @@ PConsts<real> particle_consts(const ic_ctx *ctx) {
   c.cutoff = real((4.0 + kSkin) * p.h);
   c.rebuild_at = real(0.25 * kSkin * p.h);
   c.skin_limit = real(0.5 * kSkin * p.h);
+  c.nbins = neighbour_bins(p, c.nb);
   return c;
 }
 

@@ -18,7 +18,11 @@
 // among the particles whose stencil holds the point), which sums the
 // contributions of itself and its neighbours in ascending index order.
 // Neighbour lists (|dq_a| < 4h + skin on every axis) are rebuilt when a
-// particle has moved more than a quarter skin.
+// particle has moved more than a quarter skin: a counting sort of the
+// particles into bins of whole cells at least the cutoff wide (kBin), then
+// each particle tests the members of the 27 bins around its own and sorts its
+// hits by index, so a rebuild is O(N_p) and gives the same ascending lists as
+// a scan of all pairs would.
 //
 // Positions.  The FP64 path keeps positions in length units (double).  The
 // FP32 path keeps them in 64-bit fixed point, q / h in units of 2^-40, so
@@ -27,6 +31,7 @@
 // stays resolved; its weights and forces are FP32.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -112,7 +117,7 @@ __device__ void stencil_group(typename Pos<real>::T qa, const Lanes &L, const PC
 
 template <typename real>
 __device__ __forceinline__ size_t cell_index(int x, int y, int z, const PConsts<real> &pc) {
-  return size_t(x) + size_t(pc.n[0]) * (size_t(y) + size_t(pc.n[1]) * size_t(z));
+  return size_t(IC_CHK(x, pc.n[0])) + size_t(pc.n[0]) * (size_t(IC_CHK(y, pc.n[1])) + size_t(pc.n[1]) * size_t(IC_CHK(z, pc.n[2])));
 }
 
 __device__ __forceinline__ int step_coord(int b, int d, int n) {
@@ -200,7 +205,7 @@ __device__ __forceinline__ void for_near_members(const PV<real> &P, int p, const
     int m_l = 0;
     bool near = false;
     if (j < nn) {
-      m_l = nb[j];
+      m_l = IC_CHK(nb[j], P.n);
       near = true;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
@@ -331,6 +336,84 @@ __device__ void update_owned_faces(const PV<real> &P, const Grid4<real> &G, int 
 }
 
 // ------------------------------------------------------------------ kernels
+// bin coordinate of particle p along axis a (slabs of whole cells)
+template <typename real>
+__device__ __forceinline__ int bin_axis(typename Pos<real>::T q, const PConsts<real> &pc, int a) {
+  return Pos<real>::cell(q, pc, a) * pc.nb[a] / n_of(pc, a);
+}
+
+// bin of particle p; its position read from L2 (the last CTA of k_final bins
+// positions that other CTAs of the same launch wrote)
+template <typename real>
+__device__ __forceinline__ int bin_of(const PV<real> &P, int p, const PConsts<real> &pc) {
+  const int bx = bin_axis<real>(__ldcg(P.q + 3 * p), pc, 0), by = bin_axis<real>(__ldcg(P.q + 3 * p + 1), pc, 1),
+            bz = bin_axis<real>(__ldcg(P.q + 3 * p + 2), pc, 2);
+  return IC_CHK(bx + pc.nb[0] * (by + pc.nb[1] * bz), pc.nbins);
+}
+
+// Counting sort of the particles into the neighbour bins by the threads of
+// one CTA (blockDim.x a multiple of 32): counts, exclusive prefix sums into
+// bins[0..nbins], then each particle takes a slot of its bin through a
+// cursor.  The order within a bin is that of the atomics; the lists built
+// from it are sorted by index.  Counts and cursors live in L2 (atomics; read
+// back with __ldcg).
+template <typename real>
+__device__ void bin_particles(const PV<real> &P, const PConsts<real> &pc, long long *rebuilds) {
+  __shared__ int warp_off[32];
+  const int t = threadIdx.x, nt = blockDim.x, nb = pc.nbins;
+  int *start = P.bins, *cur = P.bins + nb + 1;
+  for (int b = t; b < nb; b += nt) cur[b] = 0;
+  __syncthreads();
+  for (int p = t; p < P.n; p += nt) atomicAdd(cur + bin_of(P, p, pc), 1);
+  __syncthreads();
+  // thread t scans the contiguous chunk [b0, b1) of the bins
+  const int chunk = (nb + nt - 1) / nt;
+  const int b0 = min(nb, t * chunk), b1 = min(nb, b0 + chunk);
+  int own = 0;
+  for (int b = b0; b < b1; ++b) own += __ldcg(cur + b);
+  int incl = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((t & 31) >= o) incl += v;
+  }
+  if ((t & 31) == 31) warp_off[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    const int w = t < nt / 32 ? warp_off[t] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (t >= o) wi += v;
+    }
+    if (t < nt / 32) warp_off[t] = wi - w;
+  }
+  __syncthreads();
+  int run = warp_off[t >> 5] + incl - own;
+  for (int b = b0; b < b1; ++b) {
+    const int c = __ldcg(cur + b);
+    start[b] = run;
+    cur[b] = run;
+    run += c;
+  }
+  if (t == 0) start[nb] = P.n;
+  __syncthreads();
+  for (int p = t; p < P.n; p += nt) P.order[IC_CHK(atomicAdd(cur + bin_of(P, p, pc), 1), P.n)] = p;
+  if (t == 0) ++*rebuilds;
+}
+
+// The sort when the host has flagged a rebuild (particles added, a state
+// restored); in a step the last CTA of k_final does it.
+constexpr int kBinThreads = 1024;
+
+template <typename real>
+__global__ void __launch_bounds__(kBinThreads) k_bin(PV<real> P, PConsts<real> pc, const int *rebuild,
+                                                     long long *rebuilds) {
+  if (*rebuild == 0) return;
+  bin_particles(P, pc, rebuilds);
+}
+
 template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc,
                                                              int *rebuild, int *status) {
@@ -341,28 +424,49 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_half_step
   if (p >= P.n) return;
 
   if (*rebuild) {
-    // neighbour list from q^n, in ascending index order
+    // neighbour list from q^n: the hits among the members of the 27 bins
+    // around p's (fewer where an axis has fewer than 3 bins), then sorted by
+    // index (all distinct: a rank each)
+    __shared__ int found[kGroupsPerBlock][kMaxNeighbours];
+    __shared__ int nfound[kGroupsPerBlock];
+    const int g = threadIdx.x / kGroup;
     const T q0 = P.q[3 * p], q1 = P.q[3 * p + 1], q2 = P.q[3 * p + 2];
-    const int shift = (threadIdx.x & 31) & ~(kGroup - 1);
-    int count = 0;
-    for (int j0 = 0; j0 < P.n; j0 += kGroup) {
-      const int j = j0 + L.sub;
-      bool hit = false;
-      if (j < P.n && j != p) {
-        hit = fabs(PosT::diff(P.q[3 * j], q0, pc, 0)) < pc.cutoff &&
-              fabs(PosT::diff(P.q[3 * j + 1], q1, pc, 1)) < pc.cutoff &&
-              fabs(PosT::diff(P.q[3 * j + 2], q2, pc, 2)) < pc.cutoff;
+    const int cb[3] = {bin_axis(q0, pc, 0), bin_axis(q1, pc, 1), bin_axis(q2, pc, 2)};
+    if (L.sub == 0) nfound[g] = 0;
+    __syncwarp(L.mask);
+    for (int o = L.sub; o < 27; o += kGroup) {
+      const int d[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      bool repeat = false;
+      int b = 0;
+#pragma unroll
+      for (int a = 2; a >= 0; --a) {
+        repeat = repeat || (pc.nb[a] == 1 && d[a] != 0) || (pc.nb[a] == 2 && d[a] < 0);
+        b = b * pc.nb[a] + wrap(cb[a] + d[a], pc.nb[a]);
       }
-      const unsigned m = (__ballot_sync(L.mask, hit) & L.mask) >> shift;
-      if (hit) {
-        const int slot = count + __popc(m & ((1u << L.sub) - 1u));
-        if (slot < kMaxNeighbours) P.nbr[size_t(p) * kMaxNeighbours + slot] = j;
+      if (repeat) continue;
+      const int i1 = P.bins[IC_CHK(b, pc.nbins) + 1];
+      for (int i = P.bins[b]; i < i1; ++i) {
+        const int j = IC_CHK(P.order[IC_CHK(i, P.n)], P.n);
+        if (j == p) continue;
+        if (fabs(PosT::diff(P.q[3 * j], q0, pc, 0)) < pc.cutoff &&
+            fabs(PosT::diff(P.q[3 * j + 1], q1, pc, 1)) < pc.cutoff &&
+            fabs(PosT::diff(P.q[3 * j + 2], q2, pc, 2)) < pc.cutoff) {
+          const int slot = atomicAdd(&nfound[g], 1);
+          if (slot < kMaxNeighbours) found[g][slot] = j;
+        }
       }
-      count += __popc(m);
+    }
+    __syncwarp(L.mask);
+    const int total = nfound[g], count = min(total, kMaxNeighbours);
+    for (int e = L.sub; e < count; e += kGroup) {
+      const int v = found[g][e];
+      int rank = 0;
+      for (int k = 0; k < count; ++k) rank += found[g][k] < v ? 1 : 0;
+      P.nbr[size_t(p) * kMaxNeighbours + rank] = v;
     }
     if (L.sub == 0) {
-      if (count > kMaxNeighbours) atomicOr(status, kStatusNbrOverflow);
-      P.nnbr[p] = min(count, kMaxNeighbours);
+      if (total > kMaxNeighbours) atomicOr(status, kStatusNbrOverflow);
+      P.nnbr[p] = count;
     }
     if (L.sub < 3) P.q_build[3 * p + L.sub] = P.q[3 * p + L.sub];
   }
@@ -485,13 +589,33 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_impulse(P
 }
 
 template <typename real>
+__device__ void final_particle(const PV<real> &P, const Grid4<real> &G, const PConsts<real> &pc, const int64_t *step,
+                               const double *weights, int *rebuild, real *pp, int p, const Lanes &L);
+
+// Substep 7 for every particle; the CTA that finishes last then sorts the
+// particles into the neighbour bins if any of them asked for a rebuild.
+template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<real> P, Grid4<real> G, PConsts<real> pc,
                                                          const int64_t *step, const double *weights, int *rebuild,
-                                                         real *pp) {
-  using PosT = Pos<real>;
+                                                         real *pp, int *done, long long *rebuilds) {
   const int p = group_particle();
   const Lanes L = group_lanes();
-  if (p >= P.n) return;
+  if (p < P.n) final_particle(P, G, pc, step, weights, rebuild, pp, p, L);
+  __shared__ int last;
+  __threadfence();   // this thread's q^{n+1} and rebuild flag, before the CTA counts itself done
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (*reinterpret_cast<volatile int *>(rebuild)) bin_particles(P, pc, rebuilds);
+  if (threadIdx.x == 0) *done = 0;
+}
+
+template <typename real>
+__device__ void final_particle(const PV<real> &P, const Grid4<real> &G, const PConsts<real> &pc, const int64_t *step,
+                               const double *weights, int *rebuild, real *pp, int p, const Lanes &L) {
+  using PosT = Pos<real>;
   int base[6];
   real w[18];
   load_stencil(P, p, base, w);
@@ -584,7 +708,7 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
       break;
     case kFinal:
       k_final<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, ctx->d.step, ctx->d.weights,
-                                                     ctx->d.rebuild, pp);
+                                                     ctx->d.rebuild, pp, ctx->d.bin_done, ctx->d.rebuilds);
       break;
   }
   return cudaGetLastError();
@@ -592,10 +716,28 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
 
 }  // namespace
 
+int neighbour_bins(const ic_grid_params &p, int nb[3]) {
+  const int width = int(std::floor(4.0 + kSkin)) + 1;   // cells: the cutoff is (4 + skin) h
+  const int n[3] = {p.nx, p.ny, p.nz};
+  for (int a = 0; a < 3; ++a) nb[a] = std::max(1, n[a] / width);
+  return nb[0] * nb[1] * nb[2];
+}
+
 cudaError_t launch_particles(ic_ctx *ctx, ParticlePhase phase, int stage, void *const cur[4],
                              void *const tgt[4]) {
   if (ctx->p.precision == IC_FP32) return launch_particles_t<float>(ctx, phase, stage, cur, tgt);
   return launch_particles_t<double>(ctx, phase, stage, cur, tgt);
+}
+
+cudaError_t launch_particle_bins(ic_ctx *ctx) {
+  if (ctx->ps.n == 0) return cudaSuccess;
+  if (ctx->p.precision == IC_FP32)
+    k_bin<float><<<1, kBinThreads, 0, ctx->stream>>>(view<float>(ctx->ps), particle_consts<float>(ctx),
+                                                     ctx->d.rebuild, ctx->d.rebuilds);
+  else
+    k_bin<double><<<1, kBinThreads, 0, ctx->stream>>>(view<double>(ctx->ps), particle_consts<double>(ctx),
+                                                      ctx->d.rebuild, ctx->d.rebuilds);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_particle_velocity(ic_ctx *ctx, int first, int n, void *const state[4]) {
@@ -644,5 +786,7 @@ void positions_to_host(const ic_ctx *ctx, const void *in, size_t n3, double *q) 
     std::memcpy(q, in, n3 * sizeof(double));
   }
 }
+
+IC_BOUNDS_READER(bounds_flag_particles)
 
 }  // namespace ic

@@ -256,7 +256,15 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
                            : which == 1 ? (f == 0 ? a.s[1] : f == 1 ? a.s[2] : f == 2 ? a.s[3] : a.pp)
                                         : (f < NUN ? (f == 0 ? a.n[0] : f == 1 ? a.n[1] : f == 2 ? a.n[2] : a.n[3])
                                                    : (f == NUN ? a.d_in[0] : f == NUN + 1 ? a.d_in[1] : a.d_in[2]));
-        bulk_g2s(smem_u32(dst + f * fstride + rr * NX), src + (size_t(z) * NY + yy) * NX, uint32_t(cnt * NX * 4), bar);
+        size_t first = (size_t(z) * NY + yy) * NX;
+#ifdef IC_BOUNDS_CHECK
+        // the piece [first, first + cnt NX) lies in the field; else it is copied from the field's start
+        if (first + size_t(cnt) * NX > size_t(NX) * NY * NZ) {
+          (void)IC_CHK(1, 0);
+          first = 0;
+        }
+#endif
+        bulk_g2s(smem_u32(dst + f * fstride + rr * NX), src + first, uint32_t(cnt * NX * 4), bar);
       }
     };
     const auto issue_d = [&](int p) {
@@ -382,7 +390,7 @@ __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(c
       const float *VXk = sv + (k & 1) * 3 * plane, *VYk = VXk + plane, *VZk = VXk + 2 * plane;
       const float *VXq = sv + ((k + 1) & 1) * 3 * plane, *VYq = VXq + plane;
       const int row = r * NX;
-      const size_t gi = (size_t(zw(k)) * NY + y) * NX + xq;
+      const size_t gi = IC_CHK((size_t(zw(k)) * NY + y) * NX + xq, size_t(NX) * NY * NZ - (VC - 1));
       const Cells<VC> qvy_ym = ldc<VC>(VYq + rm * NX + xq);
       const float qvx_l = VXq[row + em];
       float bulk_up[VC], tzz_up[VC], txz[VC], tyz[VC];
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(kNoiseMaxThreads, 1) k_noise_rows(const NoiseA
             yz_prev[e] = yz.v[e];
           }
         }
-        const size_t gi = (size_t(zw(k)) * NY + y) * NX + xq;
+        const size_t gi = IC_CHK((size_t(zw(k)) * NY + y) * NX + xq, size_t(NX) * NY * NZ - (VC - 1));
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           float d1[VC], d2[VC];
@@ -899,5 +907,7 @@ cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4],
   a.stall = stall && stall[0] == '1' ? 1 : 0;
   return launch_rows_v<kRowsVC>(a, pl, stage, noise, ctx->stream);
 }
+
+IC_BOUNDS_READER(bounds_flag_rows)
 
 }  // namespace ic

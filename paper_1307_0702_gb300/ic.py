@@ -203,6 +203,12 @@ class Grid:
         self._check(self._lib.ic_stats(self._ctx, _ptr(p), ctypes.byref(a), ctypes.byref(s)))
         return p, a.value, s.value
 
+    def neighbour_rebuilds(self):
+        """Neighbour-list rebuilds made so far (counting sort into cell bins)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.ic_neighbour_rebuilds(self._ctx, ctypes.byref(n)))
+        return n.value
+
     def checkpoint(self):
         size = ctypes.c_size_t()
         self._check(self._lib.ic_checkpoint(self._ctx, None, ctypes.byref(size)))

@@ -100,5 +100,5 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
 
     monkeypatch.setattr(_lib, "_lib", None)
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
-    with pytest.raises(RuntimeError, match="libic.so is missing"):
+    with pytest.raises(RuntimeError, match="missing.so is missing at"):
         _lib.load()

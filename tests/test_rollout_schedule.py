@@ -51,6 +51,13 @@ class FakeGrid:
             self.sums = 0.0
         return out
 
+    def objective(self, direction=None, reset=False):
+        if self.sums == 0.0:
+            raise RuntimeError("no sums")
+        if reset:
+            self.sums = 0.0
+        return 0.0
+
     # one step recorded, then reversed
     def step_record(self):
         self.recorded = self.step_n
@@ -71,6 +78,9 @@ class FakeGrid:
 
     def adjoint_read(self):
         return {"eps": np.zeros(1), "m_e": np.zeros(1), "A": 0.0}
+
+    def adjoint_read_kappa(self):
+        return np.zeros(1)
 
 
 @pytest.mark.parametrize("tapes", [True, False])

@@ -44,14 +44,16 @@ def rel(a, b):
     return np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_step_matches_ic_step_twice(prec):
+@pytest.mark.parametrize("shape,prec", [((20, 18, 22), "fp64"), ((20, 18, 22), "fp32"), ((32, 32, 32), "fp64")])
+def test_noalloc_step_matches_ic_step_twice(shape, prec):
+    """Two calls against two ic_step steps; 32^3 FP64 (the single-particle
+    box's grid) is IC_NOALLOC_MAX_CELLS, the largest the scratch holds."""
     import torch
 
     from paper_1307_0702_gb300 import Grid, _lib
 
     lib = _lib.load()
-    gp = W.grid_params((20, 18, 22), kT=1e-3, wave_amp=2e-3, forcing="mode", zeta=0.3, seed=9, precision=prec)
+    gp = W.grid_params(shape, kT=1e-3, wave_amp=2e-3, forcing="mode", zeta=0.3, seed=9, precision=prec)
     rho, g = W.random_fields(gp, seed=2)
     # reference: the context API, two steps
     ref = []
@@ -95,3 +97,14 @@ def test_noalloc_rejects_oversized_and_aliased():
     gp = W.grid_params(16, precision="fp32")
     params = c_params(gp, torch.cuda.current_stream().cuda_stream)
     assert lib.ic_fluid_step_noalloc(ctypes.byref(params), ins, ins, 0) == _lib.IC_ERR_ARG
+    # partial overlaps: an output 8 bytes into an input, two outputs overlapping
+    shifted = (ctypes.c_void_p * 4)(t[0].data_ptr() + 8, *[x.data_ptr() for x in t[5:8]])
+    assert lib.ic_fluid_step_noalloc(ctypes.byref(params), ins, shifted, 0) == _lib.IC_ERR_ARG
+    crossed = (ctypes.c_void_p * 4)(t[4].data_ptr(), t[4].data_ptr() + 4 * (16 ** 3 - 1), t[6].data_ptr(),
+                                    t[7].data_ptr())
+    assert lib.ic_fluid_step_noalloc(ctypes.byref(params), ins, crossed, 0) == _lib.IC_ERR_ARG
+    # adjacent but disjoint arrays are accepted: the four outputs back to back in one buffer
+    flat = torch.zeros(4 * 16 ** 3, device="cuda")
+    packed = (ctypes.c_void_p * 4)(*[flat.data_ptr() + 4 * 16 ** 3 * j for j in range(4)])
+    assert lib.ic_fluid_step_noalloc(ctypes.byref(params), ins, packed, 0) == _lib.IC_OK
+    torch.cuda.synchronize()
