@@ -52,6 +52,11 @@ void dev_free(ic_ctx *ctx, void *p) {
   }
 }
 
+bool pdl_enabled() {
+  const char *v = std::getenv("IC_PDL");
+  return v && v[0] == '1';
+}
+
 }  // namespace ic
 
 namespace {

@@ -245,6 +245,16 @@ __device__ __forceinline__ real warp_sum(real v) {
   return v;
 }
 
+// Entry of a kernel launched with programmatic dependent launch (launch_k):
+// wait until the preceding grid in the stream has completed and its writes
+// are visible, then let the next grid launch (its CTAs become resident as
+// this grid's leave, and wait in turn).  Without the launch attribute both
+// return at once.  Nothing before this call may touch global memory.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Index checks of the debug build (compiled with -DIC_BOUNDS_CHECK into
 // libic_bounds.so).  IC_CHK(i, n) passes an element index i of an array of n
 // elements; outside [0, n) it sets this translation unit's flag and yields 0,

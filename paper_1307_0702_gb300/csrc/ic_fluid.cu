@@ -98,6 +98,7 @@ constexpr int min_ctas() {
 template <typename real, int TX, int TY, int STAGE, bool NOISE>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) * (TY + 2)>())
     k_rk3_stage(const StageArgs<real> a) {
+  pdl_enter();
   constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY;
   enum { GX = 0, GY, GZ, VX, VY, VZ };
   enum { TXX = 0, TYY, TXY, TYX, TZX, TZY };
@@ -453,6 +454,7 @@ enum { kStageThread = 0, kStageBulk = 1, kStageRows16 = 2 };
 template <int TX, int TY, int STAGE, bool NOISE, int STG>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (TY + 2)>())
     k_rk3_stage_z2(const StageArgs<float> a) {
+  pdl_enter();
   constexpr int EX = TX + 2, EY = TY + 2, EXY = EX * EY, RP = TX + 8;
   constexpr bool BULK = STG != kStageThread;   // row layout, mbarrier
   static_assert(bulk_rows_max<TX, TY>() <= EXY, "one staged row per thread");
@@ -930,12 +932,12 @@ void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream
                 : stg == kStageRows16 ? k_rk3_stage_z2<TX, TY, STAGE, NOISE, kStageRows16>
                                       : k_rk3_stage_z2<TX, TY, STAGE, NOISE, kStageThread>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    kern<<<ctas, EXY, smem, stream>>>(a);
+    launch_k(kern, dim3(ctas), dim3(EXY), smem, stream, a);
   } else {
     const size_t smem = 18 * EXY * sizeof(real);
     auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    kern<<<ctas, EXY, smem, stream>>>(a);
+    launch_k(kern, dim3(ctas), dim3(EXY), smem, stream, a);
   }
 }
 
@@ -1109,6 +1111,7 @@ __global__ void k_field_sums(int nx, int ny, int nz, int axis, const double *cos
 __global__ void k_end_of_step(const double *partials, int nb, double inv_cells, int has_mode,
                               int64_t *step, const double *weights, double *scalars, int *status,
                               double amp, double omega, double dt, double phase, double *drive, float *drive_f) {
+  pdl_enter();
   __shared__ double s[kRedThreads];
   const int64_t n0 = step[0];   // read by every thread before thread 0 advances it
   double acc = 0.0;
@@ -1297,10 +1300,9 @@ cudaError_t launch_end_of_step(ic_ctx *ctx) {
   const int has_mode = 1;
   const ic_grid_params &p = ctx->p;
   const double amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;
-  k_end_of_step<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d.partials, nb, 1.0 / double(ctx->cells), has_mode,
-                                                    ctx->d.step, ctx->d.weights, ctx->d.scalars, ctx->d.status,
-                                                    amp, ctx->omega, p.dt, p.wave_phase, ctx->drive, ctx->drive_f);
-  return cudaGetLastError();
+  return launch_k(k_end_of_step, dim3(1), dim3(kRedThreads), 0, ctx->stream, ctx->d.partials, nb,
+                  1.0 / double(ctx->cells), has_mode, ctx->d.step, ctx->d.weights, ctx->d.scalars, ctx->d.status, amp,
+                  ctx->omega, p.dt, p.wave_phase, ctx->drive, ctx->drive_f);
 }
 
 // An index equal to its extent passed to the check, no memory touched: the

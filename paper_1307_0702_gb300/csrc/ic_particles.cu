@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(PV<real> P, PConsts<real> p
 template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_half_step(PV<real> P, Grid4<real> G, PConsts<real> pc,
                                                              int *rebuild, int *status) {
+  pdl_enter();
   using PosT = Pos<real>;
   using T = typename PosT::T;
   const int p = group_particle();
@@ -511,6 +512,7 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_half_step
 template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_pressure(PV<real> P, Grid4<real> G, PConsts<real> pc, real *pp,
                                                             int *rebuild) {
+  pdl_enter();
   const int p = group_particle();
   const Lanes L = group_lanes();
   // the neighbour lists were rebuilt (if flagged) by the half step: clear the flag
@@ -558,6 +560,7 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_pressure(
 template <typename real, int KIND>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_face_update(PV<real> P, Grid4<real> G, PConsts<real> pc,
                                                                real scale) {
+  pdl_enter();
   __shared__ Member<real> sm[kGroupsPerBlock];
   const int p = group_particle();
   const Lanes L = group_lanes();
@@ -567,6 +570,7 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_face_upda
 
 template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_impulse(PV<real> P, Grid4<real> G, PConsts<real> pc) {
+  pdl_enter();
   const int p = group_particle();
   const Lanes L = group_lanes();
   if (p >= P.n) return;
@@ -598,6 +602,7 @@ template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<real> P, Grid4<real> G, PConsts<real> pc,
                                                          const int64_t *step, const double *weights, int *rebuild,
                                                          real *pp, int *done, long long *rebuilds) {
+  pdl_enter();
   const int p = group_particle();
   const Lanes L = group_lanes();
   if (p < P.n) final_particle(P, G, pc, step, weights, rebuild, pp, p, L);
@@ -690,26 +695,21 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
   real *pp = static_cast<real *>(ctx->pp);
   switch (phase) {
     case kHalfStep:
-      k_half_step<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(cur), pc, ctx->d.rebuild, ctx->d.status);
-      break;
+      return launch_k(k_half_step<real>, grid, block, 0, ctx->stream, P, grid4<real>(cur), pc, ctx->d.rebuild,
+                      ctx->d.status);
     case kPressure:
-      k_pressure<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, pp,
-                                                        stage == 0 ? ctx->d.rebuild : nullptr);
-      break;
+      return launch_k(k_pressure<real>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, pp,
+                      stage == 0 ? ctx->d.rebuild : nullptr);
     case kForce:
-      k_face_update<real, 0><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc,
-                                                                real(kCoef[stage] * ctx->p.dt));
-      break;
+      return launch_k(k_face_update<real, 0>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc,
+                      real(kCoef[stage] * ctx->p.dt));
     case kImpulse:
-      k_impulse<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc);
-      break;
+      return launch_k(k_impulse<real>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc);
     case kSpread:
-      k_face_update<real, 1><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, real(-1));
-      break;
+      return launch_k(k_face_update<real, 1>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, real(-1));
     case kFinal:
-      k_final<real><<<grid, block, 0, ctx->stream>>>(P, grid4<real>(tgt), pc, ctx->d.step, ctx->d.weights,
-                                                     ctx->d.rebuild, pp, ctx->d.bin_done, ctx->d.rebuilds);
-      break;
+      return launch_k(k_final<real>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, ctx->d.step,
+                      ctx->d.weights, ctx->d.rebuild, pp, ctx->d.bin_done, ctx->d.rebuilds);
   }
   return cudaGetLastError();
 }

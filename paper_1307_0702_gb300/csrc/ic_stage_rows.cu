@@ -153,6 +153,7 @@ __device__ __forceinline__ bool cbar_or(int T, bool pred) {
 
 template <int VC, int STAGE, bool NOISE, bool PROD>
 __global__ void __launch_bounds__(rows_max_threads<VC>() + 32, 1) k_stage_rows(const RowArgs a) {
+  pdl_enter();
   constexpr int NSD = kRowsNSD, NSG = rows_nsg(STAGE), NSN = kRowsNSN;
   constexpr int NUN = rows_nun(STAGE), NFN = rows_nfn(STAGE, NOISE);
   extern __shared__ __align__(16) float sm[];
@@ -567,6 +568,7 @@ struct NoiseArgs {
 
 template <int VC>
 __global__ void __launch_bounds__(kNoiseMaxThreads, 1) k_noise_rows(const NoiseArgs a) {
+  pdl_enter();
   extern __shared__ __align__(16) float sm[];   // [plane parity][stream A, B][xx, yy, xy, xz, yz][R][NX]
   const int NX = a.nx, NY = a.ny, NZ = a.nz, QX = NX / VC;
   const int R = a.nrow, TY = a.ty, wrapy = a.wrapy;
@@ -761,8 +763,7 @@ cudaError_t launch_rows_t(const RowArgs &a, const RowsPlan &pl, cudaStream_t str
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  kern<<<pl.ctas, pl.threads, pl.smem, stream>>>(a);
-  return cudaGetLastError();
+  return launch_k(kern, dim3(pl.ctas), dim3(pl.threads), pl.smem, stream, a);
 }
 
 template <int VC, bool PROD>
@@ -848,8 +849,7 @@ cudaError_t launch_noise_rows(const ic_ctx *ctx) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  kern<<<pl.ctas, pl.threads, pl.smem, ctx->stream>>>(a);
-  return cudaGetLastError();
+  return launch_k(kern, dim3(pl.ctas), dim3(pl.threads), pl.smem, ctx->stream, a);
 }
 
 }  // namespace
