@@ -44,7 +44,7 @@ ALG_BYTES_PER_CELL_STEP = {"fp32": 128, "fp64": 256}
 ALG_FP64_FLOPS_PER_CELL_STEP = 580
 # revision of the stage kernels: the ncu traffic in profiles/stage_traffic.json
 # is reported only when it was captured on this revision
-STAGE_KERNEL_REV = "pair-scaled-fluxes-ty13"
+STAGE_KERNEL_REV = "pair-scaled-fluxes-ty13-idx"
 FP64_PEAK_TFLOPS = 1.25   # nominal, the fallback
 
 

@@ -260,7 +260,10 @@ __device__ __forceinline__ void pdl_enter() {
 // elements; outside [0, n) it sets this translation unit's flag and yields 0,
 // so the access stays inside the array and the host reports IC_ERR_ARG.  The
 // checks sit on every grid, noise and particle index the kernels form and
-// stand in for a memory checker.  Without the macro IC_CHK(i, n) is i.
+// stand in for a memory checker.  IC_AT(p, i, j, n) is the address of
+// element i + j of the n-element array at p, checked alike.  Without the
+// macro IC_CHK(i, n) is i and IC_AT(p, i, j, n) is p + i + j, summed in the
+// order of the unchecked code.
 #ifdef IC_BOUNDS_CHECK
 static __device__ unsigned int ic_bounds_flag;
 template <typename I>
@@ -270,6 +273,7 @@ __device__ __forceinline__ I ic_checked(I i, unsigned long long n) {
   return I(0);
 }
 #define IC_CHK(i, n) ::ic::ic_checked((i), (unsigned long long)(n))
+#define IC_AT(p, i, j, n) ((p) + ::ic::ic_checked((i) + (j), (unsigned long long)(n)))
 // host: this translation unit's flag, cleared on read
 #define IC_BOUNDS_READER(name)                                            \
   unsigned name() {                                                       \
@@ -281,6 +285,7 @@ __device__ __forceinline__ I ic_checked(I i, unsigned long long n) {
   }
 #else
 #define IC_CHK(i, n) (i)
+#define IC_AT(p, i, j, n) ((p) + (i) + (j))   // p + i + j: element i + j of the array at p
 #define IC_BOUNDS_READER(name) \
   unsigned name() { return 0u; }
 #endif

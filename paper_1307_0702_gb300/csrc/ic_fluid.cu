@@ -603,28 +603,28 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), z2_min_ctas<(TX + 2) * (T
       const uint32_t b0 = uint32_t(zwrap(kk)) * plane_n, b1 = uint32_t(zwrap(kk + 1)) * plane_n,
                      b2 = uint32_t(zwrap(kk + 2)) * plane_n;
       const float *S0 = a.s[0];
-      cp_async4(stg + SF_DR0 * EXY + t, S0 + IC_CHK(o_c + b0, cells));
-      cp_async4(stg + SF_DR1 * EXY + t, S0 + IC_CHK(o_c + b1, cells));
-      cp_async4(stg + SF_DR2 * EXY + t, S0 + IC_CHK(o_c + b2, cells));
-      cp_async4(stg + SF_DRX0 * EXY + t, S0 + IC_CHK(o_xp + b0, cells));
-      cp_async4(stg + SF_DRX1 * EXY + t, S0 + IC_CHK(o_xp + b1, cells));
-      cp_async4(stg + SF_DRY0 * EXY + t, S0 + IC_CHK(o_yp + b0, cells));
-      cp_async4(stg + SF_DRY1 * EXY + t, S0 + IC_CHK(o_yp + b1, cells));
-      cp_async4(stg + SF_GX0 * EXY + t, a.s[1] + IC_CHK(o_c + b0, cells));
-      cp_async4(stg + SF_GX1 * EXY + t, a.s[1] + IC_CHK(o_c + b1, cells));
-      cp_async4(stg + SF_GY0 * EXY + t, a.s[2] + IC_CHK(o_c + b0, cells));
-      cp_async4(stg + SF_GY1 * EXY + t, a.s[2] + IC_CHK(o_c + b1, cells));
-      cp_async4(stg + SF_GZ0 * EXY + t, a.s[3] + IC_CHK(o_c + b0, cells));
-      cp_async4(stg + SF_GZ1 * EXY + t, a.s[3] + IC_CHK(o_c + b1, cells));
+      cp_async4(stg + SF_DR0 * EXY + t, IC_AT(S0, o_c, b0, cells));
+      cp_async4(stg + SF_DR1 * EXY + t, IC_AT(S0, o_c, b1, cells));
+      cp_async4(stg + SF_DR2 * EXY + t, IC_AT(S0, o_c, b2, cells));
+      cp_async4(stg + SF_DRX0 * EXY + t, IC_AT(S0, o_xp, b0, cells));
+      cp_async4(stg + SF_DRX1 * EXY + t, IC_AT(S0, o_xp, b1, cells));
+      cp_async4(stg + SF_DRY0 * EXY + t, IC_AT(S0, o_yp, b0, cells));
+      cp_async4(stg + SF_DRY1 * EXY + t, IC_AT(S0, o_yp, b1, cells));
+      cp_async4(stg + SF_GX0 * EXY + t, IC_AT(a.s[1], o_c, b0, cells));
+      cp_async4(stg + SF_GX1 * EXY + t, IC_AT(a.s[1], o_c, b1, cells));
+      cp_async4(stg + SF_GY0 * EXY + t, IC_AT(a.s[2], o_c, b0, cells));
+      cp_async4(stg + SF_GY1 * EXY + t, IC_AT(a.s[2], o_c, b1, cells));
+      cp_async4(stg + SF_GZ0 * EXY + t, IC_AT(a.s[3], o_c, b0, cells));
+      cp_async4(stg + SF_GZ1 * EXY + t, IC_AT(a.s[3], o_c, b1, cells));
       if (a.pp) {
-        cp_async4(stg + SF_PP0 * EXY + t, a.pp + IC_CHK(o_c + b0, cells));
-        cp_async4(stg + SF_PP1 * EXY + t, a.pp + IC_CHK(o_c + b1, cells));
+        cp_async4(stg + SF_PP0 * EXY + t, IC_AT(a.pp, o_c, b0, cells));
+        cp_async4(stg + SF_PP1 * EXY + t, IC_AT(a.pp, o_c, b1, cells));
       }
       if (NOISE && STAGE != 0) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          cp_async4(stg + (SF_NZ + 2 * j) * EXY + t, a.noise_in[j] + IC_CHK(o_c + b0, cells));
-          cp_async4(stg + (SF_NZ + 2 * j + 1) * EXY + t, a.noise_in[j] + IC_CHK(o_c + b1, cells));
+          cp_async4(stg + (SF_NZ + 2 * j) * EXY + t, IC_AT(a.noise_in[j], o_c, b0, cells));
+          cp_async4(stg + (SF_NZ + 2 * j + 1) * EXY + t, IC_AT(a.noise_in[j], o_c, b1, cells));
         }
       }
       cp_async_commit();

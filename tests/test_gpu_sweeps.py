@@ -27,8 +27,13 @@ from paper_1307_0702_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def pair_force_ratio(mass_ratio, kappa_ratio, k_s, zeta, drive="mode", nsteps=24000, skip=8000):
-    """Measured / Gor'kov force on the pair (both particles)."""
+def pair_force_ratio(mass_ratio, kappa_ratio, k_s, zeta, drive="mode", nsteps=24000, skip=8000,
+                     paper_layout=False):
+    """Measured / Gor'kov force on the pair (both particles).  drive="plane":
+    the paper's setup of Sec. 6 (wave along z, paper_protocol_config);
+    drive="mode": the wave along x, the pair at L/8 and 7L/8 on one line, or
+    with paper_layout at the paper's places (3L/8 and 5L/8 along the wave,
+    transverse (L/2, L/2) and (0, 0))."""
     from paper_1307_0702_gb300 import Grid
 
     h = 10.0
@@ -41,6 +46,8 @@ def pair_force_ratio(mass_ratio, kappa_ratio, k_s, zeta, drive="mode", nsteps=24
         gp.update(h=h, dt=0.1 * h / gp["c"], zeta=zeta, precision="fp32")
         L = 32 * h
         parts["q"] = np.array([[L / 8, L / 2, L / 2], [7 * L / 8, L / 2, L / 2]])
+        if paper_layout:
+            parts["q"] = np.array([[3 * L / 8, L / 2, L / 2], [5 * L / 8, 0.0, 0.0]])
         parts["m_e"] = np.full(2, (mass_ratio - 1.0) * 8 * h ** 3)
         ax = 0
     rho, g = W.velocity_phase_wave_fields(gp)
@@ -85,13 +92,58 @@ def test_fig4_dipolar_force_over_density_ratio():
 
 
 def test_paper_layout_with_plane_drive():
-    """Sec. 6 as written: one-plane drive, wave along z.  Its harmonics and the
-    different layout leave the force within 12 % of Gor'kov at both points."""
-    r_mono, _ = pair_force_ratio(1.0, 0.25, k_s=0.5, zeta=0.5, drive="plane")
-    r_dip, _ = pair_force_ratio(2.0, 1.0, k_s=1.0, zeta=1.0, drive="plane")
-    for r in (r_mono, r_dip):
-        assert r[0] == pytest.approx(r[1], rel=2e-3)
-        assert r[0] == pytest.approx(1.0, abs=0.12), (r_mono, r_dip)
+    """Sec. 6 as written: one-plane drive (Eq. (pext)), wave along z, particles
+    at (1/2, 1/2, 3/8) L and (0, 0, -3/8) L.
+
+    The drive does not change the force: a drive on one plane forces every
+    Fourier mode of the wave axis alike, each harmonic answers off resonance
+    in phase with the drive, a quadrature away from the resonant mode, and the
+    cross terms average out.  The mode drive with the particles at the same
+    places gives the same ratios (measured after 24000 steps: dipole 1.1005
+    vs 1.1001, monopole 0.9127 vs 0.9130).
+
+    The layout does.  After 24000 steps the tethered particle's first-order
+    ringing (period ~3200 steps, lightly damped) still leaks into the window,
+    with the sign of the wave at the particle: the dipole reads 1.034 at
+    L/8 and 1.072 at 3L/8 on one line, and both settle at 1.051 after 128000
+    steps.  The paper's transverse offset of the mirror particle adds ~1 % to
+    the settled dipole (1.061).  The monopole of a pair on one line, 8 cells
+    apart along the wave, drifts (0.89, 0.86, 0.84 at 24k, 64k, 128k steps);
+    with the paper's offset it stays at 0.913."""
+    for args in [(1.0, 0.25, 0.5, 0.5), (2.0, 1.0, 1.0, 1.0)]:
+        r_plane, _ = pair_force_ratio(*args[:2], k_s=args[2], zeta=args[3], drive="plane")
+        r_mode, _ = pair_force_ratio(*args[:2], k_s=args[2], zeta=args[3], drive="mode", paper_layout=True)
+        assert r_plane[0] == pytest.approx(r_plane[1], rel=2e-3)
+        assert r_plane[0] == pytest.approx(r_mode[0], rel=3e-3), (args, r_plane, r_mode)
+    assert r_plane[0] == pytest.approx(1.100, abs=0.01)          # the dipole, unsettled
+    r_long, _ = pair_force_ratio(2.0, 1.0, k_s=1.0, zeta=1.0, drive="plane", nsteps=128000, skip=32000)
+    assert r_long[0] == pytest.approx(1.061, abs=0.008), r_long  # settled: Fig. 4's 1.05 plus the layout's 1 %
+
+
+def test_plane_drive_harmonics():
+    """The plane drive's spectrum along the wave axis (no particles, 4
+    periods after 8000 steps): the resonant mode at the set amplitude 1e-3
+    rho0 (rms 7.07e-4); modes 3-16 at ~0.83 % of it each, the flat spectrum
+    of a forcing on one plane answered off resonance; mode 2 at ~1.8 %, that
+    plus the advective second harmonic (1.3 % under the mode drive too)."""
+    from paper_1307_0702_gb300 import Grid
+
+    gp, _ = W.paper_protocol_config(2.0, 1.0, 1.0, 1.0, h=10.0)
+    omega = theory.discrete_sound_frequency(gp["c"], gp["h"], 32)
+    per = int(round(2 * np.pi / omega / gp["dt"]))
+    rho, g = W.velocity_phase_wave_fields(gp)
+    prof = []
+    with Grid(gp) as grid:
+        grid.set_state(rho, g)
+        grid.step(8000)
+        for _ in range(per):
+            grid.step(4)
+            prof.append((grid.get_state()[0] - gp["rho0"]).mean(axis=(1, 2)))
+    amp = np.sqrt(np.mean(np.abs(np.fft.rfft(np.array(prof), axis=1) / 16) ** 2, axis=0))
+    assert amp[1] == pytest.approx(1e-3 / np.sqrt(2), rel=5e-3)
+    assert amp[2] < 0.025 * amp[1], amp / amp[1]
+    assert np.all(amp[3:] < 0.012 * amp[1]), amp / amp[1]
+    assert np.all(amp[3:] > 0.006 * amp[1]), amp / amp[1]       # the harmonics are there
 
 
 def density_samples(cp_over_cf, dt_factor=1.0, n=48, warm=400, samples=300, every=8):
