@@ -164,7 +164,8 @@ cudaError_t enqueue_step(ic_ctx *ctx, int cur, bool record = false) {
     IC_TRY(part(ic::kSpread, 0, U1));
     IC_TRY(part(ic::kFinal, 0, U1));
   }
-  IC_TRY(timed_launch(ctx, 2, [&] { return ic::launch_end_of_step(ctx); }));
+  // with particles k_final's last CTA has done the end-of-step bookkeeping
+  if (!parts) IC_TRY(timed_launch(ctx, 2, [&] { return ic::launch_end_of_step(ctx); }));
 #undef IC_TRY
   return cudaSuccess;
 }

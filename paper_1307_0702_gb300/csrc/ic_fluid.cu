@@ -39,6 +39,7 @@
 #include <cstdlib>
 
 #include "ic_async.cuh"
+#include "ic_end_step.cuh"
 #include "ic_device.cuh"
 #include "ic_internal.hpp"
 
@@ -1108,38 +1109,10 @@ __global__ void k_field_sums(int nx, int ny, int nz, int axis, const double *cos
 // End of step: A(t) from the stage-3 partials, weighted accumulation, the
 // non-finite check, the step counter and the drive amplitudes of the next
 // step (one block).
-__global__ void k_end_of_step(const double *partials, int nb, double inv_cells, int has_mode,
-                              int64_t *step, const double *weights, double *scalars, int *status,
-                              double amp, double omega, double dt, double phase, double *drive, float *drive_f) {
+__global__ void k_end_of_step(const EndArgs e) {
   pdl_enter();
   __shared__ double s[kRedThreads];
-  const int64_t n0 = step[0];   // read by every thread before thread 0 advances it
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[b];
-  s[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double A = has_mode ? 2.0 * s[0] * inv_cells : 0.0;
-    const int64_t j = n0 - step[1];
-    const double w = (j >= 0 && j < step[2]) ? weights[j] : 0.0;
-    if (!isfinite(s[0])) atomicOr(status, kStatusNonfinite);
-    scalars[0] += w;
-    scalars[1] += w * A * A;
-    scalars[2] = A;
-    step[0] = n0 + 1;
-  }
-  if (threadIdx.x < 3) {
-    // drive amplitudes of the RK stages of the next step (t^n, t^{n+1}, t^{n+1/2})
-    const double frac = threadIdx.x == 0 ? 0.0 : (threadIdx.x == 1 ? 1.0 : 0.5);
-    const double t = (double(n0 + 1) + frac) * dt;
-    const double d = amp * sin(omega * t + phase);
-    drive[threadIdx.x] = d;
-    drive_f[threadIdx.x] = float(d);
-  }
+  end_of_step_cta(e, s);
 }
 
 }  // namespace
@@ -1293,16 +1266,31 @@ cudaError_t launch_field_sums(ic_ctx *ctx, void *const U[4], double *dev_out4) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_end_of_step(ic_ctx *ctx) {
+EndArgs end_args(const ic_ctx *ctx) {
   const int nb = rows_active(ctx)                ? rows_ctas(ctx, 2)
                  : ctx->p.precision == IC_FP32 ? stage_layout<float>(ctx).ctas
                                                : stage_layout<double>(ctx).ctas;
-  const int has_mode = 1;
   const ic_grid_params &p = ctx->p;
-  const double amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;
-  return launch_k(k_end_of_step, dim3(1), dim3(kRedThreads), 0, ctx->stream, ctx->d.partials, nb,
-                  1.0 / double(ctx->cells), has_mode, ctx->d.step, ctx->d.weights, ctx->d.scalars, ctx->d.status, amp,
-                  ctx->omega, p.dt, p.wave_phase, ctx->drive, ctx->drive_f);
+  EndArgs e{};
+  e.partials = ctx->d.partials;
+  e.nb = nb;
+  e.inv_cells = 1.0 / double(ctx->cells);
+  e.has_mode = 1;
+  e.step = ctx->d.step;
+  e.weights = ctx->d.weights;
+  e.scalars = ctx->d.scalars;
+  e.status = ctx->d.status;
+  e.amp = (p.wave_amp == 0.0 || p.forcing == IC_FORCE_NONE) ? 0.0 : ctx->force_amp;
+  e.omega = ctx->omega;
+  e.dt = p.dt;
+  e.phase = p.wave_phase;
+  e.drive = ctx->drive;
+  e.drive_f = ctx->drive_f;
+  return e;
+}
+
+cudaError_t launch_end_of_step(ic_ctx *ctx) {
+  return launch_k(k_end_of_step, dim3(1), dim3(kRedThreads), 0, ctx->stream, end_args(ctx));
 }
 
 // An index equal to its extent passed to the check, no memory touched: the

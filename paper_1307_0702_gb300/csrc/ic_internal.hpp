@@ -305,6 +305,26 @@ cudaError_t launch_stage(const ic_ctx *ctx, int stage, void *const in_s[4], void
 cudaError_t launch_thermal(ic_ctx *ctx, uint64_t seed, int add);
 cudaError_t launch_field_sums(ic_ctx *ctx, void *const state[4], double *dev_out4);
 cudaError_t launch_end_of_step(ic_ctx *ctx);
+
+// The end-of-step bookkeeping: the driven-mode amplitude A from the last
+// stage's per-CTA partial sums, the weighted sums w and w A^2, the
+// non-finite check, the step counter and the next step's drive amplitudes.
+// A box with particles does it in the last CTA of its final particle
+// substep (k_final), a box without in k_end_of_step.
+struct EndArgs {
+  const double *partials;
+  int nb;
+  double inv_cells;
+  int has_mode;
+  int64_t *step;
+  const double *weights;
+  double *scalars;
+  int *status;
+  double amp, omega, dt, phase;
+  double *drive;
+  float *drive_f;
+};
+EndArgs end_args(const ic_ctx *ctx);
 // context-free stage launch (consts points to a FluidConsts<real> of the params' precision)
 cudaError_t launch_stage_raw(const ic_grid_params &p, const void *consts, int stage, const void *const in_s[4],
                              const void *const in_n[4], void *const out[4], void *const noise[12],

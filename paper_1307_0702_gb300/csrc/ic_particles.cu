@@ -11,7 +11,9 @@
 //   kForce      after each RK stage s, only with tethers: b_s dt S F
 //   kImpulse    substeps 4-5: dg, u^{n+1}, lambda from J v~^{n+1}
 //   kSpread     substep 6: g^{n+1} = g~^{n+1} - S dg
-//   kFinal      substep 7: q^{n+1}; weighted force sums; clears the pressure
+//   kFinal      substep 7: q^{n+1}; weighted force sums; clears the pressure;
+//               its last CTA sorts the neighbour bins (when due) and does the
+//               end-of-step bookkeeping
 //
 // Spreading is deterministic and free of atomics: each grid point near
 // particles is written by exactly one particle (its "owner": the lowest index
@@ -36,6 +38,7 @@
 #include <cstring>
 
 #include "ic_device.cuh"
+#include "ic_end_step.cuh"
 #include "ic_internal.hpp"
 #include "ic_particle_common.cuh"
 
@@ -597,16 +600,19 @@ __device__ void final_particle(const PV<real> &P, const Grid4<real> &G, const PC
                                const double *weights, int *rebuild, real *pp, int p, const Lanes &L);
 
 // Substep 7 for every particle; the CTA that finishes last then sorts the
-// particles into the neighbour bins if any of them asked for a rebuild.
+// particles into the neighbour bins if any of them asked for a rebuild, and
+// does the step's end-of-step bookkeeping (after every CTA has read the step
+// counter it advances).
 template <typename real>
 __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<real> P, Grid4<real> G, PConsts<real> pc,
-                                                         const int64_t *step, const double *weights, int *rebuild,
-                                                         real *pp, int *done, long long *rebuilds) {
+                                                         const double *weights, int *rebuild, real *pp, int *done,
+                                                         long long *rebuilds, const EndArgs e) {
   pdl_enter();
   const int p = group_particle();
   const Lanes L = group_lanes();
-  if (p < P.n) final_particle(P, G, pc, step, weights, rebuild, pp, p, L);
+  if (p < P.n) final_particle(P, G, pc, e.step, weights, rebuild, pp, p, L);
   __shared__ int last;
+  __shared__ double red[kBlockThreads];
   __threadfence();   // this thread's q^{n+1} and rebuild flag, before the CTA counts itself done
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
@@ -614,6 +620,7 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<
   if (!last) return;
   __threadfence();
   if (*reinterpret_cast<volatile int *>(rebuild)) bin_particles(P, pc, rebuilds);
+  end_of_step_cta(e, red);
   if (threadIdx.x == 0) *done = 0;
 }
 
@@ -708,8 +715,8 @@ cudaError_t launch_particles_t(ic_ctx *ctx, ParticlePhase phase, int stage, void
     case kSpread:
       return launch_k(k_face_update<real, 1>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, real(-1));
     case kFinal:
-      return launch_k(k_final<real>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, ctx->d.step,
-                      ctx->d.weights, ctx->d.rebuild, pp, ctx->d.bin_done, ctx->d.rebuilds);
+      return launch_k(k_final<real>, grid, block, 0, ctx->stream, P, grid4<real>(tgt), pc, ctx->d.weights,
+                      ctx->d.rebuild, pp, ctx->d.bin_done, ctx->d.rebuilds, end_args(ctx));
   }
   return cudaGetLastError();
 }
