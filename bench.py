@@ -439,77 +439,88 @@ ALG_ADJ_WORDS_PER_CELL = 15
 ALG_ADJ_FLOPS_PER_CELL = 280
 
 
-def run_adjoint(args):
-    """Differentiable rollout (the gradient of the time-averaged tether force,
-    deterministic): one unit of work is one step of the rollout run forward
-    and reversed (checkpoints every 50 steps, each segment recomputed and its
-    steps recorded and reversed).  FP32 is the line's value; FP64 rides along."""
+def adjoint_record(prec, nsteps, warmup, flush, local, peak, peak_kind, peak64):
+    """One differentiable rollout (the gradient of the time-averaged tether
+    force, deterministic) timed forward and reversed: a unit of work is one
+    step of the rollout run forward and reversed (checkpoints every 50 steps,
+    each segment recomputed and its steps recorded and reversed)."""
     import torch
 
     from paper_1307_0702_gb300 import Grid, workloads as W
     from paper_1307_0702_gb300.adjoint import Rollout
 
-    nsteps, K = args.adj_steps, 50
+    K = 50
+    gp, rho, g, parts = W.line_config(64, 16, wave_amp=1e-3, precision=prec)
+    cells = gp["nx"] * gp["ny"] * gp["nz"]
+    grid = Grid(gp)
+    grid.set_state(rho, g)
+    grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
+    tiling = grid.autotune(reps=3)           # stage-kernel tiling for 64^3 (results do not depend on it)
+    roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K)
+    roll.forward(np.ones(max(warmup, 3)))      # warm-up: graphs captured, snapshots allocated
+    roll.backward()
+    grid.snapshot_load(roll.checkpoints[0])
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi = roll.forward(np.ones(nsteps))
+    t1 = time.perf_counter()
+    gr = roll.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    clocks = sampler.stop((t0, t2))
+    # the same rollout once more with every kernel bracketed by events
+    grid.snapshot_load(roll.checkpoints[0])
+    grid.profile(True)
+    roll.forward(np.ones(nsteps))
+    roll.backward()
+    prof = grid.profile_read()
+    grid.profile(False)
+    grid.close()
+    st_ms, st_n = prof["adjoint_stage"]
+    per_launch = st_ms / st_n * 1e-3
+    words = 4 if prec == "fp32" else 8
+    rec = {"value": nsteps / (t2 - t0), "unit": "rollout-gradient steps/s", "steps": nsteps, "phi": phi,
+           "ms_per_step": 1e3 * (t2 - t0) / nsteps, "forward_ms_per_step": 1e3 * (t1 - t0) / nsteps,
+           "reverse_ms_per_step": 1e3 * (t2 - t1) / nsteps,
+           "cell_steps_per_s": cells * nsteps / (t2 - t0),
+           "kernel_ms_per_step": {k: v[0] / nsteps for k, v in prof.items()},
+           "launches_per_step": sum(v[1] for v in prof.values()) / nsteps,
+           "grad_m_e_0": float(gr["m_e"][0]), "grad_A": float(gr["A"]), "clocks": clocks,
+           "stage_tiling": list(tiling),
+           "workload": "differentiable rollout: 64^3, 16 tethered particles on a line along x, A=1e-3, kT=0, "
+                       "checkpoint every 50, wall time of the forward sweep and the reverse sweep"}
+    if prec == "fp32":
+        achieved = ALG_ADJ_WORDS_PER_CELL * words * cells / per_launch / 1e9
+        rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                           "kernel": "k_adj_stage_rates (3 launches per reversed step)",
+                           "alg_bytes_per_launch": ALG_ADJ_WORDS_PER_CELL * words * cells,
+                           "note": "the 64^3 working set (15 fields, 16 MB) is L2-resident"}
+    else:
+        tflops = ALG_ADJ_FLOPS_PER_CELL * cells / per_launch / 1e12
+        peak_tf, kind = (peak64["tflops"], "measured (ic_fma64_rate)") if peak64 else (FP64_PEAK_TFLOPS, "nominal")
+        rec["roofline"] = {"bound": "alu", "achieved": tflops, "peak": peak_tf, "unit": "TFLOP/s",
+                           "frac": tflops / peak_tf, "traffic": None, "peak_kind": kind,
+                           "kernel": "k_adj_stage_rates (3 launches per reversed step)",
+                           "alg_flops_per_launch": ALG_ADJ_FLOPS_PER_CELL * cells}
+    return rec
+
+
+def run_adjoint(args):
+    """Differentiable rollout: FP32 is the line's value; FP64 rides along."""
+    import torch
+
+    nsteps = args.adj_steps
     peak, peak_kind = load_peaks()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
-    out = {}
-    for prec in args.adj_precision:
-        gp, rho, g, parts = W.line_config(64, 16, wave_amp=1e-3, precision=prec)
-        cells = gp["nx"] * gp["ny"] * gp["nz"]
-        grid = Grid(gp)
-        grid.set_state(rho, g)
-        grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"], parts["u"])
-        tiling = grid.autotune(reps=3)           # stage-kernel tiling for 64^3 (results do not depend on it)
-        roll = Rollout(grid, parts["kappa_ratio"], checkpoint_every=K)
-        roll.forward(np.ones(max(args.warmup, 3)))      # warm-up: graphs captured, snapshots allocated
-        roll.backward()
-        grid.snapshot_load(roll.checkpoints[0])
-        sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-        sampler.start()
-        time.sleep(0.3)
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        phi = roll.forward(np.ones(nsteps))
-        t1 = time.perf_counter()
-        gr = roll.backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        clocks = sampler.stop((t0, t2))
-        # the same rollout once more with every kernel bracketed by events
-        grid.snapshot_load(roll.checkpoints[0])
-        grid.profile(True)
-        roll.forward(np.ones(nsteps))
-        roll.backward()
-        prof = grid.profile_read()
-        grid.profile(False)
-        grid.close()
-        st_ms, st_n = prof["adjoint_stage"]
-        per_launch = st_ms / st_n * 1e-3
-        words = 4 if prec == "fp32" else 8
-        rec = {"value": nsteps / (t2 - t0), "unit": "rollout-gradient steps/s", "phi": phi,
-               "ms_per_step": 1e3 * (t2 - t0) / nsteps, "forward_ms_per_step": 1e3 * (t1 - t0) / nsteps,
-               "reverse_ms_per_step": 1e3 * (t2 - t1) / nsteps,
-               "cell_steps_per_s": cells * nsteps / (t2 - t0),
-               "kernel_ms_per_step": {k: v[0] / nsteps for k, v in prof.items()},
-               "launches_per_step": sum(v[1] for v in prof.values()) / nsteps,
-               "grad_m_e_0": float(gr["m_e"][0]), "grad_A": float(gr["A"]), "clocks": clocks,
-               "stage_tiling": list(tiling)}
-        if prec == "fp32":
-            achieved = ALG_ADJ_WORDS_PER_CELL * words * cells / per_launch / 1e9
-            rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                               "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                               "kernel": "k_adj_stage_rates (3 launches per reversed step)",
-                               "alg_bytes_per_launch": ALG_ADJ_WORDS_PER_CELL * words * cells,
-                               "note": "the 64^3 working set (15 fields, 16 MB) is L2-resident"}
-        else:
-            tflops = ALG_ADJ_FLOPS_PER_CELL * cells / per_launch / 1e12
-            rec["roofline"] = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                               "peak_kind": "nominal (FP64 units)",
-                               "kernel": "k_adj_stage_rates (3 launches per reversed step)",
-                               "alg_flops_per_launch": ALG_ADJ_FLOPS_PER_CELL * cells}
-        out[prec] = rec
+    peak64 = fp64_fma_peak(local) if "fp64" in args.adj_precision else None
+    out = {prec: adjoint_record(prec, nsteps, args.warmup, flush, local, peak, peak_kind, peak64)
+           for prec in args.adj_precision}
     r = out[args.adj_precision[0]]
     line = {
         "metric": ADJOINT_METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": nsteps,
@@ -523,6 +534,8 @@ def run_adjoint(args):
         "roofline": r["roofline"], "gpu_launches": int(round(r["launches_per_step"] * nsteps)),
         "clocks": r["clocks"], **out,
     }
+    if peak64:
+        line["fp64_fma_peak"] = peak64
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = adjoint_cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -649,6 +662,8 @@ def main():
     ap.add_argument("--long-steps", type=int, default=2000,
                     help="steps of the long-run sub-record (amortised rebuilds)")
     ap.add_argument("--adj-steps", type=int, default=1000)
+    ap.add_argument("--sub-adj-steps", type=int, default=1000,
+                    help="steps of the FP32 differentiable-rollout record beside the headline")
     ap.add_argument("--adj-precision", nargs="+", default=["fp32", "fp64"], choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="box", choices=["box", "ensemble", "adjoint"],
                     help="box: the 128^3 single box (default); ensemble: the batched 256-box ensemble")
@@ -813,6 +828,8 @@ def main():
         subs["fp64"] = sub_fp64(args.sub_steps, 3, local, flush, peak64)
         subs["ensemble"] = sub_ensemble(args.sub_steps, 3, local, flush)
         subs["long_run"] = sub_long_run(args.long_steps, local)
+        pk, pk_kind = load_peaks()
+        subs["adjoint"] = adjoint_record("fp32", args.sub_adj_steps, 3, flush, local, pk, pk_kind, peak64)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -479,7 +479,7 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   ctx->pp = dev_alloc(ctx, fbytes);
   if (!ctx->pp) return bail(IC_ERR_OOM);
   if (p.kT > 0.0)
-    for (int j = 0; j < 12; ++j)
+    for (int j = 0; j < (p.precision == IC_FP64 ? 18 : 12); ++j)
       if (!(ctx->noise[j] = dev_alloc(ctx, fbytes))) return bail(IC_ERR_OOM);
   if (cudaMemsetAsync(ctx->pp, 0, fbytes, ctx->stream) != cudaSuccess) return bail(IC_ERR_CUDA);
   ctx->n_partials = ic::fluid_num_partials(ctx);

@@ -52,7 +52,8 @@ struct StageArgs {
   const real *__restrict__ n[4];   // U^n
   real *__restrict__ o[4];         // U_{s+1}
   const real *__restrict__ pp;     // particle pressure S Omega_s at centres, or null
-  const real *__restrict__ noise_in[6];   // stages 2-3: stored W_s (xx, yy, zz, xy, xz, yz)
+  const real *__restrict__ noise_in[6];   // stages 2-3 (and a pre-drawn stage 1): stored W_s
+                                          // (xx, yy, zz, xy, xz, yz)
   real *__restrict__ noise_out[12];       // stage 1: stores W_2 = W_A + sqrt3 W_B and W_3 = W_A
   FluidConsts<real> c;
   const int64_t *step;
@@ -63,6 +64,35 @@ struct StageArgs {
   int ncols_x, ncols_y;            // tile columns along x and y
 };
 
+
+template <typename real>
+struct NoiseOut {
+  real *__restrict__ p[18];   // W_2 (0..5), W_3 (6..11), W_1 (12..17)
+};
+
+// ------------------------------------------------------------ FP64 noise
+// The step's stochastic stresses drawn once per cell (App. A.2's W_A, W_B):
+// W_1 = W_A - sqrt3 W_B, W_2 = W_A + sqrt3 W_B and W_3 = W_A, the same
+// rounded operations as the stage-1 kernel's inline draw, so the step's bits
+// do not depend on which of the two drew them.  The FP64 transcendentals of
+// the 6 Box-Muller pairs dominate an FP64 step; drawn inline they are redone
+// for the ring cells of every tile (1.6x at 32 x 4).
+template <typename real>
+__global__ void __launch_bounds__(256) k_draw_noise(RngKey key, const int64_t *step, uint32_t cells,
+                                                    NoiseOut<real> w) {
+  pdl_enter();
+  const uint32_t ustep = uint32_t(*step);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += gridDim.x * blockDim.x) {
+    real wa[6], wb[6];
+    stress_normals_ab(key, i, ustep, wa, wb);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      w.p[12 + j][i] = fma_rn(real(-1.7320508075688772), wb[j], wa[j]);
+      w.p[j][i] = fma_rn(real(1.7320508075688772), wb[j], wa[j]);
+      w.p[6 + j][i] = wa[j];
+    }
+  }
+}
 
 template <typename real>
 struct PlaneVals {
@@ -96,7 +126,7 @@ constexpr int min_ctas() {
   return sizeof(real) == 4 ? (IC_FP32_MIN_CTAS * 340 + EXY - 1) / EXY : 1;
 }
 
-template <typename real, int TX, int TY, int STAGE, bool NOISE>
+template <typename real, int TX, int TY, int STAGE, bool NOISE, bool PRE>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) * (TY + 2)>())
     k_rk3_stage(const StageArgs<real> a) {
   pdl_enter();
@@ -189,7 +219,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2), min_ctas<real, (TX + 2) *
     v.vx = fdiv(v.gx, fma_rn(half, v.dr + r.drx, rho0));
     v.vy = fdiv(v.gy, fma_rn(half, v.dr + r.dry, rho0));
     v.vz = fdiv(v.gz, fma_rn(half, v.dr + r.drz, rho0));
-    if (NOISE && STAGE == 0) {
+    if (NOISE && STAGE == 0 && !PRE) {
       // W_1 = W_A - sqrt3 W_B for this stage; the cell's own CTA stores W_2, W_3
       const uint32_t i = cell_of(kk);
       real wa[6], wb[6];
@@ -923,7 +953,7 @@ bool bulk_staging_ok(const StageArgs<float> &a) {
   return true;
 }
 
-template <int TX, int TY, int STAGE, bool NOISE, typename real>
+template <int TX, int TY, int STAGE, bool NOISE, bool PRE = false, typename real>
 void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream, int stage_copy) {
   constexpr int EXY = (TX + 2) * (TY + 2);
   if constexpr (use_pair_kernel<real, TX>()) {
@@ -936,7 +966,7 @@ void launch_stage_kernel(const StageArgs<real> &a, int ctas, cudaStream_t stream
     launch_k(kern, dim3(ctas), dim3(EXY), smem, stream, a);
   } else {
     const size_t smem = 18 * EXY * sizeof(real);
-    auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE>;
+    auto kern = k_rk3_stage<real, TX, TY, STAGE, NOISE, PRE>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     launch_k(kern, dim3(ctas), dim3(EXY), smem, stream, a);
   }
@@ -964,17 +994,29 @@ template <typename real, int V, int STAGE, bool NOISE>
 cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const in_n[4],
                            void *const out[4]) {
   constexpr int TX = TileShape<real, V>::TX, TY = TileShape<real, V>::TY;
-  StageArgs<real> a;
+  StageArgs<real> a{};
   for (int j = 0; j < 4; ++j) {
     a.s[j] = static_cast<const real *>(in_s[j]);
     a.n[j] = static_cast<const real *>(in_n[j]);
     a.o[j] = static_cast<real *>(out[j]);
   }
   a.pp = ctx->ps.n > 0 ? static_cast<const real *>(ctx->pp) : nullptr;
-  for (int j = 0; j < 12; ++j) a.noise_out[j] = STAGE == 0 ? static_cast<real *>(ctx->noise[j]) : nullptr;
+  // FP64: the step's noise drawn once per cell by k_draw_noise, stage 1 reads W_1
+  constexpr bool predraw = NOISE && sizeof(real) == 8;
+  for (int j = 0; j < 12; ++j)
+    a.noise_out[j] = STAGE == 0 && !predraw ? static_cast<real *>(ctx->noise[j]) : nullptr;
   for (int j = 0; j < 6; ++j)
-    a.noise_in[j] = STAGE == 0 ? nullptr : static_cast<const real *>(ctx->noise[(STAGE == 1 ? 0 : 6) + j]);
+    a.noise_in[j] = STAGE == 0 ? (predraw ? static_cast<const real *>(ctx->noise[12 + j]) : nullptr)
+                               : static_cast<const real *>(ctx->noise[(STAGE == 1 ? 0 : 6) + j]);
   a.c = fluid_consts<real>(ctx);
+  if (predraw && STAGE == 0) {
+    NoiseOut<real> w;
+    for (int j = 0; j < 18; ++j) w.p[j] = static_cast<real *>(ctx->noise[j]);
+    const int blocks = std::max(1, std::min<int>(int((ctx->cells + 255) / 256), 8 * ctx->sm_count));
+    const cudaError_t e = launch_k(k_draw_noise<real>, dim3(blocks), dim3(256), 0, ctx->stream,
+                                   RngKey{a.c.k0, a.c.k1, a.c.box}, ctx->d.step, uint32_t(ctx->cells), w);
+    if (e != cudaSuccess) return e;
+  }
   a.step = ctx->d.step;
   a.partials = ctx->d.partials;
   a.status = ctx->d.status;
@@ -982,7 +1024,7 @@ cudaError_t launch_stage_t(const ic_ctx *ctx, void *const in_s[4], void *const i
   const StageLayout l = stage_layout_v<real, V>(ctx->p, zchunk_for(ctx), ctx->sm_count);
   a.ncols_x = l.ncols_x;
   a.ncols_y = l.ncols_y;
-  launch_stage_kernel<TX, TY, STAGE, NOISE>(a, l.ctas, ctx->stream, ctx->stage_copy);
+  launch_stage_kernel<TX, TY, STAGE, NOISE, predraw>(a, l.ctas, ctx->stream, ctx->stage_copy);
   return cudaGetLastError();
 }
 
@@ -1185,13 +1227,13 @@ cudaError_t launch_stage_raw_t(const ic_grid_params &p, const FluidConsts<real> 
                                void *const noise[12], const int64_t *step, double *partials,
                                cudaStream_t stream) {
   constexpr int TX = TileShape<real, 0>::TX, TY = TileShape<real, 0>::TY;
-  StageArgs<real> a;
+  StageArgs<real> a{};
   for (int j = 0; j < 4; ++j) {
     a.s[j] = static_cast<const real *>(in_s[j]);
     a.n[j] = static_cast<const real *>(in_n[j]);
     a.o[j] = static_cast<real *>(out[j]);
   }
-  a.pp = nullptr;
+  a.pp = nullptr;   // the allocation-free step draws stage 1's noise inline
   for (int j = 0; j < 12; ++j) a.noise_out[j] = stage == 0 ? static_cast<real *>(noise[j]) : nullptr;
   for (int j = 0; j < 6; ++j)
     a.noise_in[j] = stage == 0 ? nullptr : static_cast<const real *>(noise[(stage == 1 ? 0 : 6) + j]);

@@ -227,7 +227,8 @@ struct ic_ctx {
   std::unordered_map<uintptr_t, std::pair<int64_t, int>> tapes;       // step tapes recorded: step, particles
   std::unordered_map<const void *, ic::AdjGraph> adj_graphs;           // reverse-step graphs by tape
   void *pp = nullptr;       // particle pressure S Omega at centres (zero outside particle stencils)
-  void *noise[12] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1
+  void *noise[18] = {};     // kT > 0: W_2 and W_3 of the current step (6 components each), written by stage 1;
+                            // FP64: also W_1 (12..17), all three drawn by k_draw_noise before stage 1
   bool any_spring = false;  // some particle is tethered: the stage force source is launched
   double *cos_table = nullptr;      // cos(k x_i) along the wave axis, FP64
   float *cos_table_f = nullptr;     // the same in FP32
