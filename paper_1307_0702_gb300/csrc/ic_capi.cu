@@ -52,9 +52,13 @@ void dev_free(ic_ctx *ctx, void *p) {
   }
 }
 
+// set while ic_batch_step enqueues or captures its boxes' steps: the many
+// small launches of an ensemble gain from programmatic dependent launch
+thread_local bool t_pdl_scope = false;
+
 bool pdl_enabled() {
   const char *v = std::getenv("IC_PDL");
-  return v && v[0] == '1';
+  return t_pdl_scope || (v && v[0] == '1');
 }
 
 }  // namespace ic
@@ -1443,6 +1447,9 @@ ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out) {
   }
   ic_batch *b = new ic_batch();
   b->ctxs.assign(ctxs, ctxs + n);
+  // the boxes' step graphs are captured again inside ic_batch_step, with
+  // programmatic dependent launch between their kernels
+  for (int i = 0; i < n; ++i) invalidate_graphs(ctxs[i]);
   b->joins.resize(n, nullptr);
   bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
@@ -1458,6 +1465,10 @@ ic_status ic_batch_create(ic_ctx *const *ctxs, int n, ic_batch **out) {
 ic_status ic_batch_step(ic_batch *b, int nsteps, const double *w) {
   const ic::TraceRange tr("ic_batch_step");
   if (!b || nsteps < 0) return IC_ERR_ARG;
+  struct PdlScope {
+    PdlScope() { ic::t_pdl_scope = true; }
+    ~PdlScope() { ic::t_pdl_scope = false; }
+  } pdl_scope;
   if (nsteps == 0) return IC_OK;
   const int parity = b->ctxs[0]->cur;
   for (ic_ctx *c : b->ctxs) {

@@ -15,11 +15,13 @@
 
 namespace ic {
 
-// Programmatic dependent launch of the step's kernels (IC_PDL=1): each may
-// be scheduled while its predecessor in the stream drains, and waits for it
-// (pdl_enter, ic_device.cuh) before its first access to global memory.  Off
-// by default: on GB300 it made the 128^3 box with 10^4 particles 2 % slower
-// per step and the 256-box ensemble 2 % faster.
+// Programmatic dependent launch of the step's kernels: each may be
+// scheduled while its predecessor in the stream drains, and waits for it
+// (pdl_enter, ic_device.cuh) before its first access to global memory.  On
+// inside ic_batch_step and with IC_PDL=1, off otherwise: on GB300 it made
+// the 128^3 box with 10^4 particles 2 % slower per step and the 256-box
+// ensemble 2 % faster.
+extern thread_local bool t_pdl_scope;
 bool pdl_enabled();
 
 template <typename... K, typename... A>
