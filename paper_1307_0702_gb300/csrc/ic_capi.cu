@@ -525,8 +525,12 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
       cudaStreamSynchronize(ctx->stream))
     return bail(IC_ERR_CUDA);
   // Deterministic FP32 boxes whose rows the whole-row stage kernel takes start
-  // on it; with noise the column-tile kernels are the default
-  if (p.kT == 0.0 && ic::rows_eligible(p) && ic::rows_buffers_aligned(ctx)) ctx->tile_variant = ic::kTileRows;
+  // on it when its CTAs march runs of at least 8 planes (measured faster at
+  // 128^3, 13 planes a CTA; slower at 64^3, 3); with noise the column-tile
+  // kernels are the default
+  if (p.kT == 0.0 && ic::rows_eligible(p) && ic::rows_buffers_aligned(ctx) &&
+      ic::rows_mean_run(p, ctx->sm_count) >= 8.0)
+    ctx->tile_variant = ic::kTileRows;
   // a state of rho = rho0 is delta rho = 0: the buffers are already zero
   *out = ctx;
   return IC_OK;
@@ -1601,14 +1605,19 @@ ic_status ic_autotune(ic_ctx *ctx, int reps, int *choice) {
   const bool rows_ok = ic::stage_copy_active(ctx) != IC_STAGE_COPY_THREAD;
   ctx->tile_variant = v_in;
   ctx->stage_copy = copy_in;
-  // A context on the whole-row kernel is tuned among its z chunks only, one on
-  // the column-tile kernels among those: with noise the two families round the
-  // stress divergence differently, and tuning must not change a run's results.
+  // With noise a context on the whole-row kernel is tuned among its z chunks
+  // only, one on the column-tile kernels among those: the two families round
+  // the stress divergence differently, and tuning must not change a run's
+  // results.  Without noise they give the same bits and all are candidates
+  // (the whole-row kernel where its layout allows it).
   const bool whole_rows = ic::rows_active(ctx);
+  const bool any_family = ctx->p.kT == 0.0;
+  const bool rows_layout = ic::rows_eligible(ctx->p) && ic::rows_buffers_aligned(ctx);
   for (int cand = 0; cand < 5 && err == cudaSuccess; ++cand) {
     const int v = cand == 4 ? ic::kTileRows : (cand == 3 ? 1 : 0), copy = cand >= 3 ? IC_STAGE_COPY_THREAD : cand;
     if (copy != IC_STAGE_COPY_THREAD && !rows_ok) continue;
-    if ((v == ic::kTileRows) != whole_rows) continue;
+    if (!any_family && (v == ic::kTileRows) != whole_rows) continue;
+    if (v == ic::kTileRows && !rows_layout) continue;
     ctx->stage_copy = copy;
     int last = -1;
     for (int z : {32, 16, 8}) {

@@ -76,7 +76,7 @@ struct NoiseOut {
 // rounded operations as the stage-1 kernel's inline draw, so the step's bits
 // do not depend on which of the two drew them.  The FP64 transcendentals of
 // the 6 Box-Muller pairs dominate an FP64 step; drawn inline they are redone
-// for the ring cells of every tile (1.6x at 32 x 4).
+// for the ring cells of every tile (1.6x the cells at 32 x 4, 1.4x at 32 x 6).
 template <typename real>
 __global__ void __launch_bounds__(256) k_draw_noise(RngKey key, const int64_t *step, uint32_t cells,
                                                     NoiseOut<real> w) {
@@ -896,7 +896,9 @@ struct TileShape<float, 1> {
 };
 template <>
 struct TileShape<double, 0> {
-  static constexpr int TX = 32, TY = 4;
+  // 34 x 8 = 272 threads: nine warps a CTA at <= 227 registers (the stages
+  // use 162-165), against six at 32 x 4, and a smaller ring share
+  static constexpr int TX = 32, TY = 6;
 };
 template <>
 struct TileShape<double, 1> {

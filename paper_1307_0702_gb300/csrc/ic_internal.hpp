@@ -345,6 +345,9 @@ constexpr int kTileRows = 2;
 bool rows_eligible(const ic_grid_params &p);
 bool rows_buffers_aligned(const ic_ctx *ctx);
 int rows_ctas(const ic_ctx *ctx, int stage);
+// planes of z a CTA of the whole-row kernel marches per step on average (its
+// runs start with a fill of the plane rings: short runs pay it often)
+double rows_mean_run(const ic_grid_params &p, int sm_count);
 void rows_tile(const ic_ctx *ctx, int *ty);
 cudaError_t launch_stage_rows(const ic_ctx *ctx, int stage, void *const in_s[4], void *const in_n[4],
                               void *const out[4]);

@@ -872,6 +872,12 @@ bool rows_buffers_aligned(const ic_ctx *ctx) {
   return true;
 }
 
+double rows_mean_run(const ic_grid_params &p, int sm_count) {
+  const RowsPlan pl = rows_plan(p, 1, sm_count, 1, kRowsVC);
+  if (pl.ty == 0 || pl.ctas == 0) return 0.0;
+  return double(pl.ncols) * double(p.nz) / double(pl.ctas);
+}
+
 int rows_ctas(const ic_ctx *ctx, int stage) {
   return rows_plan(ctx->p, stage, ctx->sm_count, rows_zmin(ctx), kRowsVC).ctas;
 }

@@ -3,7 +3,7 @@
 FP64: every field, particle quantity and weighted average within 1e-11
 relative (normwise per field: max |gpu - oracle| / max |oracle - reference|),
 with the same Philox streams on both sides.  FP32: within 1e-4 relative.
-Sizes span several CTA tiles (32 x 13 cells for FP32, 32 x 4 for FP64, each
+Sizes span several CTA tiles (32 x 13 cells for FP32, 32 x 6 for FP64, each
 marching runs of z planes) and ragged tails.
 """
 import numpy as np
