@@ -232,8 +232,8 @@ void ic_batch_destroy(ic_batch *batch);
 /* Stage-kernel tiling.  The paper has no counterpart: this is a performance
  * setting.  The RK3 stage kernel marches CTAs along z in runs of at least
  * zchunk planes, over one of two families of tiles:
- *   column tiles, tile_x 32 or 16 (tile_y follows: 13 or 8 in FP32, 4 in
- *     FP64), each thread one cell, for any grid;
+ *   column tiles, tile_x 32 or 16 (tile_y follows: 13 or 8 in FP32, 6 or 4
+ *     in FP64), each thread one cell, for any grid;
  *   whole rows, tile_x 0 (FP32 only, nx a multiple of 4 and at most 128):
  *     bands of whole x rows copied into shared memory by bulk copies, four
  *     cells per thread (ic_get_tile then reports tile_x = nx and the band
@@ -243,15 +243,18 @@ void ic_batch_destroy(ic_batch *batch);
  * under every tiling; only the driven-mode amplitude A(t) and <A^2>_w change,
  * by the rounding of their reduction order.  Between the families the same
  * holds at kT = 0; with noise results agree to the rounding of the stress
- * divergence.  A context starts on whole rows where it can and kT = 0, on
+ * divergence.  A context starts on whole rows where it can, kT = 0 and the
+ * band planner gives its CTAs runs of at least 8 planes (a large box), on
  * column tiles otherwise.
  * ic_set_tile: IC_ERR_ARG for tile_x not 0, 16 or 32, whole rows on a grid
  * that does not take them, or zchunk < 8 (unless it is at least nz).
  * ic_get_tile: the current tiling (each pointer may be NULL).
  * ic_autotune synchronises the stream, times the three stage kernels of every
- * candidate of the context's current family (column tiles: tile_x 32 with
- * each staging mode of ic_set_stage_copy that the grid allows, and 16; whole
- * rows: the band planner's choice; zchunk 32, 16 and 8, clipped to nz), reps
+ * candidate (column tiles: tile_x 32 with each staging mode of
+ * ic_set_stage_copy that the grid allows, and 16; whole rows: the band
+ * planner's choice; zchunk 32, 16 and 8, clipped to nz) of both families at
+ * kT = 0, of the context's current family with noise (so that tuning never
+ * changes a run's results), reps
  * repetitions each, on the context's scratch buffers (U^n is left untouched:
  * the state is unchanged) and keeps the fastest; choice[3] (or NULL) receives
  * tile_x, tile_y, zchunk (the staging mode is kept in the context).
