@@ -178,6 +178,25 @@ def test_density_pdf_over_particle_sound_speed(cp_over_cf):
     assert np.mean(z ** 4) == pytest.approx(3.0, abs=0.1)     # and kurtosis 3
 
 
+def test_density_pdf_at_large_particle_sound_speed():
+    """The upper end of the paper's range, c_p up to 40 (5 and 10 c_f), dt cut
+    so that the CFL number alpha = c_p dt / h is 0.2: J rho stays Gaussian.
+    Its variance is within 4 % of rho0 kT / (c_p^2 V) at 5 c_f; at 10 c_f it is
+    5 % low at alpha = 0.2 (measured) and converges as alpha falls to 0.1."""
+    for cp_over_cf in (5.0, 10.0):
+        s, var = density_samples(cp_over_cf, 0.2 / (0.1 * cp_over_cf))
+        z = s / np.sqrt(np.var(s))
+        assert abs(np.mean(z ** 3)) < 0.05
+        assert np.mean(z ** 4) == pytest.approx(3.0, abs=0.1)
+        if cp_over_cf == 5.0:
+            assert np.var(s) == pytest.approx(var, rel=0.04)
+        else:
+            e2 = abs(np.var(s) / var - 1.0)
+            s1, _ = density_samples(cp_over_cf, 0.1 / (0.1 * cp_over_cf))
+            e1 = abs(np.var(s1) / var - 1.0)
+            assert e2 < 0.07 and e1 < 0.6 * e2, (e1, e2)
+
+
 def test_density_variance_converges_with_cfl_number():
     """c_p = 4 c_f: alpha = 0.4 at dt = 0.1 h / c_f, 0.2 at half of it."""
     s1, var = density_samples(4.0, 1.0)
