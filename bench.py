@@ -277,6 +277,33 @@ def sub_long_run(steps, local):
             "how": "one ic_step call of all steps after 3 warm-up steps, CUDA events around it, L2 not flushed"}
 
 
+def sub_force_accuracy():
+    """The radiation force of the single tethered particle (32^3, h = 1,
+    kT = 0, 8000 steps, Blackman-Harris window from step 3000) in FP32 and
+    FP64 against the FP64 oracle's value stored in
+    tests/golden/config1_force.json (written by the oracle alone)."""
+    from paper_1307_0702_gb300 import Grid, workloads as W
+
+    with open(os.path.join(ROOT, "tests", "golden", "config1_force.json")) as f:
+        gold = json.load(f)
+    out = {"workload": "one tethered particle at L/8 in the driven 32^3 box (h=1, kT=0, m_p=1.5 rho0 V, "
+                       f"kappa_p=0.5 kappa_f), {gold['nsteps']} steps, window from step {gold['skip']}",
+           "oracle_force": gold["f_spring"][0], "oracle_a2": gold["a2"]}
+    for prec in ("fp32", "fp64"):
+        gp, parts, _ = W.single_particle_config()
+        gp["precision"] = prec
+        rho, g = W.velocity_phase_wave_fields(gp)
+        w = W.blackman_harris(gold["nsteps"], gold["skip"])
+        with Grid(gp) as grid:
+            grid.set_state(rho, g)
+            grid.add_particles(parts["q"], parts["m_e"], parts["kappa_ratio"], parts["k_spring"])
+            grid.step(len(w), w)
+            fs, _, a2 = grid.time_average()
+        out[prec] = {"force_rel_err": float(fs[0][0] / gold["f_spring"][0] - 1.0),
+                     "a2_rel_err": float(a2 / gold["a2"] - 1.0)}
+    return out
+
+
 def setup_box(gp, parts, seed_thermal):
     from paper_1307_0702_gb300 import Grid, workloads as W
 
@@ -830,6 +857,7 @@ def main():
         subs["long_run"] = sub_long_run(args.long_steps, local)
         pk, pk_kind = load_peaks()
         subs["adjoint"] = adjoint_record("fp32", args.sub_adj_steps, 3, flush, local, pk, pk_kind, peak64)
+        subs["force_accuracy"] = sub_force_accuracy()
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
