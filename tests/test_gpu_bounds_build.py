@@ -5,8 +5,9 @@ status check.  It stands in for a memory checker.
 
 The parity tests (GPU against the oracle, ragged grids, every tiling and
 staging mode, particles on the periodic seam), the rebuilt neighbour lists,
-the whole-row kernel's tests and the check's own self-test run once more
-against that build in a child process; none may raise a flag.
+the whole-row kernel's tests, the adjoint's oracle comparisons and seeded
+random configurations, and the check's own self-test run once more against
+that build in a child process; none may raise a flag.
 """
 import os
 import subprocess
@@ -38,7 +39,9 @@ def test_parity_suite_under_index_checks():
     build.build(bounds_check=True)
     env = dict(os.environ, IC_LIBRARY="bounds")
     files = ["tests/test_gpu_bounds_build.py", "tests/test_gpu_parity.py", "tests/test_gpu_neighbours.py",
-             "tests/test_gpu_rows.py"]
-    r = subprocess.run([sys.executable, "-m", "pytest", *files, "-m", "gpu", "-x", "-q", "-p", "no:cacheprovider"],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
+             "tests/test_gpu_rows.py", "tests/test_gpu_adjoint.py"]
+    # the adjoint's seeded random configurations and its oracle comparison (short runs)
+    select = "not adjoint or random_configurations or matches_the_oracle_adjoint"
+    r = subprocess.run([sys.executable, "-m", "pytest", *files, "-m", "gpu", "-k", select, "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
