@@ -311,10 +311,12 @@ ic_status grow_particles(ic_ctx *ctx, int need) {
     s.bins = static_cast<int *>(dev_alloc(ctx, bytes));
     if (!s.bins) return fail(ctx, IC_ERR_OOM, "neighbour bin table allocation of %zu bytes failed", bytes);
   }
+  // one spare particle slot per array: lambda's holds the copy of the status
+  // word that the final substep leaves after the last particle's lambda
   for (PArray a : particle_arrays(ctx)) {
-    void *fresh = dev_alloc(ctx, a.per * size_t(cap));
-    if (!fresh) return fail(ctx, IC_ERR_OOM, "particle buffer allocation of %zu bytes failed", a.per * cap);
-    IC_CUDA(ctx, cudaMemsetAsync(fresh, 0, a.per * size_t(cap), ctx->stream));
+    void *fresh = dev_alloc(ctx, a.per * size_t(cap + 1));
+    if (!fresh) return fail(ctx, IC_ERR_OOM, "particle buffer allocation of %zu bytes failed", a.per * (cap + 1));
+    IC_CUDA(ctx, cudaMemsetAsync(fresh, 0, a.per * size_t(cap + 1), ctx->stream));
     if (*a.slot) {
       if (s.n > 0)
         IC_CUDA(ctx, cudaMemcpyAsync(fresh, *a.slot, a.per * size_t(s.n), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -332,11 +334,15 @@ ic_status grow_particles(ic_ctx *ctx, int need) {
 // (the caller's w is only read during the call).
 ic_status upload_weights(ic_ctx *ctx, int nsteps, const double *w) {
   if (w && nsteps > ctx->weights_cap) {
-    double *fresh = (double *)dev_alloc(ctx, size_t(nsteps) * sizeof(double));
+    // the step counter, the weights' header and the weights share one block,
+    // so that one copy uploads a call's header and weights
+    int64_t *fresh = (int64_t *)dev_alloc(ctx, (3 + size_t(nsteps)) * sizeof(int64_t));
     if (!fresh) return fail(ctx, IC_ERR_OOM, "weights buffer");
     IC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    dev_free(ctx, ctx->d.weights);
-    ctx->d.weights = fresh;
+    IC_CUDA(ctx, cudaMemcpy(fresh, ctx->d.step, 3 * sizeof(int64_t), cudaMemcpyDeviceToDevice));
+    dev_free(ctx, ctx->d.step);
+    ctx->d.step = fresh;
+    ctx->d.weights = reinterpret_cast<double *>(fresh + 3);
     cudaFreeHost(ctx->staging);
     ctx->staging = nullptr;
     IC_CUDA(ctx, cudaMallocHost(&ctx->staging, (size_t(nsteps) + 3) * sizeof(double)));
@@ -348,10 +354,9 @@ ic_status upload_weights(ic_ctx *ctx, int nsteps, const double *w) {
     const int64_t hdr[2] = {ctx->host_step, w ? int64_t(nsteps) : 0};
     std::memcpy(ctx->staging, hdr, sizeof(hdr));
     size_t bytes = sizeof(hdr);
-    if (w) {
+    if (w) {   // the weights follow the header in the device block too
       std::memcpy(ctx->staging + 2, w, size_t(nsteps) * sizeof(double));
-      IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.weights, ctx->staging + 2, size_t(nsteps) * sizeof(double),
-                                   cudaMemcpyHostToDevice, ctx->stream));
+      bytes += size_t(nsteps) * sizeof(double);
     }
     IC_CUDA(ctx, cudaMemcpyAsync(ctx->d.step + 1, ctx->staging, bytes, cudaMemcpyHostToDevice, ctx->stream));
     IC_CUDA(ctx, cudaEventRecord(ctx->staging_done, ctx->stream));
@@ -488,7 +493,9 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   if (cudaMemsetAsync(ctx->pp, 0, fbytes, ctx->stream) != cudaSuccess) return bail(IC_ERR_CUDA);
   ctx->n_partials = ic::fluid_num_partials(ctx);
   ctx->d.partials = (double *)dev_alloc(ctx, ctx->n_partials * sizeof(double));
-  ctx->d.step = (int64_t *)dev_alloc(ctx, 4 * sizeof(int64_t));
+  ctx->weights_cap = 1024;
+  // [0] step counter, [1] step of weights[0], [2] number of weights, then the weights
+  ctx->d.step = (int64_t *)dev_alloc(ctx, (3 + size_t(ctx->weights_cap)) * sizeof(int64_t));
   ctx->d.scalars = (double *)dev_alloc(ctx, 16 * sizeof(double));
   ctx->d.status = (int *)dev_alloc(ctx, 4 * sizeof(int));   // status, rebuild, bin_done, spare
   ctx->d.rebuilds = (long long *)dev_alloc(ctx, sizeof(long long));
@@ -496,8 +503,7 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   ctx->cos_table_f = (float *)dev_alloc(ctx, n_ax * sizeof(float));
   ctx->drive = (double *)dev_alloc(ctx, 3 * sizeof(double));
   ctx->drive_f = (float *)dev_alloc(ctx, 3 * sizeof(float));
-  ctx->weights_cap = 1024;
-  ctx->d.weights = (double *)dev_alloc(ctx, ctx->weights_cap * sizeof(double));
+  ctx->d.weights = ctx->d.step ? reinterpret_cast<double *>(ctx->d.step + 3) : nullptr;
   if (!ctx->d.partials || !ctx->d.step || !ctx->d.scalars || !ctx->d.status || !ctx->d.rebuilds || !ctx->cos_table ||
       !ctx->d.weights ||
       !ctx->cos_table_f || !ctx->drive || !ctx->drive_f)
@@ -517,10 +523,9 @@ ic_status ic_create_grid(const ic_grid_params *params, ic_ctx **out) {
   if (upload_drive(ctx, 0) != IC_OK ||
       cudaMemcpyAsync(ctx->cos_table, tab.data(), n_ax * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaMemcpyAsync(ctx->cos_table_f, tab_f.data(), n_ax * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) ||
-      cudaMemsetAsync(ctx->d.step, 0, 4 * sizeof(int64_t), ctx->stream) ||
+      cudaMemsetAsync(ctx->d.step, 0, (3 + size_t(ctx->weights_cap)) * sizeof(int64_t), ctx->stream) ||
       cudaMemsetAsync(ctx->d.scalars, 0, 16 * sizeof(double), ctx->stream) ||
       cudaMemsetAsync(ctx->d.rebuilds, 0, sizeof(long long), ctx->stream) ||
-      cudaMemsetAsync(ctx->d.weights, 0, ctx->weights_cap * sizeof(double), ctx->stream) ||
       cudaMemcpyAsync(ctx->d.status, zero_rebuild, sizeof(zero_rebuild), cudaMemcpyHostToDevice, ctx->stream) ||
       cudaStreamSynchronize(ctx->stream))
     return bail(IC_ERR_CUDA);
@@ -695,9 +700,14 @@ ic_status ic_forces_async(ic_ctx *ctx, int slot) {
     IC_CUDA(ctx, cudaMallocHost(&ctx->fetch[slot], need));
     ctx->fetch_cap[slot] = need;
   }
-  if (n3) IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot], ctx->ps.lam, rb, cudaMemcpyDeviceToHost, ctx->stream));
-  IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot] + rb, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost,
-                               ctx->stream));
+  // with particles one copy: lambda and, after it, the status word as the
+  // last step's final substep left it
+  if (n3)
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot], ctx->ps.lam, rb + sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  else
+    IC_CUDA(ctx, cudaMemcpyAsync(ctx->fetch[slot] + rb, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
   IC_CUDA(ctx, cudaEventRecord(ctx->fetch_done[slot], ctx->stream));
   ctx->fetch_n[slot] = ctx->ps.n;
   return IC_OK;

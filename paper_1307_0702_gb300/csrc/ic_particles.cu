@@ -621,7 +621,11 @@ __global__ void __launch_bounds__(kBlockThreads, min_blocks<real>()) k_final(PV<
   __threadfence();
   if (*reinterpret_cast<volatile int *>(rebuild)) bin_particles(P, pc, rebuilds);
   end_of_step_cta(e, red);
-  if (threadIdx.x == 0) *done = 0;
+  if (threadIdx.x == 0) {
+    // the step's status word beside lambda, so that one copy reads both back
+    *reinterpret_cast<int *>(P.lam + 3 * size_t(P.n)) = *reinterpret_cast<volatile int *>(e.status);
+    *done = 0;
+  }
 }
 
 template <typename real>
